@@ -1,0 +1,88 @@
+"""Shared test helpers: problem builders, error norms, golden-file loading."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+from paper_2402_04514_gb300 import assembly, workloads
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_vortex_tables():
+    rows = []
+    with open(os.path.join(GOLDEN, "vortex_l1_tables.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    a = np.array(rows)
+    return dict(dofs=a[:, 0].astype(int), limited={1: a[:, 1], 2: a[:, 2], 3: a[:, 3]},
+                first_order={1: a[:, 4], 2: a[:, 5], 3: a[:, 6]})
+
+
+def four_quadrant_problem(ne, degree, seed=0, gamma=1.4):
+    P = assembly.assemble_2d(ne, ne, degree)
+    U = workloads.four_quadrant(P.x[0], P.x[1], gamma=gamma, seed=seed)
+    return P, U
+
+
+def periodic_vortex_problem(ne, degree, gamma=1.4):
+    P = assembly.assemble_2d(ne, ne, degree, box=(-5.0, 5.0, -5.0, 5.0), periodic=(True, True))
+    U = workloads.vortex(P.x[0], P.x[1], 0.0, gamma=gamma)
+    return P, U
+
+
+def dirichlet_vortex_problem(ne, degree, gamma=5.0 / 3.0):
+    sides = dict(left="dirichlet", right="dirichlet", bottom="dirichlet", top="dirichlet")
+    P = assembly.assemble_2d(ne, ne, degree, box=(-5.0, 5.0, -5.0, 5.0), bc=sides)
+    U = workloads.vortex(P.x[0], P.x[1], 0.0, gamma=gamma)
+
+    def bdata(t):
+        return workloads.vortex(P.b_x[0], P.b_x[1], t, gamma=gamma)
+
+    return P, U, bdata
+
+
+def consolidated_l1(P, U, Ue):
+    """Sec. 6.2 error: sum over rho, momentum, E of ||q_h - q||_L1 / ||q||_L1 (lumped quadrature;
+    |.| of the momentum is the Euclidean norm)."""
+    d = P.dim
+    err = 0.0
+    for sl in (slice(0, 1), slice(1, d + 1), slice(d + 1, d + 2)):
+        dif = np.sqrt(((U[sl] - Ue[sl]) ** 2).sum(0))
+        ref = np.sqrt((Ue[sl] ** 2).sum(0))
+        err += float((P.mi * dif).sum() / (P.mi * ref).sum())
+    return err
+
+
+def transpose_map(P):
+    n = P.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(P.row_ptr))
+    key = rows * n + P.col_idx
+    tkey = P.col_idx.astype(np.int64) * n + rows
+    order = np.argsort(key)
+    pos = np.searchsorted(key[order], tkey)
+    tr = order[pos]
+    assert (key[tr] == tkey).all()
+    return tr, rows
+
+
+def entropy(U, gamma):
+    """Sec. 2.2, eq. (EntropyEuler): s = log(rho^{-gamma} p), eta = -rho s, q = -m s."""
+    d = U.shape[0] - 2
+    rho = U[0]
+    p = (gamma - 1.0) * (U[d + 1] - 0.5 * (U[1:d + 1] ** 2).sum(0) / rho)
+    s = np.log(rho ** (-gamma) * p)
+    return s, -rho * s, -U[1:d + 1] * s
+
+
+def rel_err(a, b):
+    """Per-component max |a - b| / max |b| (the parity norm), maximised over components."""
+    a = np.atleast_2d(a)
+    b = np.atleast_2d(b)
+    out = 0.0
+    for c in range(b.shape[0]):
+        scale = max(np.abs(b[c]).max(), 1e-300)
+        out = max(out, float(np.abs(a[c] - b[c]).max() / scale))
+    return out

@@ -1,0 +1,276 @@
+"""Pins of the oracle against what the paper and the mathematics fix (no GPU).
+
+Each check is independent of the oracle's own formulas: an exact Riemann solver, identities of the
+paper that relate separately computed quantities, invariants the paper proves, and the numbers the
+paper prints (tests/golden)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_04514_gb300 import assembly, workloads
+from tests import riemann_exact
+from tests.helpers import (consolidated_l1, dirichlet_vortex_problem, entropy, four_quadrant_problem,
+                           load_vortex_tables, periodic_vortex_problem, rel_err, transpose_map)
+
+
+def _random_pairs(rng, count, gamma, d=2):
+    rho = np.exp(rng.uniform(np.log(0.05), np.log(20.0), (2, count)))
+    p = np.exp(rng.uniform(np.log(0.05), np.log(20.0), (2, count)))
+    vel = rng.uniform(-3.0, 3.0, (2, d, count))
+    th = rng.uniform(0, 2 * np.pi, count)
+    nrm = np.stack([np.cos(th), np.sin(th)], 1)
+    UL = workloads.prim_to_cons(rho[0], vel[0], p[0], gamma).T.copy()
+    UR = workloads.prim_to_cons(rho[1], vel[1], p[1], gamma).T.copy()
+    return UL, UR, nrm, rho, vel, p
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_lambda_max_bounds_exact_wave_speed(oracle_mod, gamma):
+    """lambda_max^+ >= the exact maximum wave speed (Sec. 3.1 requires an upper bound); equality when
+    both waves are rarefactions (the two-rarefaction pressure is then exact)."""
+    rng = np.random.default_rng(11)
+    UL, UR, nrm, rho, vel, p = _random_pairs(rng, 3000, gamma)
+    lam = oracle_mod.lambda_max(UL, UR, nrm, gamma)
+    uL = (vel[0] * nrm.T).sum(0)
+    uR = (vel[1] * nrm.T).sum(0)
+    checked = rare = 0
+    for q in range(len(lam)):
+        try:
+            ex, ps = riemann_exact.max_wave_speed(rho[0, q], uL[q], p[0, q], rho[1, q], uR[q], p[1, q], gamma)
+        except ValueError:
+            continue  # vacuum: the bound is then the rarefaction heads, still an upper bound
+        checked += 1
+        assert lam[q] >= ex * (1 - 1e-12), (q, lam[q], ex)
+        if ps <= min(p[0, q], p[1, q]):
+            rare += 1
+            assert abs(lam[q] - ex) <= 1e-9 * ex
+    assert checked > 2500 and rare > 100
+
+
+def test_lambda_max_symmetry(oracle_mod):
+    """d_ij = d_ji needs lambda(U_i, U_j, n_ij) = lambda(U_j, U_i, n_ji) with n_ji = -n_ij (Sec. 3.2)."""
+    rng = np.random.default_rng(12)
+    UL, UR, nrm, *_ = _random_pairs(rng, 2000, 1.4)
+    a = oracle_mod.lambda_max(UL, UR, nrm, 1.4)
+    b = oracle_mod.lambda_max(UR, UL, -nrm, 1.4)
+    assert np.abs(a - b).max() <= 4e-16 * np.abs(a).max()
+
+
+def test_constant_state_preserved(oracle_mod):
+    for k in (1, 2):
+        P, _ = periodic_vortex_problem(4, k)
+        U = workloads.prim_to_cons(np.full(P.n, 1.3), np.stack([np.full(P.n, 0.4), np.full(P.n, -0.7)]),
+                                   np.full(P.n, 2.1), 1.4)
+        for order in (oracle_mod.LOW, oracle_mod.HIGH, oracle_mod.LIMITED):
+            O = oracle_mod.Oracle(P, params=dict(order=order))
+            tau = O.max_dt(U, 0.5)
+            U1, flags = O.stage(U, tau)
+            assert flags == 0
+            assert rel_err(U1, U) < 1e-14
+
+
+def _fq(order, k=2, ne=4, seed=3, passes=2, bounds_mode=0):
+    from oracle import oracle as om
+    P, U = four_quadrant_problem(ne, k, seed=seed)
+    O = om.Oracle(P, params=dict(order=order, limiter_passes=passes, bounds_mode=bounds_mode))
+    tau = O.max_dt(U, 0.5)
+    U1, flags, tr = O.stage(U, tau, trace=True)
+    return P, U, tau, U1, flags, tr
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_convex_reformulation(oracle_mod, k):
+    """Lemma ConveRef, eq. (ConvexRef): U^L = (1 + 2 tau d_ii/m_i) U_i + sum_j 2 tau d_ij/m_i Ubar_ij
+    + sum_k 2 tau d_i^k/m_i Ubar_i^k, with the bar states of eqs. (UsualBarState), (BoundaryBarState)."""
+    P, U, tau, _, flags, tr = _fq(oracle_mod.LOW, k=k)
+    assert flags == 0
+    m, n = P.m, P.n
+    rows = np.repeat(np.arange(n), np.diff(P.row_ptr))
+    R = (1.0 + 2.0 * tau * tr["dii"] / P.mi) * U
+    for q in range(m):
+        np.add.at(R[q], rows, 2.0 * tau * tr["dL"] / P.mi[rows] * tr["ubar"][q])
+        np.add.at(R[q], P.b_node, 2.0 * tau * tr["dB"] / P.mi[P.b_node] * tr["ubarB"][q])
+    assert rel_err(R, tr["UL"]) < 1e-13
+    # CFL (eq. (CFLcond)) holds with tau from eq. (MaxCFLdt) at Cr = 0.5
+    assert (-2.0 * tau * tr["dii"] / P.mi).max() <= 0.5 + 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_low_order_invariants(oracle_mod, k):
+    """Lemma InvariantProp (U^L in A), the local minimum principle of s (U^L is a convex combination of
+    U_i and bar states, s is quasi-concave) and the pointwise entropy inequality eq. (EntropyIneq) for
+    eta = -rho s."""
+    for seed in range(4):
+        P, U, tau, UL, flags, tr = _fq(oracle_mod.LOW, k=k, seed=seed)
+        g = 1.4
+        s_new, eta_new, _ = entropy(UL, g)
+        assert (UL[0] > 0).all() and np.isfinite(s_new).all()
+        s, eta, q = entropy(U, g)
+        rows = np.repeat(np.arange(P.n), np.diff(P.row_ptr))
+        stencil = np.abs(P.cij).sum(0) > 0
+        sb, _, _ = entropy(tr["ubar"][:, stencil], g)
+        smin = s.copy()
+        np.minimum.at(smin, rows[stencil], sb)
+        sbB, etaB, qB = entropy(tr["ubarB"], g)
+        np.minimum.at(smin, P.b_node, sbB)
+        assert (s_new >= smin - 1e-12 * np.abs(smin).max()).all()
+        # eq. (EntropyIneq)
+        sB, etaBd, qBd = entropy(tr["UB"], g)
+        lhs = P.mi * (eta_new - eta) / tau
+        for c in range(P.dim):
+            np.add.at(lhs, rows[stencil], q[c][P.col_idx[stencil]] * P.cij[c][stencil])
+            np.add.at(lhs, P.b_node, qBd[c] * P.b_c[c])
+        np.add.at(lhs, rows[stencil], -tr["dL"][stencil] * (eta[P.col_idx[stencil]] - eta[rows[stencil]]))
+        np.add.at(lhs, P.b_node, -tr["dB"] * (etaBd - eta[P.b_node]))
+        scale = np.abs(P.mi * eta / tau).max()
+        assert lhs.max() <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("k", [1, 2])
+def test_conservation(oracle_mod, order, k):
+    """Corollary TotBalLemma: periodic -> sum m_i U_i conserved; slip walls -> rho and E conserved (the
+    wall flux of eq. (eq:slip_boundary) only moves normal momentum)."""
+    P, U = periodic_vortex_problem(6, k)
+    O = oracle_mod.Oracle(P, params=dict(order=order))
+    tau = O.max_dt(U, 0.5)
+    U1, _ = O.stage(U, tau)
+    tot0, tot1 = (P.mi * U).sum(1), (P.mi * U1).sum(1)
+    assert np.abs(tot1 - tot0).max() <= 1e-13 * np.abs(tot0).max()
+    P, U, tau, U1, flags, tr = _fq(order, k=k)
+    tot0, tot1 = (P.mi * U).sum(1), (P.mi * U1).sum(1)
+    for c in (0, P.dim + 1):
+        assert abs(tot1[c] - tot0[c]) <= 1e-13 * abs(tot0[c])
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_high_low_identity_and_limiter_knobs(oracle_mod, k):
+    """eq. (HighLowOrderIdentity): m_i U^H = m_i U^L + sum_j A_ij + sum_k A_i^k; A_ij = -A_ji;
+    l = 0 gives U^L and l = 1 gives U^H (eq. (LimitedScheme)); |N_i| <= 1; l symmetric."""
+    P, U, tau, U1, flags, tr = _fq(oracle_mod.LIMITED, k=k)
+    m, n = P.m, P.n
+    tr_map, rows = transpose_map(P)
+    R = P.mi * tr["UL"]
+    for q in range(m):
+        np.add.at(R[q], rows, tr["A"][q])
+        np.add.at(R[q], P.b_node, tr["AB"][q])
+    assert rel_err(R, P.mi * tr["UH"]) < 1e-12
+    assert np.abs(tr["A"] + tr["A"][:, tr_map]).max() <= 1e-13 * np.abs(tr["A"]).max()
+    assert np.abs(tr["N"]).max() <= 1.0 + 1e-15
+    assert np.array_equal(tr["l1"], tr["l1"][tr_map]) and np.array_equal(tr["l2"], tr["l2"][tr_map])
+    assert tr["l1"].min() >= 0 and tr["l1"].max() <= 1 and tr["l1"].min() < 1  # the limiter is active
+    if k == 1:  # p_k = 0: d^min = d^L on collocated pairs, d^ev <= d^L
+        assert (tr["dH"] <= tr["dL"]).all() and (tr["dH"] >= 0).all()
+        co = P.coloc.astype(bool)
+        assert np.array_equal(tr["dH"][co], tr["dL"][co])
+    # l = 0 (no limiter pass) is the low-order update
+    _, _, _, U0, _, tr0 = _fq(oracle_mod.LIMITED, k=k, passes=0)
+    assert np.array_equal(U0, tr0["UL"])
+    # high-order scheme
+    _, _, _, UH, _, _ = _fq(oracle_mod.HIGH, k=k)
+    assert np.array_equal(UH, tr["UH"])
+
+
+def test_limiter_is_identity_when_bounds_are_loose(oracle_mod):
+    """With only positivity as the constraint (bounds_mode=1) a smooth admissible U^H is not limited:
+    l = 1 everywhere and the limited update equals the high-order update (eq. (LimitedScheme))."""
+    P, U = periodic_vortex_problem(6, 2)
+    O = oracle_mod.Oracle(P, params=dict(order=oracle_mod.LIMITED, bounds_mode=1))
+    tau = O.max_dt(U, 0.5)
+    U1, _, tr = O.stage(U, tau, trace=True)
+    assert (tr["l1"] == 1.0).all()
+    assert rel_err(U1, tr["UH"]) < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_limited_state_within_local_bounds(oracle_mod, k):
+    """Sec. 5.4: the final state lies in B_i (eq. (BiSet)): rho_min <= rho <= rho_max, s~ >= s~_min,
+    for the pass-1 and the final states; and the bounds contain U^L (convex combination of bar states)."""
+    g = 1.4
+    for seed in (0, 5):
+        P, U, tau, U1, flags, tr = _fq(oracle_mod.LIMITED, k=k, seed=seed)
+        for V in (tr["U1"], U1, tr["UL"]):
+            rho = V[0]
+            eps = V[-1] - 0.5 * (V[1:-1] ** 2).sum(0) / rho
+            st = rho ** (-g) * eps
+            tol = 1e-13
+            assert (rho >= tr["rho_min"] * (1 - tol)).all()
+            assert (rho <= tr["rho_max"] * (1 + tol)).all()
+            assert (st >= tr["s_min"] * (1 - 1e-12)).all()
+
+
+def test_sod_exact_solution(oracle_mod):
+    """Shock tube (gamma = 1.4, walls, t = 0.2): the first-order and limited schemes converge to the
+    exact Riemann solution in L1; the limited scheme is more accurate than the first-order one."""
+    g = 1.4
+    errs = {0: [], 2: []}
+    for cells in (50, 100, 200):
+        P = assembly.assemble_1d(cells, 1)
+        x = P.x[0]
+        rho_e, u_e, p_e = riemann_exact.sample((x - 0.5) / 0.2, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g)
+        for order in (0, 2):
+            O = oracle_mod.Oracle(P, params=dict(order=order))
+            U = workloads.sod(x)
+            t = 0.0
+            while t < 0.2 - 1e-14:
+                tau = min(O.max_dt(U, 0.5), 0.2 - t)
+                U, flags = O.ssprk3_step(U, tau)
+                assert not (flags & oracle_mod.F_INADMISSIBLE)
+                t += tau
+            errs[order].append(float((P.mi * np.abs(U[0] - rho_e)).sum()))
+    for order in (0, 2):
+        e = errs[order]
+        assert e[0] > e[1] > e[2]
+        assert math.log2(e[0] / e[2]) / 2 > 0.5
+    assert all(a < b for a, b in zip(errs[2], errs[0]))
+    assert errs[2][-1] < 0.01
+
+
+def _vortex_error(oracle_mod, ne, k, order):
+    P, U, bdata = dirichlet_vortex_problem(ne, k)
+    g = 5.0 / 3.0
+    O = oracle_mod.Oracle(P, gamma=g, params=dict(order=order))
+    t, tF = 0.0, 2.0
+    while t < tF - 1e-12:
+        tau = min(O.max_dt(U, 0.5, bdata=bdata(t)), tF - t)
+        U, flags = O.ssprk3_step(U, tau, bdata, t)
+        assert flags == 0
+        t += tau
+    return consolidated_l1(P, U, workloads.vortex(P.x[0], P.x[1], tF, gamma=g))
+
+
+def test_isentropic_vortex_against_paper_tables(oracle_mod):
+    """Isentropic vortex at 2304 DoFs (Sec. 6.2, test case (i); gamma = 5/3, exact Dirichlet data).
+    Limited scheme: the L1 errors printed in Appendix A, Table ErrorIsentropicConvex, for Q1 and Q2.
+    First-order scheme: the error ratios Q2/Q1 and Q3/Q1 of Table ErrorGrowthTable (1.22 and 1.36).
+    SSPRK3 replaces SSPRK54 (its coefficients are not in the paper); Cr = 0.5."""
+    tab = load_vortex_tables()
+    e1 = _vortex_error(oracle_mod, 24, 1, oracle_mod.LIMITED)
+    e2 = _vortex_error(oracle_mod, 16, 2, oracle_mod.LIMITED)
+    assert abs(e1 / tab["limited"][1][0] - 1.0) < 0.2, e1
+    assert abs(e2 / tab["limited"][2][0] - 1.0) < 0.1, e2
+    f = {k: _vortex_error(oracle_mod, ne, k, oracle_mod.LOW) for k, ne in ((1, 24), (2, 16), (3, 12))}
+    fo = tab["first_order"]
+    assert abs((f[2] / f[1]) / (fo[2][0] / fo[1][0]) - 1.0) < 0.05
+    assert abs((f[3] / f[1]) / (fo[3][0] / fo[1][0]) - 1.0) < 0.05
+    assert 0.5 < f[1] / fo[1][0] < 1.0  # same order of magnitude; see the design doc on the wave-speed bound
+
+
+def test_vortex_is_a_steady_solution_in_its_frame():
+    """The generator's vortex satisfies radial equilibrium dp/dr = rho v_theta^2 / r (the fix of the
+    printed formula) and p = rho^gamma (isentropic)."""
+    g = 1.4
+    r = np.linspace(0.2, 3.0, 50)
+    h = 1e-5
+    for x0 in ((0.0, 0.0),):
+        def prim(rr):
+            U = workloads.vortex(rr + x0[0], np.zeros_like(rr) + x0[1], 0.0, gamma=g, vinf=(0.0, 0.0),
+                                 x0=x0)
+            rho, vel, p = workloads.cons_to_prim(U, g)
+            return rho, vel, p
+        rho, vel, p = prim(r)
+        dp = (prim(r + h)[2] - prim(r - h)[2]) / (2 * h)
+        vt = vel[1]
+        assert np.allclose(dp, rho * vt ** 2 / r, rtol=1e-6, atol=1e-12)
+        assert np.allclose(p, rho ** g, rtol=1e-13)
