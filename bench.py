@@ -1,0 +1,288 @@
+#!/usr/bin/env python
+"""Throughput of the convex-limited graph-dG stage sweep on GB300 (DoF-stage updates per second).
+
+Workload (default): 2D Euler, gamma = 1.4, dG Q2 on 1024 x 1024 uniform quads of [0,1]^2 (9,437,184
+nodes), four-quadrant Riemann data drawn from default_rng(0), slip walls, full limited scheme (two limiter
+passes), CFL 0.5.  One step = one SSP-RK3 step = gdg_max_dt + 3 gdg_stage calls, i.e. 3 DoF-stage
+updates per node.  Inputs are synthetic and resident in HBM; the working set (several GB) is larger than
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own instance (replicas: the path has no
+exchange step); value = all ranks' DoF-stage updates / max over ranks of the timed region.
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only) on a bounded sample of the
+same workload (the same four-quadrant data on a 128 x 128 Q2 mesh).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF-stage updates/s"
+WORKLOADS = {
+    "q2_1024_four_quadrant": dict(N=1024, k=2, seed=0),
+    "q2_512_four_quadrant": dict(N=512, k=2, seed=0),
+    "q1_512_vortex_periodic": dict(N=512, k=1, vortex=True),
+}
+SAMPLE_N = 128  # oracle sample: same data on a 128 x 128 mesh
+
+
+def make_problem(spec):
+    from paper_2402_04514_gb300 import assembly, workloads
+
+    N, k = spec["N"], spec["k"]
+    if spec.get("vortex"):
+        P = assembly.assemble_2d(N, N, k, box=(-5.0, 5.0, -5.0, 5.0), periodic=(True, True))
+        U = workloads.vortex(P.x[0], P.x[1], 0.0, gamma=1.4)
+    else:
+        P = assembly.assemble_2d(N, N, k)
+        U = workloads.four_quadrant(P.x[0], P.x[1], gamma=1.4, seed=spec.get("seed", 0))
+    return P, U
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample_rate(steps, warmup=0, log=None):
+    """DoF-stage updates/s of the CPU oracle (single thread) on the 128^2 sample; returns (value, seconds)."""
+    from oracle.oracle import Oracle
+
+    spec = dict(WORKLOADS["q2_1024_four_quadrant"], N=SAMPLE_N)
+    P, U = make_problem(spec)
+    O = Oracle(P)
+    for _ in range(warmup):
+        tau = O.max_dt(U, 0.5)
+        U, _ = O.ssprk3_step(U, tau)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tau = O.max_dt(U, 0.5)
+        U, _ = O.ssprk3_step(U, tau)
+    dt = time.perf_counter() - t0
+    return P.n * 3 * steps / dt, dt, P.n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    value, secs, n_s = oracle_sample_rate(args.steps, args.warmup)
+    sample = (f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.steps} SSP-RK3 steps after "
+              f"{args.warmup} warm-up steps, single thread, {secs:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(args, None),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(args, n):
+    spec = WORKLOADS[args.workload]
+    return {"workload": args.workload, "mesh": f"{spec['N']}x{spec['N']} quads", "degree": spec["k"],
+            "dofs_per_gpu": n, "gamma": 1.4, "cfl": 0.5, "scheme": "convex-limited, 2 limiter passes",
+            "step": "SSP-RK3 step (max_dt + 3 stages)", "parallelism": f"replicas x{args.gpus}",
+            "l2": "no flush: working set larger than L2 (129 MB)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="q2_1024_four_quadrant", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2402_04514_gb300 import costmodel
+    from paper_2402_04514_gb300.gdg import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    spec = WORKLOADS[args.workload]
+    P, U0 = make_problem(spec)
+    counts = costmodel.Counts.of(P)
+    solver = Solver(P)
+    stream = torch.cuda.current_stream()
+    U = torch.from_numpy(U0).cuda()
+    bufs = (torch.empty_like(U), torch.empty_like(U))
+    nxt = torch.empty_like(U)
+    n = P.n
+
+    def step(Uc, out):
+        tau = solver.max_dt(Uc, 0.5)
+        solver.ssprk3_step(Uc, tau, bufs, out)
+        return out
+
+    for _ in range(args.warmup):
+        step(U, nxt)
+        U, nxt = nxt, U
+    torch.cuda.synchronize()
+    assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    solver.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(U, nxt)
+        U, nxt = nxt, U
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    prof = solver.profile_read()
+    solver.profile(False)
+    flags = solver.status()
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * n * 3 * args.steps / (ms_max / 1e3)
+    launches = sum(c for _, c in prof.values())
+
+    # roofline of the dominant kernel (its own launches' CUDA-event times inside the timed region)
+    top = max(prof, key=lambda k: prof[k][0])
+    top_ms, top_cnt = prof[top]
+    avg_s = top_ms / top_cnt / 1e3
+    fl = costmodel.flops_per_launch(counts)[top]
+    by = costmodel.bytes_per_launch(counts)[top]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": fl / avg_s / 1e12,
+                "peak": costmodel.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "alg_flops_per_launch": fl}
+    roofline_hbm = {"bound": "hbm", "kernel": f"k_{top}", "achieved": by / avg_s / 1e9, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": by / avg_s / 1e9 / hbm_peak, "alg_bytes_per_launch": by,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items() if v[1]}
+
+    # end to end through the public API with host buffers: H2D of the step's input from pinned memory,
+    # the step, D2H of its result, every step
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        hin.copy_(U)
+        hout = torch.empty_like(hin, pin_memory=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            U.copy_(hin, non_blocking=True)
+            step(U, nxt)
+            hout.copy_(nxt, non_blocking=True)
+            stream.synchronize()
+            hin, hout = hout, hin
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = torch.tensor([e0.elapsed_time(e1)], device="cuda", dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n * 3 * args.steps / (float(ems.item()) / 1e3), "unit": METRIC,
+               "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(U.numel() * 8)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, secs, n_s = oracle_sample_rate(args.cpu_baseline_steps)
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.cpu_baseline_steps} "
+                         f"SSP-RK3 steps, single thread, {secs:.1f} s"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(args, n), "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
+            "kernels": kernels, "status_flags": flags}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

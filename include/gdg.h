@@ -1,0 +1,160 @@
+/* gdg: GB300-native forward-Euler stage of the invariant-domain-preserving graph-based
+ * discontinuous Galerkin scheme for the compressible Euler equations (Kronbichler, Maier, Tomas,
+ * arXiv 2402.04514).  C ABI; all compute runs in CUDA kernels for sm_103a, in FP64.
+ *
+ * One stage (gdg_stage) computes, on the algebraic stencil of Sec. 2.3:
+ *   - the low-order update, Sec. 3.1, eq. (cijdijscheme), with the graph viscosity of
+ *     eq. (eq:dij_low_order) and the multi-valued boundary terms of Sec. 4.2,
+ *     eq. (cijdijschememodified);
+ *   - the high-order update of Sec. 5, eq. (HighScheme), with the viscosity of eq. (HighOrderViscosity)
+ *     (minimal viscosity, Sec. 5.1, eq. (ViscMin); entropy viscosity, Sec. 5.2) and the consistent
+ *     element mass;
+ *   - the relaxed local bounds of Sec. 5.4, eq. (eq:local_bounds), and two passes of the convex-limiting
+ *     line search of eq. (ConvexScheme) that blend the two (Sec. 6.1);
+ *   - the Shu-Osher combination U_out = alpha U_base + (1 - alpha) U_FE of an SSP Runge-Kutta stage.
+ * gdg_max_dt computes the time step of Sec. 3.3, eq. (MaxCFLdt).
+ *
+ * Conventions
+ *   States are FP64, component-major: U[c * n + i], c = 0 (rho), 1..dim (momentum), dim+1 (E).
+ *   Vector-valued per-entry data is [dim][count] (component-major).
+ *   Every pointer named "device" is a CUDA device pointer on the handle's device; "host" pointers are
+ *   read during the call only and stay owned by the caller.
+ *   Return codes are gdg_status_code values; gdg_error_string() names them.
+ *   stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ */
+#ifndef GDG_H
+#define GDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GDG_OK = 0,
+  GDG_EINVAL = 1,       /* bad argument (NULL pointer, size out of range, aliasing) */
+  GDG_ENOMEM = 2,       /* device or host allocation failed */
+  GDG_ECUDA = 3,        /* a CUDA runtime call failed */
+  GDG_ESETUP = 4,       /* problem data violates a requirement listed at gdg_problem */
+  GDG_EADMISSIBLE = 5,  /* a state handed to a stage is not admissible (rho <= 0 or eps <= 0) */
+  GDG_ECFL = 6,         /* a stage ran with tau above the CFL limit of eq. (CFLcond) */
+  GDG_ETIMEOUT = 7,     /* reserved: a bounded device-side wait gave up */
+  GDG_ENOTSUP = 8       /* configuration not supported (dim > 3, n_loc > 32, nnz >= 2^31, ...) */
+} gdg_status_code;
+
+enum { GDG_ORDER_LOW = 0, GDG_ORDER_HIGH = 1, GDG_ORDER_LIMITED = 2 };
+enum { GDG_BC_SLIP = 0, GDG_BC_DIRICHLET = 1 };
+/* sticky device flags, read by gdg_status */
+enum { GDG_FLAG_INADMISSIBLE = 1, GDG_FLAG_CFL = 2 };
+
+/* Method parameters.  gdg_default_params fills the paper's values: c_k = 1 and p_k = 1/2 (k even),
+ * 0 (k odd) of Sec. 5.1; c_ev = 1, 0.5, 0.25 for k = 1, 2, >= 3 (Sec. 5.2); c_r = 4, p_r = 1.5
+ * (Sec. 5.4, eq. (ViscMinConst2)); two limiter passes (Sec. 6.1); line-search bracket tolerance
+ * 1e-14 with at most 50 iterations. */
+typedef struct {
+  int32_t order;          /* GDG_ORDER_LOW: eq. (cijdijscheme) only; GDG_ORDER_HIGH: eq. (HighScheme)
+                             without limiting; GDG_ORDER_LIMITED: eq. (LimitedScheme) */
+  int32_t limiter_passes; /* 0, 1 or 2 */
+  int32_t bounds_mode;    /* 0: relaxed local bounds of eq. (eq:local_bounds); 1: only rho >= 0 and
+                             s~ >= 0 (a test knob: the limiter then keeps every admissible U^H) */
+  double c_k, p_k, c_ev, c_r, p_r;
+  double ls_tol;
+  int32_t ls_maxit;
+} gdg_params;
+
+/* One mesh instance (all host pointers, copied by gdg_setup).
+ * Requirements (gdg_setup returns GDG_ESETUP when one fails):
+ *   - rows are element-contiguous: element e owns nodes [e n_loc, (e+1) n_loc), n % n_loc == 0;
+ *   - row i lists every other node of its element (the consistent mass couples them all) and every j
+ *     with c_ij != 0; no diagonal entry; no duplicates; entries with c_ij = 0 carry only m_ij;
+ *   - c_ji == -c_ij exactly for every entry (Lemma PropSkew) and the transpose of every entry exists;
+ *   - partition of unity sum_j c_ij + sum_k c_i^{d,k} = 0 (Lemma LemPart) to 1e-12 relative;
+ *   - coloc[e] = 1 iff x_i == x_j (face partners across an element face), symmetric;
+ *   - m_i > 0 and sum_j MK[e][a][j] == m_i to 1e-12 relative (Sec. 5.3 absorbs the consistent mass into
+ *     the fluxes using sum_j (m_ij - delta_ij m_i) = 0); every MK block symmetric positive definite;
+ *   - boundary entries: 0 <= b_node < n, |c_i^{d,k}| > 0, b_type GDG_BC_SLIP or GDG_BC_DIRICHLET;
+ *   - gamma > 1, omega_measure = |Omega| > 0; for the limited order with bounds_mode 0,
+ *     r_h^- = 1 - c_r h_i^{p_r} > 0 at every node (h_i = (m_i / |Omega|)^{1/dim}). */
+typedef struct {
+  int32_t dim;            /* 1, 2 or 3 (m = dim + 2 components) */
+  int32_t degree;         /* polynomial degree k of the Q^k elements */
+  int32_t n_loc;          /* nodes per element, (k+1)^dim for Q^k, at most 32 */
+  int64_t n;              /* nodes */
+  int64_t nnz;            /* CSR entries (< 2^31) */
+  int64_t nb;             /* boundary entries (i, k) of Sec. 4.2 */
+  const int64_t* row_ptr; /* host [n+1] */
+  const int32_t* col_idx; /* host [nnz] */
+  const double* cij;      /* host [dim][nnz]: c_ij of eq. (eq:cij_def1) */
+  const uint8_t* coloc;   /* host [nnz] */
+  const double* mi;       /* host [n]: lumped mass m_i of eq. (eq:mass_matrices) */
+  const double* MK;       /* host [n / n_loc][n_loc][n_loc]: consistent element mass blocks m_ij */
+  const int32_t* b_node;  /* host [nb] */
+  const double* b_c;      /* host [dim][nb]: c_i^{d,k} of Sec. 4.2 */
+  const int32_t* b_type;  /* host [nb] */
+  double gamma;           /* ratio of specific heats, eq. (PressurEuler) */
+  double omega_measure;   /* |Omega| (Sec. 5.1 and 5.4 dimensionless mesh sizes) */
+  gdg_params params;
+} gdg_problem;
+
+typedef struct gdg_handle gdg_handle;
+
+typedef struct {
+  int64_t n, nnz, nb;
+  int32_t dim, n_loc;
+  int64_t device_bytes;   /* device memory held by the handle (setup copies and scratch) */
+} gdg_info;
+
+void gdg_default_params(int32_t degree, gdg_params* out);
+
+/* Validates and copies the problem to the current CUDA device, derives the per-entry and per-node
+ * data of the sweep (unit normals, transpose map, element mass inverses, relaxation factors) and
+ * allocates all scratch.  *out is owned by the caller and released with gdg_destroy.
+ * Errors: GDG_EINVAL (NULL), GDG_ENOTSUP, GDG_ESETUP, GDG_ENOMEM, GDG_ECUDA; *out is NULL on error. */
+int gdg_setup(const gdg_problem* prob, gdg_handle** out);
+
+/* Replaces the method parameters of a handle (same validation as gdg_setup). */
+int gdg_set_params(gdg_handle* h, const gdg_params* params);
+
+/* Sec. 3.3, eq. (MaxCFLdt): *tau_out = cfl * min_i (-m_i / (2 d_ii)), d_ii of
+ * eq. (eq:dij_low_order_supplement) at the state U (device [m][n]).  bdata (device [m][nb], in the
+ * order of gdg_problem's boundary entries) holds the Dirichlet data; it may be NULL when no entry is
+ * Dirichlet.  Synchronises the stream (the only call that does).  Flags an inadmissible U. */
+int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out,
+               void* stream);
+
+/* One forward-Euler stage with step tau followed by the SSP Runge-Kutta combination:
+ *   U_out = alpha * U_base + (1 - alpha) * FE(U_in)        (U_base may be NULL when alpha == 0).
+ * U_in, U_base, U_out: device [m][n]; U_out must not alias U_in or U_base.  bdata as in gdg_max_dt,
+ * evaluated at the stage time.  Asynchronous on stream; allocates nothing; inadmissible input and a
+ * CFL violation set sticky flags (gdg_status), never trap. */
+int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double alpha, double tau,
+              const double* bdata, double* U_out, void* stream);
+
+/* Reads (and with clear != 0 resets) the sticky device flags GDG_FLAG_*; synchronises the stream. */
+int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream);
+
+/* Copies an intermediate of the last stage to host memory (for tests and diagnostics): name is one of
+ * "dL" [nnz], "dB" [nb], "N" [n], "UL" [m][n], "rho_min" [n], "rho_max" [n], "s_min" [n], "l1" [nnz],
+ * "l2" [nnz], "U1" [m][n], "A" [m][nnz]; entries follow gdg_problem's order (boundary data its own).
+ * count must equal the array size.  Synchronises the stream. */
+int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t count, void* stream);
+
+/* Kernel timing for measurement.  With gdg_profile(h, 1) every kernel launch of gdg_stage and
+ * gdg_max_dt is bracketed by CUDA events recorded on the launching stream (no synchronisation is
+ * added).  gdg_profile_read synchronises, accumulates the elapsed time of each kernel of the sweep
+ * (indices GDG_K_*) into total_ms[GDG_NKERNELS] and launches[GDG_NKERNELS], and clears the records.
+ * gdg_profile(h, 0) stops recording and drops pending records. */
+enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIMIT2 = 4, GDG_K_FINAL = 5,
+       GDG_NKERNELS = 6 };
+int gdg_profile(gdg_handle* h, int32_t enable);
+int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
+
+int gdg_get_info(gdg_handle* h, gdg_info* out);
+void gdg_destroy(gdg_handle* h);
+const char* gdg_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,76 @@
+"""Algorithmic work of each sweep kernel per launch: compulsory HBM bytes and FP64 operations.
+
+Bytes: every array a kernel must read is read once and every array it writes is written once (per-entry
+arrays of nnz entries, per-node arrays of n nodes); neighbour states are counted once per node, not per
+entry (an ideal cache).  FP64 operations: the arithmetic of the method as the kernels state it, counted
+per stencil entry (c_ij != 0), per CSR entry and per node, with add/sub/mul = 1, fused multiply-add = 2,
+and division, square root and power = 1 each (the usual floating-point operation count; their cost in
+hardware is several to ~100 FMA issue slots, which is why the sweep is bound by the FP64 pipe).
+The line-search counts assume no bracketing iteration (the common case); iterations add work that is
+not counted, so the FP64 fraction reported is a lower bound.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final")
+
+
+@dataclass
+class Counts:
+    dim: int
+    n: int
+    nnz: int  # CSR entries
+    nnz_s: int  # entries with c_ij != 0
+    nb: int
+    n_loc: int
+
+    @property
+    def m(self):
+        return self.dim + 2
+
+    @staticmethod
+    def of(problem):
+        cs = np.abs(problem.cij).sum(0) > 0
+        return Counts(problem.dim, int(problem.n), int(problem.col_idx.size), int(cs.sum()), int(problem.b_node.size),
+                      int(problem.n_loc))
+
+
+def bytes_per_launch(c: Counts) -> dict:
+    m, d, n, nnz, s, nb, nl = c.m, c.dim, c.n, c.nnz, c.nnz_s, c.nb, c.n_loc
+    NPRIM = 6
+    rowptr = 4 * (n + 1)
+    ent_geom = nnz * (4 + 8) + s * 8 * d  # col, |c| of every entry; n_ij of stencil entries
+    return dict(
+        prim=8 * m * n + 8 * NPRIM * n,
+        maxdt=8 * m * n + 8 * 4 * n + rowptr + ent_geom + 8 * n,
+        low=8 * m * n + 8 * NPRIM * n + rowptr + ent_geom + 8 * s + 8 * (2 * m + 1 + 3) * n + 8 * 3 * nb,
+        high=8 * m * n * 2 + 8 * n + rowptr + nnz * (4 + 8 + 8 + 8) + 8 * s * 2 + 8 * n * nl
+        + 8 * 3 * n * 2 + 8 * m * n + 8 * n * 3 + 8 * (m + 1) * nnz + 8 * (m + 1) * nb,
+        limit2=rowptr + nnz * (4 + 8 + 8 * m) + 8 * m * n * 2 + 8 * 3 * n + 8 * 2 * n + 8 * nnz,
+        final=rowptr + nnz * (4 + 8 * 2 + 8 * m) + 8 * m * n * 3 + 8 * n,
+    )
+
+
+def flops_per_launch(c: Counts) -> dict:
+    m, d, n, nnz, s, nb, nl = c.m, c.dim, c.n, c.nnz, c.nnz_s, c.nb, c.n_loc
+    lam = 28  # wave-speed bound from the per-node primitives
+    vel = 2 * (2 * d) + 2  # two normal velocities
+    flux = 2 * (3 * d + 2)  # f(U_i) n and f(U_j) n
+    ls = 2 * m + (3 * d + 3) + 3  # U0 + l P, eps, s_min rho^gamma (one psi evaluation)
+    low_entry = vel + lam + 2 + flux + 2 + 11 * m + 4 + (3 * d + 3 + 2)
+    low_node = 3 * m + 3 + 3 + 1 + 3 * d + 4 * m + 5 * m + 1
+    return dict(
+        prim=n * (1 + 3 * d + 3 + 1 + 2 + 3 + 1 + 2),
+        maxdt=s * (vel + lam + 2) + n * 3 + nb * (lam + vel + 10),
+        low=s * low_entry + n * low_node + nb * (low_entry + 6),
+        high=s * (4 + 3 * m) + n * (2 * nl * m + m + 3) + nnz * (4 * m + m + ls) + nb * (3 * m + ls),
+        limit2=nnz * (2 * m + 2 + m + ls) + n * 2 * m + nb * (2 * m + m + 2 + ls),
+        final=nnz * (2 + 2 * m) + n * 3 * m + nb * (2 + 2 * m),
+    )
+
+
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12

@@ -1,0 +1,690 @@
+// C ABI of the gdg library (include/gdg.h): problem validation, derived per-entry / per-node data,
+// one device arena per handle, and the kernel sequence of a stage.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gdg_internal.cuh"
+
+using gdg::Dev;
+using gdg::Scratch;
+
+struct gdg_handle {
+  int device = 0;
+  int dim = 0, degree = 0, n_loc = 0;
+  int64_t n = 0, nnz = 0, nb = 0;
+  double gamma = 1.4, omega = 1.0;
+  gdg_params params{};
+  bool has_dirichlet = false;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  Dev D{};
+  Scratch S{};
+  // host copies needed after setup
+  std::vector<int> row_ptr, col, tr, borig, bnode_sorted;
+  std::vector<uint8_t> coloc;
+  std::vector<double> mi;
+  // device pointers of the parameter-dependent arrays
+  double *d_mu = nullptr, *d_rminus = nullptr, *d_rplus = nullptr, *d_muB = nullptr;
+  // kernel timing (gdg_profile)
+  struct Rec {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(gdg_handle* h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Runs one launcher, bracketed by events when profiling.
+template <class F>
+cudaError_t timed(gdg_handle* h, int kernel, cudaStream_t s, F&& launch) {
+  if (!h->profiling) return launch();
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, s);
+  cudaError_t e = launch();
+  cudaEventRecord(b, s);
+  h->recs.push_back({kernel, a, b});
+  return e;
+}
+
+}  // namespace
+
+namespace {
+
+template <class F>
+void parallel_for(int64_t count, F&& f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::min<int64_t>(std::max(1u, std::min(hw, 32u)), std::max<int64_t>(1, count / 65536));
+  if (nt <= 1) {
+    f(0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (count + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    int64_t b = t * chunk, e = std::min(count, b + chunk);
+    if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+  }
+  for (auto& x : th) x.join();
+}
+
+bool check_params(const gdg_params& p) {
+  if (p.order < GDG_ORDER_LOW || p.order > GDG_ORDER_LIMITED) return false;
+  if (p.limiter_passes < 0 || p.limiter_passes > 2) return false;
+  if (p.bounds_mode < 0 || p.bounds_mode > 1) return false;
+  if (!(p.c_k >= 0) || !(p.c_ev >= 0) || !(p.c_r >= 0) || !std::isfinite(p.p_k) || !std::isfinite(p.p_r))
+    return false;
+  if (!(p.ls_tol > 0) || p.ls_maxit < 0) return false;
+  return true;
+}
+
+// Invert a symmetric positive definite block by Cholesky; returns false if not SPD.
+bool spd_inverse(const double* A, int nl, double* Ainv) {
+  std::vector<double> L(nl * nl, 0.0);
+  for (int j = 0; j < nl; ++j) {
+    double s = A[j * nl + j];
+    for (int k = 0; k < j; ++k) s -= L[j * nl + k] * L[j * nl + k];
+    if (!(s > 0.0)) return false;
+    L[j * nl + j] = std::sqrt(s);
+    for (int i = j + 1; i < nl; ++i) {
+      double t = A[i * nl + j];
+      for (int k = 0; k < j; ++k) t -= L[i * nl + k] * L[j * nl + k];
+      L[i * nl + j] = t / L[j * nl + j];
+    }
+  }
+  for (int c = 0; c < nl; ++c) {  // solve L L^T x = e_c
+    std::vector<double> y(nl, 0.0);
+    for (int i = 0; i < nl; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * nl + k] * y[k];
+      y[i] = s / L[i * nl + i];
+    }
+    for (int i = nl - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < nl; ++k) s -= L[k * nl + i] * y[k];
+      y[i] = s / L[i * nl + i];
+    }
+    for (int i = 0; i < nl; ++i) Ainv[i * nl + c] = y[i];
+  }
+  for (int i = 0; i < nl; ++i)  // symmetrise
+    for (int j = i + 1; j < nl; ++j) {
+      double v = 0.5 * (Ainv[i * nl + j] + Ainv[j * nl + i]);
+      Ainv[i * nl + j] = Ainv[j * nl + i] = v;
+    }
+  return true;
+}
+
+struct Arena {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    size_t o = off;
+    off += (count * sizeof(T) + 255) / 256 * 256;
+    if (count == 0) off += 256;
+    return o;
+  }
+};
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? GDG_ENOMEM : GDG_ECUDA; }
+
+// Parameter-dependent per-entry / per-node data: c_k h^{p_k} (Sec. 5.1) and r_h^{+-} (Sec. 5.4).
+struct ParamArrays {
+  std::vector<double> mu, rm, rp, muB;
+};
+
+int param_arrays(const gdg_handle* h, const gdg_params& p, ParamArrays& A) {
+  const int64_t n = h->n, nnz = h->nnz;
+  const double dinv = 1.0 / h->dim;
+  A.mu.assign(nnz, 0.0);
+  A.rm.resize(n);
+  A.rp.resize(n);
+  A.muB.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double hi = std::pow(h->mi[i] / h->omega, dinv);
+    double rel = p.c_r * std::pow(hi, p.p_r);
+    A.rm[i] = 1.0 - rel;
+    A.rp[i] = 1.0 + rel;
+    A.muB[i] = p.c_k * std::pow(hi, p.p_k);
+    if (p.order == GDG_ORDER_LIMITED && p.bounds_mode == 0 && !(A.rm[i] > 0.0)) return GDG_ESETUP;
+    for (int e = h->row_ptr[i]; e < h->row_ptr[i + 1]; ++e) {
+      if (!h->coloc[e]) continue;
+      int j = h->col[e];
+      double hij = std::pow(0.5 * (h->mi[i] + h->mi[j]) / h->omega, dinv);
+      A.mu[e] = p.c_k * std::pow(hij, p.p_k);
+    }
+  }
+  return GDG_OK;
+}
+
+int upload_param_arrays(gdg_handle* h, const ParamArrays& A) {
+  const int64_t n = h->n, nnz = h->nnz;
+  cudaError_t e;
+  if ((nnz > 0 && (e = cudaMemcpy(h->d_mu, A.mu.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (n > 0 && (e = cudaMemcpy(h->d_rminus, A.rm.data(), sizeof(double) * n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (n > 0 && (e = cudaMemcpy(h->d_rplus, A.rp.data(), sizeof(double) * n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (n > 0 && (e = cudaMemcpy(h->d_muB, A.muB.data(), sizeof(double) * n, cudaMemcpyHostToDevice)) != cudaSuccess))
+    return cuda_fail(e);
+  const gdg_params& p = h->params;
+  Dev& D = h->D;
+  D.c_ev = p.c_ev;
+  D.order = p.order;
+  D.passes = p.limiter_passes;
+  D.bounds_mode = p.bounds_mode;
+  D.ls_tol = p.ls_tol;
+  D.ls_maxit = p.ls_maxit;
+  return GDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gdg_default_params(int32_t degree, gdg_params* out) {
+  if (!out) return;
+  out->order = GDG_ORDER_LIMITED;
+  out->limiter_passes = 2;
+  out->bounds_mode = 0;
+  out->c_k = 1.0;
+  out->p_k = (degree % 2 == 0) ? 0.5 : 0.0;
+  out->c_ev = degree <= 1 ? 1.0 : (degree == 2 ? 0.5 : 0.25);
+  out->c_r = 4.0;
+  out->p_r = 1.5;
+  out->ls_tol = 1e-14;
+  out->ls_maxit = 50;
+}
+
+const char* gdg_error_string(int code) {
+  switch (code) {
+    case GDG_OK: return "GDG_OK";
+    case GDG_EINVAL: return "GDG_EINVAL: invalid argument";
+    case GDG_ENOMEM: return "GDG_ENOMEM: out of memory";
+    case GDG_ECUDA: return "GDG_ECUDA: CUDA runtime error";
+    case GDG_ESETUP: return "GDG_ESETUP: problem data violates a documented requirement";
+    case GDG_EADMISSIBLE: return "GDG_EADMISSIBLE: inadmissible state";
+    case GDG_ECFL: return "GDG_ECFL: CFL condition violated";
+    case GDG_ETIMEOUT: return "GDG_ETIMEOUT: bounded device wait gave up";
+    case GDG_ENOTSUP: return "GDG_ENOTSUP: unsupported configuration";
+    default: return "gdg: unknown status code";
+  }
+}
+
+int gdg_setup(const gdg_problem* P, gdg_handle** out) {
+  if (!out) return GDG_EINVAL;
+  *out = nullptr;
+  if (!P || !P->row_ptr || !P->mi || !P->MK) return GDG_EINVAL;
+  if (P->nnz > 0 && (!P->col_idx || !P->cij || !P->coloc)) return GDG_EINVAL;
+  if (P->nb > 0 && (!P->b_node || !P->b_c || !P->b_type)) return GDG_EINVAL;
+  if (P->dim < 1 || P->dim > 3) return GDG_ENOTSUP;
+  if (P->n_loc < 1 || P->n_loc > 32 || P->degree < 1) return GDG_ENOTSUP;
+  if (P->n < 0 || P->nnz < 0 || P->nb < 0) return GDG_EINVAL;
+  if (P->n >= (int64_t(1) << 31) || P->nnz >= (int64_t(1) << 31) || P->nb >= (int64_t(1) << 31))
+    return GDG_ENOTSUP;
+  if (P->n % P->n_loc != 0) return GDG_ESETUP;
+  if (!(P->gamma > 1.0) || !(P->omega_measure > 0.0)) return GDG_ESETUP;
+  if (!check_params(P->params)) return GDG_EINVAL;
+
+  gdg_handle* h = new (std::nothrow) gdg_handle();
+  if (!h) return GDG_ENOMEM;
+  auto fail = [&](int code) {
+    gdg_destroy(h);
+    return code;
+  };
+  cudaGetDevice(&h->device);
+  const int dim = P->dim, nl = P->n_loc, m = dim + 2;
+  const int64_t n = P->n, nnz = P->nnz, nb = P->nb;
+  h->dim = dim;
+  h->degree = P->degree;
+  h->n_loc = nl;
+  h->n = n;
+  h->nnz = nnz;
+  h->nb = nb;
+  h->gamma = P->gamma;
+  h->omega = P->omega_measure;
+  h->params = P->params;
+
+  // ---- CSR structure ----
+  if (P->row_ptr[0] != 0 || P->row_ptr[n] != nnz) return fail(GDG_ESETUP);
+  h->row_ptr.resize(n + 1);
+  for (int64_t i = 0; i <= n; ++i) {
+    if (i > 0 && P->row_ptr[i] < P->row_ptr[i - 1]) return fail(GDG_ESETUP);
+    h->row_ptr[i] = (int)P->row_ptr[i];
+  }
+  h->col.assign(P->col_idx, P->col_idx + nnz);
+  h->coloc.assign(P->coloc, P->coloc + nnz);
+  h->mi.assign(P->mi, P->mi + n);
+  {
+    std::vector<char> rowbad(n, 0);
+    parallel_for(n, [&](int64_t b, int64_t e) {
+      std::vector<int> tmp;
+      for (int64_t i = b; i < e; ++i) {
+        if (!(h->mi[i] > 0.0)) { rowbad[i] = 1; continue; }
+        uint32_t mask = 0;
+        int same = 0;
+        tmp.assign(h->col.begin() + h->row_ptr[i], h->col.begin() + h->row_ptr[i + 1]);
+        std::sort(tmp.begin(), tmp.end());
+        if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) { rowbad[i] = 1; continue; }
+        for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
+          int j = h->col[q];
+          if (j < 0 || j >= n || j == i) { rowbad[i] = 1; break; }
+          if (j / nl == i / nl) {
+            mask |= 1u << (j % nl);
+            ++same;
+          }
+        }
+        if (same != nl - 1 || (mask & (1u << (i % nl)))) rowbad[i] = 1;
+      }
+    });
+    for (int64_t i = 0; i < n; ++i)
+      if (rowbad[i]) return fail(GDG_ESETUP);
+  }
+  // transpose map, exact skew symmetry (Lemma PropSkew), collocation symmetry
+  h->tr.assign(nnz, -1);
+  {
+    std::vector<char> bad(n, 0);
+    parallel_for(n, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i)
+        for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
+          int j = h->col[q], t = -1;
+          for (int r = h->row_ptr[j]; r < h->row_ptr[j + 1]; ++r)
+            if (h->col[r] == i) { t = r; break; }
+          if (t < 0 || h->coloc[t] != h->coloc[q]) { bad[i] = 1; continue; }
+          for (int k = 0; k < dim; ++k)
+            if (P->cij[(size_t)k * nnz + t] != -P->cij[(size_t)k * nnz + q]) bad[i] = 1;
+          h->tr[q] = t;
+        }
+    });
+    for (int64_t i = 0; i < n; ++i)
+      if (bad[i]) return fail(GDG_ESETUP);
+  }
+  // boundary entries sorted by node
+  std::vector<int> border(nb);
+  for (int64_t b = 0; b < nb; ++b) {
+    if (P->b_node[b] < 0 || P->b_node[b] >= n) return fail(GDG_ESETUP);
+    if (P->b_type[b] != GDG_BC_SLIP && P->b_type[b] != GDG_BC_DIRICHLET) return fail(GDG_ESETUP);
+    if (P->b_type[b] == GDG_BC_DIRICHLET) h->has_dirichlet = true;
+    double c2 = 0;
+    for (int k = 0; k < dim; ++k) c2 += P->b_c[(size_t)k * nb + b] * P->b_c[(size_t)k * nb + b];
+    if (!(c2 > 0.0)) return fail(GDG_ESETUP);
+    border[b] = (int)b;
+  }
+  std::stable_sort(border.begin(), border.end(), [&](int a, int b) { return P->b_node[a] < P->b_node[b]; });
+  std::vector<int> b_ptr(n + 1, 0);
+  for (int64_t b = 0; b < nb; ++b) b_ptr[P->b_node[b] + 1]++;
+  for (int64_t i = 0; i < n; ++i) b_ptr[i + 1] += b_ptr[i];
+  h->borig = border;
+  // partition of unity (Lemma LemPart)
+  {
+    std::vector<char> bad(n, 0);
+    parallel_for(n, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i)
+        for (int k = 0; k < dim; ++k) {
+          double s = 0, a = 0;
+          for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
+            double c = P->cij[(size_t)k * nnz + q];
+            s += c;
+            a += std::fabs(c);
+          }
+          for (int t = b_ptr[i]; t < b_ptr[i + 1]; ++t) {
+            double c = P->b_c[(size_t)k * nb + border[t]];
+            s += c;
+            a += std::fabs(c);
+          }
+          if (std::fabs(s) > 1e-12 * a) bad[i] = 1;
+        }
+    });
+    for (int64_t i = 0; i < n; ++i)
+      if (bad[i]) return fail(GDG_ESETUP);
+  }
+  // element mass blocks: row sums equal m_i (Sec. 5.3), SPD, inverse
+  const int64_t nel = n / nl;
+  std::vector<double> MKinv((size_t)nel * nl * nl);
+  {
+    std::vector<char> bad(nel, 0);
+    parallel_for(nel, [&](int64_t b, int64_t e) {
+      for (int64_t K = b; K < e; ++K) {
+        const double* A = P->MK + (size_t)K * nl * nl;
+        for (int a = 0; a < nl; ++a) {
+          double s = 0;
+          for (int c = 0; c < nl; ++c) s += A[a * nl + c];
+          double mi = h->mi[K * nl + a];
+          if (std::fabs(s - mi) > 1e-12 * mi) bad[K] = 1;
+          for (int c = 0; c < nl; ++c)
+            if (A[a * nl + c] != A[c * nl + a]) bad[K] = 1;
+        }
+        if (!spd_inverse(A, nl, MKinv.data() + (size_t)K * nl * nl)) bad[K] = 1;
+      }
+    });
+    for (int64_t K = 0; K < nel; ++K)
+      if (bad[K]) return fail(GDG_ESETUP);
+  }
+  // per-entry data: |c_ij|, n_ij, m_ij
+  std::vector<double> cnorm(nnz), cn((size_t)dim * nnz), mij(nnz, 0.0);
+  parallel_for(n, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i)
+      for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
+        double c2 = 0;
+        for (int k = 0; k < dim; ++k) c2 += P->cij[(size_t)k * nnz + q] * P->cij[(size_t)k * nnz + q];
+        double cm = std::sqrt(c2);
+        cnorm[q] = cm;
+        for (int k = 0; k < dim; ++k) cn[(size_t)k * nnz + q] = cm > 0 ? P->cij[(size_t)k * nnz + q] / cm : 0.0;
+        int j = h->col[q];
+        if (j / nl == i / nl) mij[q] = P->MK[((size_t)(i / nl) * nl + i % nl) * nl + j % nl];
+      }
+  });
+  // per-node: 1/m_i, 1/(kappa_i m_i) with kappa_i = 1/(row length + boundary entries of i)
+  std::vector<double> inv_mi(n), inv_km(n);
+  for (int64_t i = 0; i < n; ++i) {
+    inv_mi[i] = 1.0 / h->mi[i];
+    double terms = (h->row_ptr[i + 1] - h->row_ptr[i]) + (b_ptr[i + 1] - b_ptr[i]);
+    inv_km[i] = terms > 0 ? terms / h->mi[i] : 0.0;
+  }
+  std::vector<double> bnorm(nb), bn((size_t)dim * nb);
+  std::vector<int> btype(nb);
+  for (int64_t t = 0; t < nb; ++t) {
+    int b = border[t];
+    double c2 = 0;
+    for (int k = 0; k < dim; ++k) c2 += P->b_c[(size_t)k * nb + b] * P->b_c[(size_t)k * nb + b];
+    bnorm[t] = std::sqrt(c2);
+    for (int k = 0; k < dim; ++k) bn[(size_t)k * nb + t] = P->b_c[(size_t)k * nb + b] / bnorm[t];
+    btype[t] = P->b_type[b];
+  }
+
+  ParamArrays pa;
+  if (int rc = param_arrays(h, h->params, pa); rc != GDG_OK) return fail(rc);
+
+  // ---- device arena ----
+  Arena ar;
+  size_t o_rowptr = ar.take<int>(n + 1), o_col = ar.take<int>(nnz), o_tr = ar.take<int>(nnz);
+  size_t o_cnorm = ar.take<double>(nnz), o_cn = ar.take<double>((size_t)dim * nnz), o_mij = ar.take<double>(nnz);
+  size_t o_mu = ar.take<double>(nnz);
+  size_t o_mi = ar.take<double>(n), o_imi = ar.take<double>(n), o_ikm = ar.take<double>(n);
+  size_t o_rm = ar.take<double>(n), o_rp = ar.take<double>(n), o_muB = ar.take<double>(n);
+  size_t o_bptr = ar.take<int>(n + 1), o_bnorm = ar.take<double>(nb), o_bn = ar.take<double>((size_t)dim * nb);
+  size_t o_btype = ar.take<int>(nb), o_borig = ar.take<int>(nb);
+  size_t o_minv = ar.take<double>((size_t)nel * nl * nl);
+  size_t o_prim = ar.take<double>((size_t)gdg::NPRIM * n), o_dL = ar.take<double>(nnz), o_dB = ar.take<double>(nb);
+  size_t o_bbar = ar.take<double>(2 * nb), o_UL = ar.take<double>((size_t)m * n), o_RHSL = ar.take<double>((size_t)m * n);
+  size_t o_N = ar.take<double>(n), o_agg = ar.take<double>(3 * n), o_dd = ar.take<double>(nnz);
+  size_t o_A = ar.take<double>((size_t)m * nnz), o_AB = ar.take<double>((size_t)m * nb);
+  size_t o_bounds = ar.take<double>(3 * n), o_l1 = ar.take<double>(nnz), o_l1B = ar.take<double>(nb);
+  size_t o_l2 = ar.take<double>(nnz), o_l2B = ar.take<double>(nb), o_U1 = ar.take<double>((size_t)m * n);
+  size_t o_flags = ar.take<unsigned>(4), o_tau = ar.take<unsigned long long>(1);
+  h->arena_bytes = ar.off;
+  cudaError_t ce = cudaMalloc(&h->arena, h->arena_bytes);
+  if (ce != cudaSuccess) {
+    h->arena = nullptr;
+    cudaGetLastError();
+    return fail(cuda_fail(ce));
+  }
+  char* base = (char*)h->arena;
+  auto ptr = [&](size_t o) { return (void*)(base + o); };
+  auto up = [&](size_t o, const void* src, size_t bytes) {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpy(ptr(o), src, bytes, cudaMemcpyHostToDevice);
+  };
+  if ((ce = up(o_rowptr, h->row_ptr.data(), sizeof(int) * (n + 1))) != cudaSuccess ||
+      (ce = up(o_col, h->col.data(), sizeof(int) * nnz)) != cudaSuccess ||
+      (ce = up(o_tr, h->tr.data(), sizeof(int) * nnz)) != cudaSuccess ||
+      (ce = up(o_cnorm, cnorm.data(), sizeof(double) * nnz)) != cudaSuccess ||
+      (ce = up(o_cn, cn.data(), sizeof(double) * dim * nnz)) != cudaSuccess ||
+      (ce = up(o_mij, mij.data(), sizeof(double) * nnz)) != cudaSuccess ||
+      (ce = up(o_mi, h->mi.data(), sizeof(double) * n)) != cudaSuccess ||
+      (ce = up(o_imi, inv_mi.data(), sizeof(double) * n)) != cudaSuccess ||
+      (ce = up(o_ikm, inv_km.data(), sizeof(double) * n)) != cudaSuccess ||
+      (ce = up(o_bptr, b_ptr.data(), sizeof(int) * (n + 1))) != cudaSuccess ||
+      (ce = up(o_bnorm, bnorm.data(), sizeof(double) * nb)) != cudaSuccess ||
+      (ce = up(o_bn, bn.data(), sizeof(double) * dim * nb)) != cudaSuccess ||
+      (ce = up(o_btype, btype.data(), sizeof(int) * nb)) != cudaSuccess ||
+      (ce = up(o_borig, border.data(), sizeof(int) * nb)) != cudaSuccess ||
+      (ce = up(o_minv, MKinv.data(), sizeof(double) * MKinv.size())) != cudaSuccess ||
+      (ce = cudaMemset(ptr(o_flags), 0, 16)) != cudaSuccess)
+    return fail(cuda_fail(ce));
+
+  Dev& D = h->D;
+  D.n = (int)n;
+  D.nnz = (int)nnz;
+  D.nb = (int)nb;
+  D.n_loc = nl;
+  D.row_ptr = (const int*)ptr(o_rowptr);
+  D.col = (const int*)ptr(o_col);
+  D.tr = (const int*)ptr(o_tr);
+  D.cnorm = (const double*)ptr(o_cnorm);
+  D.cn = (const double*)ptr(o_cn);
+  D.mij = (const double*)ptr(o_mij);
+  D.mu = (const double*)ptr(o_mu);
+  D.mi = (const double*)ptr(o_mi);
+  D.inv_mi = (const double*)ptr(o_imi);
+  D.inv_km = (const double*)ptr(o_ikm);
+  D.rminus = (const double*)ptr(o_rm);
+  D.rplus = (const double*)ptr(o_rp);
+  D.muB = (const double*)ptr(o_muB);
+  D.b_ptr = (const int*)ptr(o_bptr);
+  D.bnorm = (const double*)ptr(o_bnorm);
+  D.bn = (const double*)ptr(o_bn);
+  D.btype = (const int*)ptr(o_btype);
+  D.borig = (const int*)ptr(o_borig);
+  D.MKinv = (const double*)ptr(o_minv);
+  D.gamma = P->gamma;
+  D.gm1 = P->gamma - 1.0;
+  D.e_exp = (P->gamma - 1.0) / (2.0 * P->gamma);
+  D.inv_e = 1.0 / D.e_exp;
+  double r = std::round(D.inv_e);
+  D.ie = (std::fabs(D.inv_e - r) < 1e-12 * D.inv_e && r >= 1 && r <= 64) ? (int)r : 0;
+  D.k13 = (P->gamma + 1.0) / (2.0 * P->gamma);
+  D.inv_gp1 = 1.0 / (P->gamma + 1.0);
+  h->d_mu = (double*)ptr(o_mu);
+  h->d_rminus = (double*)ptr(o_rm);
+  h->d_rplus = (double*)ptr(o_rp);
+  h->d_muB = (double*)ptr(o_muB);
+
+  Scratch& S = h->S;
+  S.prim = (double*)ptr(o_prim);
+  S.dL = (double*)ptr(o_dL);
+  S.dB = (double*)ptr(o_dB);
+  S.bbar = (double*)ptr(o_bbar);
+  S.UL = (double*)ptr(o_UL);
+  S.RHSL = (double*)ptr(o_RHSL);
+  S.N = (double*)ptr(o_N);
+  S.agg = (double*)ptr(o_agg);
+  S.ddiff = (double*)ptr(o_dd);
+  S.A = (double*)ptr(o_A);
+  S.AB = (double*)ptr(o_AB);
+  S.bounds = (double*)ptr(o_bounds);
+  S.l1 = (double*)ptr(o_l1);
+  S.l1B = (double*)ptr(o_l1B);
+  S.l2 = (double*)ptr(o_l2);
+  S.l2B = (double*)ptr(o_l2B);
+  S.U1 = (double*)ptr(o_U1);
+  S.flags = (unsigned*)ptr(o_flags);
+  S.tau_bits = (unsigned long long*)ptr(o_tau);
+
+  if (int rc = upload_param_arrays(h, pa); rc != GDG_OK) return fail(rc);
+  *out = h;
+  return GDG_OK;
+}
+
+int gdg_set_params(gdg_handle* h, const gdg_params* params) {
+  if (!h || !params || !check_params(*params)) return GDG_EINVAL;
+  ParamArrays pa;
+  if (int rc = param_arrays(h, *params, pa); rc != GDG_OK) return rc;
+  h->params = *params;
+  return upload_param_arrays(h, pa);
+}
+
+int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out, void* stream) {
+  if (!h || !U || !tau_out || !(cfl > 0)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->S.tau_bits, 0x7f, sizeof(unsigned long long), s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_prim(h->dim, h->D, h->S, U, s); })) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = timed(h, GDG_K_MAXDT, s, [&] { return gdg::launch_maxdt(h->dim, h->D, h->S, U, bdata, s); })) !=
+      cudaSuccess)
+    return cuda_fail(e);
+  unsigned long long bits = 0;
+  if ((e = cudaMemcpyAsync(&bits, h->S.tau_bits, sizeof(bits), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+  double v;
+  std::memcpy(&v, &bits, sizeof(v));
+  *tau_out = (bits == 0x7f7f7f7f7f7f7f7fULL) ? INFINITY : cfl * v;
+  return GDG_OK;
+}
+
+int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double alpha, double tau,
+              const double* bdata, double* U_out, void* stream) {
+  if (!h || !U_in || !U_out || !(tau >= 0) || !std::isfinite(tau)) return GDG_EINVAL;
+  if (U_out == U_in || (U_base && U_out == U_base)) return GDG_EINVAL;
+  if (alpha != 0.0 && !U_base) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int dim = h->dim;
+  const Dev& D = h->D;
+  cudaError_t e;
+  const Scratch& S = h->S;
+  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_prim(dim, D, S, U_in, s); })) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = timed(h, GDG_K_LOW, s, [&] {
+         return gdg::launch_low(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);
+       })) != cudaSuccess)
+    return cuda_fail(e);
+  if (D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0)) return GDG_OK;
+  if ((e = timed(h, GDG_K_HIGH, s, [&] {
+         return gdg::launch_high(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);
+       })) != cudaSuccess)
+    return cuda_fail(e);
+  if (D.order == GDG_ORDER_HIGH) return GDG_OK;
+  if ((e = timed(h, GDG_K_LIMIT2, s, [&] { return gdg::launch_limit2(dim, D, S, U_base, alpha, U_out, s); })) !=
+      cudaSuccess)
+    return cuda_fail(e);
+  if (D.passes == 1) return GDG_OK;
+  if ((e = timed(h, GDG_K_FINAL, s, [&] { return gdg::launch_final(dim, D, S, U_base, alpha, U_out, s); })) !=
+      cudaSuccess)
+    return cuda_fail(e);
+  return GDG_OK;
+}
+
+int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream) {
+  if (!h || !flags) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned v = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&v, h->S.flags, sizeof(v), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e);
+  if (clear && (e = cudaMemsetAsync(h->S.flags, 0, sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+  *flags = (int32_t)v;
+  return GDG_OK;
+}
+
+int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count, void* stream) {
+  if (!h || !name || !dst) return GDG_EINVAL;
+  const int64_t n = h->n, nnz = h->nnz, nb = h->nb, m = h->dim + 2;
+  const double* src = nullptr;
+  int64_t want = -1;
+  int kind = 0;  // 0 plain copy, 1 symmetrised per-entry limiter, 2 boundary order
+  std::string nm(name);
+  if (nm == "dL") { src = h->S.dL; want = nnz; }
+  else if (nm == "dB") { src = h->S.dB; want = nb; kind = 2; }
+  else if (nm == "N") { src = h->S.N; want = n; }
+  else if (nm == "UL") { src = h->S.UL; want = m * n; }
+  else if (nm == "U1") { src = h->S.U1; want = m * n; }
+  else if (nm == "A") { src = h->S.A; want = m * nnz; }
+  else if (nm == "rho_min") { src = h->S.bounds; want = n; }
+  else if (nm == "rho_max") { src = h->S.bounds + n; want = n; }
+  else if (nm == "s_min") { src = h->S.bounds + 2 * n; want = n; }
+  else if (nm == "l1") { src = h->S.l1; want = nnz; kind = 1; }
+  else if (nm == "l2") { src = h->S.l2; want = nnz; kind = 1; }
+  else return GDG_EINVAL;
+  if (count != want) return GDG_EINVAL;
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
+  std::vector<double> tmp(want);
+  if (want > 0 && (e = cudaMemcpy(tmp.data(), src, sizeof(double) * want, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e);
+  if (kind == 0) {
+    std::memcpy(dst, tmp.data(), sizeof(double) * want);
+  } else if (kind == 1) {
+    for (int64_t q = 0; q < want; ++q) dst[q] = std::min(tmp[q], tmp[h->tr[q]]);
+  } else {
+    for (int64_t t = 0; t < want; ++t) dst[h->borig[t]] = tmp[t];
+  }
+  return GDG_OK;
+}
+
+int gdg_profile(gdg_handle* h, int32_t enable) {
+  if (!h) return GDG_EINVAL;
+  for (auto& r : h->recs) {
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+  h->profiling = enable != 0;
+  return GDG_OK;
+}
+
+int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches) {
+  if (!h || !total_ms || !launches) return GDG_EINVAL;
+  for (int k = 0; k < GDG_NKERNELS; ++k) {
+    total_ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  int rc = GDG_OK;
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    total_ms[r.kernel] += ms;
+    launches[r.kernel] += 1;
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+  return rc;
+}
+
+int gdg_get_info(gdg_handle* h, gdg_info* out) {
+  if (!h || !out) return GDG_EINVAL;
+  out->n = h->n;
+  out->nnz = h->nnz;
+  out->nb = h->nb;
+  out->dim = h->dim;
+  out->n_loc = h->n_loc;
+  out->device_bytes = (int64_t)h->arena_bytes;
+  return GDG_OK;
+}
+
+void gdg_destroy(gdg_handle* h) {
+  if (!h) return;
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+  if (h->arena) cudaFree(h->arena);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,238 @@
+// Internal declarations of the gdg library: device-side problem layout, scratch, the Euler helpers
+// shared by the sweep kernels, and the kernel launchers.  Not part of the C ABI (include/gdg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/gdg.h"
+
+namespace gdg {
+
+// Per-node primitive record written by k_prim and read for every neighbour in the sweeps.
+enum { PR_IRHO = 0, PR_P, PR_A, PR_PME, PR_F, PR_ST, NPRIM };
+
+// Per-entry flag bits.
+enum { EF_STENCIL = 1, EF_COLOC = 2, EF_SAME_ELEM = 4 };
+
+// Everything a kernel needs, passed by value.  Per-entry and per-node arrays are device pointers in
+// CSR order (rows element-contiguous); boundary entries are sorted by node (b_ptr indexes them).
+struct Dev {
+  int n, nnz, nb, n_loc;
+  // CSR
+  const int* row_ptr;   // [n+1]
+  const int* col;       // [nnz]
+  const int* tr;        // [nnz] position of the transposed entry (j, i)
+  const double* cnorm;  // [nnz] |c_ij| (0 when c_ij = 0)
+  const double* cn;     // [dim][nnz] n_ij = c_ij / |c_ij|
+  const double* mij;    // [nnz] consistent mass m_ij (0 across elements)
+  const double* mu;     // [nnz] c_k h_ij^{p_k} for collocated pairs, else 0 (Sec. 5.1, eq. (ViscMin))
+  // nodes
+  const double* mi;     // [n]
+  const double* inv_mi; // [n]
+  const double* inv_km; // [n] 1 / (kappa_i m_i), Sec. 5.4, eq. (ConvexScheme)
+  const double* rminus; // [n] r_h^- (Sec. 5.4)
+  const double* rplus;  // [n] r_h^+
+  const double* muB;    // [n] c_k h_i^{p_k} (boundary minimal-viscosity factor)
+  const int* b_ptr;     // [n+1]
+  // boundary entries (sorted by node)
+  const double* bnorm;  // [nb] |c_i^{d,k}|
+  const double* bn;     // [dim][nb] unit normals
+  const int* btype;     // [nb]
+  const int* borig;     // [nb] index of the entry in the caller's order (for Dirichlet data)
+  const double* MKinv;  // [n / n_loc][n_loc][n_loc]
+  // equation of state and method constants
+  double gamma, gm1;    // gamma, gamma - 1
+  double e_exp;         // e = (gamma - 1) / (2 gamma)
+  double inv_e;         // 1 / e
+  int ie;               // 1 / e when it is an integer (7 for gamma = 1.4, 5 for gamma = 5/3), else 0
+  double k13;           // (gamma + 1) / (2 gamma)
+  double inv_gp1;       // 1 / (gamma + 1)
+  double c_ev;
+  int order, passes, bounds_mode;
+  double ls_tol;
+  int ls_maxit;
+};
+
+struct Scratch {
+  double* prim;    // [NPRIM][n]
+  double* dL;      // [nnz]
+  double* dB;      // [nb]
+  double* bbar;    // [2][nb] rho and s~ of the boundary bar states
+  double* UL;      // [m][n]
+  double* RHSL;    // [m][n] low-order right-hand side (sum of fluxes and viscous terms)
+  double* N;       // [n]
+  double* agg;     // [3][n] one-hop aggregates (rho min, rho max, s~ min)
+  double* ddiff;   // [nnz] d^H - d^L
+  double* A;       // [m][nnz]
+  double* AB;      // [m][nb]
+  double* bounds;  // [3][n] rho_min, rho_max, s~_min
+  double* l1;      // [nnz] per-row limiter coefficients, pass 1 (before symmetrisation)
+  double* l1B;     // [nb]
+  double* l2;      // [nnz] pass 2
+  double* l2B;     // [nb]
+  double* U1;      // [m][n]
+  unsigned int* flags;
+  unsigned long long* tau_bits;  // min of positive doubles via their bit patterns
+};
+
+#define GDG_DISPATCH(dim, fn, ...)        \
+  switch (dim) {                          \
+    case 1: return fn<1>(__VA_ARGS__);    \
+    case 2: return fn<2>(__VA_ARGS__);    \
+    case 3: return fn<3>(__VA_ARGS__);    \
+    default: return cudaErrorInvalidValue; \
+  }
+
+// Kernel launchers (kernels_low.cu, kernels_high.cu, kernels_limit.cu); dim in 1..3.
+cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s);
+cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
+                         cudaStream_t s);
+cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
+                       double tau, const double* Ubase, double alpha, double* Uout, cudaStream_t s);
+cudaError_t launch_high(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
+                        double tau, const double* Ubase, double alpha, double* Uout, cudaStream_t s);
+cudaError_t launch_limit2(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha,
+                          double* Uout, cudaStream_t s);
+cudaError_t launch_final(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha,
+                         double* Uout, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------------
+// Device helpers (Euler equations of Sec. 2.2 and the pieces of Sec. 3-5 used by several kernels).
+
+__device__ __forceinline__ double ipow(double x, int k) {
+  double r = 1.0;
+  while (k > 0) {
+    if (k & 1) r *= x;
+    x *= x;
+    k >>= 1;
+  }
+  return r;
+}
+
+// lambda_max^+ of the Riemann problem along n (Sec. 3.1, eq. (eq:dij_low_order)), from the normal
+// velocities u, pressures p, sound speeds a and p^{-e} of both states: the two-rarefaction pressure
+// p~ bounds the star pressure from above for 1 < gamma <= 5/3; the outer wave speeds at p~ bound the
+// exact ones.
+__device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL, double aL, double pmeL,
+                                             double uR, double pR, double aR, double pmeR) {
+  double num = fmax(aL + aR - 0.5 * D.gm1 * (uR - uL), 0.0);
+  double r = num / (aL * pmeL + aR * pmeR);
+  double pt = D.ie > 0 ? ipow(r, D.ie) : pow(r, D.inv_e);
+  double xL = pt - pL, xR = pt - pR;
+  double sL = xL > 0.0 ? sqrt(1.0 + D.k13 * xL / pL) : 1.0;
+  double sR = xR > 0.0 ? sqrt(1.0 + D.k13 * xR / pR) : 1.0;
+  double l1 = uL - aL * sL;
+  double l3 = uR + aR * sR;
+  return fmax(fmax(-l1, 0.0), fmax(l3, 0.0));
+}
+
+// f(U) n for a unit vector n, given m.n = mn, v.n = un and p: [m.n, m un + p n, (E + p) un].
+template <int DIM>
+__device__ __forceinline__ void flux_n(const double* U, const double* n, double mn, double un, double p,
+                                       double* out) {
+  out[0] = mn;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) out[1 + k] = U[1 + k] * un + p * n[k];
+  out[DIM + 1] = (U[DIM + 1] + p) * un;
+}
+
+template <int DIM>
+__device__ __forceinline__ double internal_energy(const double* U) {
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += U[1 + k] * U[1 + k];
+  return U[DIM + 1] - 0.5 * m2 / U[0];
+}
+
+// Slip (Sec. 4.1, eq. (eq:slip_boundary)) or Dirichlet boundary state of entry b.
+template <int DIM>
+__device__ __forceinline__ void boundary_state(const Dev& D, int b, const double* Ui, const double* bdata,
+                                               const double* n, double* UB) {
+  constexpr int M = DIM + 2;
+  if (D.btype[b] == GDG_BC_DIRICHLET) {
+    int o = D.borig[b];
+#pragma unroll
+    for (int q = 0; q < M; ++q) UB[q] = bdata[(size_t)q * D.nb + o];
+  } else {
+    double mn = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) mn += Ui[1 + k] * n[k];
+    UB[0] = Ui[0];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) UB[1 + k] = Ui[1 + k] - 2.0 * mn * n[k];
+    UB[DIM + 1] = Ui[DIM + 1];
+  }
+}
+
+// psi(t) = eps(U0 + t P) - s_min rho(t)^gamma (the entropy constraint of the set B_i, Sec. 5.4,
+// eq. (BiSet), times rho^gamma); concave in t.
+template <int DIM>
+__device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const double* P, double t, double smin) {
+  double V[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
+  if (!(V[0] > 0.0)) return -1.0;
+  return internal_energy<DIM>(V) - smin * pow(V[0], D.gamma);
+}
+
+template <int DIM>
+__device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const double* P, double t, double smin) {
+  double V[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
+  double rho = V[0], mP = 0.0, m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    mP += V[1 + k] * P[1 + k];
+    m2 += V[1 + k] * V[1 + k];
+  }
+  double deps = P[DIM + 1] - mP / rho + 0.5 * m2 * P[0] / (rho * rho);
+  return deps - smin * D.gamma * pow(rho, D.gamma - 1.0) * P[0];
+}
+
+// Largest l in [0, 1] with U0 + l P in B_i (Sec. 5.4, eq. (ConvexScheme), Lemma ConsInvariants):
+// closed form for the density bounds, then, if the entropy constraint fails at l_rho, a bracketed
+// iteration on the concave psi: the chord root stays feasible, the tangent root from the infeasible end
+// stays infeasible; stops when the bracket is at most ls_tol wide and returns the feasible end.
+template <int DIM>
+__device__ __forceinline__ double line_search(const Dev& D, const double* U0, const double* P, double rmin,
+                                              double rmax, double smin) {
+  double l = 1.0;
+  if (U0[0] + P[0] < rmin) l = (rmin - U0[0]) / P[0];
+  if (U0[0] + P[0] > rmax) l = (rmax - U0[0]) / P[0];
+  if (!(l > 0.0)) l = 0.0;
+  if (l > 1.0) l = 1.0;
+  double fb = ls_psi<DIM>(D, U0, P, l, smin);
+  if (fb >= 0.0) return l;
+  double fa = ls_psi<DIM>(D, U0, P, 0.0, smin);
+  if (fa < 0.0) return 0.0;
+  double a = 0.0, b = l;
+  for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {
+    bool moved = false;
+    double ts = a + (b - a) * fa / (fa - fb);
+    double dfb = ls_dpsi<DIM>(D, U0, P, b, smin);
+    double tn = dfb < 0.0 ? b - fb / dfb : b;
+    if (ts > a && ts < b) {
+      double fs = ls_psi<DIM>(D, U0, P, ts, smin);
+      if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; }
+      moved = true;
+    }
+    if (tn > a && tn < b) {
+      double fn = ls_psi<DIM>(D, U0, P, tn, smin);
+      if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
+      moved = true;
+    }
+    if (!moved) break;
+  }
+  return a;
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_state(const double* U, int n, int i, double* out) {
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) out[q] = U[(size_t)q * n + i];
+}
+
+}  // namespace gdg

@@ -1,0 +1,182 @@
+// Sweep B: high-order update with the consistent element mass, relaxed local bounds, antidiffusive
+// fluxes and the first convex-limiting pass.  One thread per node; a block holds whole elements so the
+// element solve and the m_ij coupling of A_ij stay in shared memory.
+#include "gdg_internal.cuh"
+
+namespace gdg {
+
+namespace {
+
+constexpr int kMaxBlock = 288;
+
+// Per node i of the block:
+//  1. d_ij^H = max(d^min, d^ev) (Sec. 5, eq. (HighOrderViscosity); Sec. 5.1, eq. (ViscMin); Sec. 5.2),
+//     the boundary d^{d,H} = max(c_k h_i^{p_k}, min(c_ev |N_i|, 1)) d^{d,L} (ghost node read as
+//     collocated with x_i), and the high-order right-hand side
+//       RHS^H_i = RHS^L_i - sum_j (d^H_ij - d^L_ij)(U_j - U_i) - sum_k (d^{d,H} - d^{d,L})(U^{d,k} - U_i);
+//  2. the element solve of Sec. 5, eq. (HighScheme): dU^H_K = -tau M_K^{-1} RHS^H_K;
+//  3. the relaxed bounds of Sec. 5.4, eq. (eq:local_bounds), from the one-hop aggregates of i and of
+//     its stencil neighbours and node i's own boundary bar states;
+//  4. A_ij = tau (d^H_ij - d^L_ij)(U_j - U_i) - m_ij (dU^H_j - dU^H_i) and
+//     A_i^{d,k} = tau (d^{d,H} - d^{d,L})(U^{d,k} - U_i) (Sec. 5.3, eq. (HighLowOrderIdentity)), and the
+//     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i).
+// With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
+template <int DIM>
+__global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const double* __restrict__ U,
+                                                    const double* __restrict__ bdata, double tau,
+                                                    const double* __restrict__ Ubase, double alpha,
+                                                    double* __restrict__ Uout, int nodes_per_block) {
+  constexpr int M = DIM + 2;
+  __shared__ double sR[M][kMaxBlock];
+  __shared__ double sdU[M][kMaxBlock];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * nodes_per_block + t;
+  const bool valid = t < nodes_per_block && i < D.n;
+  const size_t n = D.n;
+  double Ui[M], dUi[M];
+  double Ni = 0.0;
+  if (valid) {
+    load_state<DIM>(U, D.n, i, Ui);
+    Ni = fabs(S.N[i]);
+    double rhs[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) rhs[q] = S.RHSL[(size_t)q * n + i];
+    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+      double dl = S.dL[e];
+      if (D.cnorm[e] == 0.0) continue;
+      int j = D.col[e];
+      double Nj = fabs(S.N[j]);
+      double dev = dl * fmin(D.c_ev * fmax(Ni, Nj), 1.0);
+      double dh = fmax(D.mu[e] * dl, dev);
+      double dd = dh - dl;
+      S.ddiff[e] = dd;
+#pragma unroll
+      for (int q = 0; q < M; ++q) rhs[q] -= dd * (U[(size_t)q * n + j] - Ui[q]);
+    }
+    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+      double nv[DIM], UB[M];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
+      boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
+      double dl = S.dB[b];
+      double dd = (fmax(D.muB[i], fmin(D.c_ev * Ni, 1.0)) - 1.0) * dl;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        rhs[q] -= dd * (UB[q] - Ui[q]);
+        S.AB[(size_t)q * D.nb + b] = tau * dd * (UB[q] - Ui[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < M; ++q) sR[q][t] = rhs[q];
+  }
+  __syncthreads();
+  if (valid) {
+    const int nl = D.n_loc;
+    const int il = i % nl;
+    const int t0 = t - il;  // first node of the element in the block
+    const double* Minv = D.MKinv + ((size_t)(i / nl) * nl + il) * nl;
+    double acc[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) acc[q] = 0.0;
+    for (int l = 0; l < nl; ++l) {
+      double w = Minv[l];
+#pragma unroll
+      for (int q = 0; q < M; ++q) acc[q] += w * sR[q][t0 + l];
+    }
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      dUi[q] = -tau * acc[q];
+      sdU[q][t] = dUi[q];
+    }
+    if (D.order == GDG_ORDER_HIGH) {
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        double uh = Ui[q] + dUi[q];
+        Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * Ubase[(size_t)q * n + i] + (1.0 - alpha) * uh : uh;
+      }
+    }
+  }
+  if (D.order == GDG_ORDER_HIGH) return;
+  __syncthreads();
+  if (!valid) return;
+  // relaxed local bounds
+  double lo = S.agg[i], hi = S.agg[n + i], sl = S.agg[2 * n + i];
+  for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+    lo = fmin(lo, S.bbar[b]);
+    hi = fmax(hi, S.bbar[b]);
+    sl = fmin(sl, S.bbar[(size_t)D.nb + b]);
+  }
+  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+    if (D.cnorm[e] == 0.0) continue;
+    int j = D.col[e];
+    lo = fmin(lo, S.agg[j]);
+    hi = fmax(hi, S.agg[n + j]);
+    sl = fmin(sl, S.agg[2 * n + j]);
+  }
+  double rmin, rmax, smin;
+  if (D.bounds_mode == 0) {
+    rmin = D.rminus[i] * lo;
+    rmax = D.rplus[i] * hi;
+    smin = D.rminus[i] * sl;
+  } else {
+    rmin = 0.0;
+    rmax = INFINITY;
+    smin = 0.0;
+  }
+  S.bounds[i] = rmin;
+  S.bounds[n + i] = rmax;
+  S.bounds[2 * n + i] = smin;
+  // antidiffusive fluxes and pass-1 line search
+  double UL[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) UL[q] = S.UL[(size_t)q * n + i];
+  const double ikm = D.inv_km[i];
+  const int nl = D.n_loc;
+  const int elem = i / nl;
+  const int t0 = t - (i % nl);
+  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+    int j = D.col[e];
+    double A[M], Pv[M];
+    double vis = D.cnorm[e] != 0.0 ? tau * S.ddiff[e] : 0.0;
+    bool same = (j / nl) == elem;
+    double mij = same ? D.mij[e] : 0.0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      double a = vis != 0.0 ? vis * (U[(size_t)q * n + j] - Ui[q]) : 0.0;
+      if (same) a -= mij * (sdU[q][t0 + (j % nl)] - dUi[q]);
+      A[q] = a;
+      S.A[(size_t)q * D.nnz + e] = a;
+      Pv[q] = a * ikm;
+    }
+    S.l1[e] = line_search<DIM>(D, UL, Pv, rmin, rmax, smin);
+  }
+  for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+    double Pv[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) Pv[q] = S.AB[(size_t)q * D.nb + b] * ikm;
+    S.l1B[b] = line_search<DIM>(D, UL, Pv, rmin, rmax, smin);
+  }
+}
+
+template <int DIM>
+cudaError_t high_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
+                      const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
+  if (D.n == 0) return cudaSuccess;
+  int epb = kMaxBlock / D.n_loc;  // whole elements per block
+  if (epb < 1) return cudaErrorInvalidValue;
+  int npb = epb * D.n_loc;
+  int threads = (npb + 31) / 32 * 32;
+  if (threads > kMaxBlock) threads = kMaxBlock;
+  int blocks = (D.n + npb - 1) / npb;
+  k_high<DIM><<<blocks, threads, 0, s>>>(D, S, U, bdata, tau, Ubase, alpha, Uout, npb);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_high(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
+                        const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
+  GDG_DISPATCH(dim, high_impl, D, S, U, bdata, tau, Ubase, alpha, Uout, s);
+}
+
+}  // namespace gdg

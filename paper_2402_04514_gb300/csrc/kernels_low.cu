@@ -1,0 +1,279 @@
+// Low-order sweep: per-node primitives, the time-step reduction (Sec. 3.3, eq. (MaxCFLdt)) and the
+// first stage sweep (low-order update, entropy-viscosity indicator, one-hop bound aggregates).
+#include "gdg_internal.cuh"
+
+namespace gdg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Per-node primitives (Sec. 2.2): 1/rho, p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
+// f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
+// Flags a state outside the admissible set of eq. (AddSet).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_prim(Dev D, Scratch S, const double* __restrict__ U) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.n) return;
+  double Ui[DIM + 2];
+  load_state<DIM>(U, D.n, i, Ui);
+  double irho = 1.0 / Ui[0];
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += Ui[1 + k] * Ui[1 + k];
+  double eps = Ui[DIM + 1] - 0.5 * m2 * irho;
+  if (!(Ui[0] > 0.0) || !(eps > 0.0)) atomicOr(S.flags, (unsigned)GDG_FLAG_INADMISSIBLE);
+  double p = D.gm1 * eps;
+  double st = pow(Ui[0], -D.gamma) * eps;
+  double* P = S.prim;
+  size_t n = D.n;
+  P[PR_IRHO * n + i] = irho;
+  P[PR_P * n + i] = p;
+  P[PR_A * n + i] = sqrt(D.gamma * p * irho);
+  P[PR_PME * n + i] = pow(p, -D.e_exp);
+  P[PR_F * n + i] = pow(D.gm1 * st, D.inv_gp1);
+  P[PR_ST * n + i] = st;
+}
+
+// Sum over the row of d_ij^L plus the boundary viscosities, i.e. -d_ii of
+// eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const double* __restrict__ U,
+                                                    const double* __restrict__ bdata) {
+  constexpr int M = DIM + 2;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double val = INFINITY;
+  if (i < D.n) {
+    size_t n = D.n;
+    double Ui[M];
+    load_state<DIM>(U, D.n, i, Ui);
+    const double* P = S.prim;
+    double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], a_i = P[PR_A * n + i],
+           pme_i = P[PR_PME * n + i];
+    double dsum = 0.0;
+    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+      double cnm = D.cnorm[e];
+      if (cnm == 0.0) continue;
+      int j = D.col[e];
+      double nv[DIM], uL = 0.0, uR = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        nv[k] = D.cn[(size_t)k * D.nnz + e];
+        uL += Ui[1 + k] * nv[k];
+        uR += U[(size_t)(1 + k) * n + j] * nv[k];
+      }
+      uL *= irho_i;
+      uR *= P[PR_IRHO * n + j];
+      dsum += cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, P[PR_P * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
+    }
+    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+      double nv[DIM], UB[M];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
+      boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
+      double irB = 1.0 / UB[0];
+      double pB = D.gm1 * internal_energy<DIM>(UB);
+      double uL = 0.0, uR = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        uL += Ui[1 + k] * nv[k];
+        uR += UB[1 + k] * nv[k];
+      }
+      dsum += D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, a_i, pme_i, uR * irB, pB, sqrt(D.gamma * pB * irB),
+                                      pow(pB, -D.e_exp));
+    }
+    if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
+  }
+  // block minimum, then one atomic per block on the bit pattern (positive doubles order like uint64)
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    val = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : INFINITY;
+    for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+    if (threadIdx.x == 0 && val < INFINITY)
+      atomicMin(S.tau_bits, (unsigned long long)__double_as_longlong(val));
+  }
+}
+
+// Sweep A, one thread per row i:
+//  - d_ij^L = |c_ij| lambda_max^+(U_i, U_j, n_ij) (Sec. 3.1, eq. (eq:dij_low_order)), boundary states
+//    and viscosities (Sec. 4.1; Sec. 4.2, eq. (eq:dij_low_order_modified));
+//  - the low-order update of Sec. 4.2, eq. (cijdijschememodified), and the CFL check (CFLcond);
+//  - the entropy-viscosity indicator N_i = R_i / D_i (Sec. 5.2);
+//  - the one-hop aggregates of the local bounds (Sec. 5.4, eq. (eq:local_bounds)): min/max of rho_j,
+//    rho(Ubar_jk), rho_k and min of s~ over node j's stencil, with the bar states of
+//    eq. (UsualBarState); and rho, s~ of node i's boundary bar states (eq. (BoundaryBarState)).
+// With order LOW (or no limiter pass) it also writes U_out = alpha U_base + (1 - alpha) U^L.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double* __restrict__ U,
+                                                  const double* __restrict__ bdata, double tau,
+                                                  const double* __restrict__ Ubase, double alpha,
+                                                  double* __restrict__ Uout, int write_out) {
+  constexpr int M = DIM + 2;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.n) return;
+  size_t n = D.n;
+  const double* P = S.prim;
+  double Ui[M];
+  load_state<DIM>(U, D.n, i, Ui);
+  const double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], a_i = P[PR_A * n + i],
+               pme_i = P[PR_PME * n + i], f_i = P[PR_F * n + i], st_i = P[PR_ST * n + i];
+  double rhs[M], Fsum[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) rhs[q] = Fsum[q] = 0.0;
+  double psum = 0.0, dsum = 0.0;
+  double lo = Ui[0], hi = Ui[0], sl = st_i;
+  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+    double cnm = D.cnorm[e];
+    if (cnm == 0.0) continue;  // m_ij-only entry: not in I(i)
+    int j = D.col[e];
+    double Uj[M], nv[DIM];
+    load_state<DIM>(U, D.n, j, Uj);
+    double uL = 0.0, uR = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      nv[k] = D.cn[(size_t)k * D.nnz + e];
+      uL += Ui[1 + k] * nv[k];
+      uR += Uj[1 + k] * nv[k];
+    }
+    const double mnL = uL, mnR = uR;
+    uL *= irho_i;
+    const double irho_j = P[PR_IRHO * n + j], p_j = P[PR_P * n + j];
+    uR *= irho_j;
+    double d = cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, p_j, P[PR_A * n + j], P[PR_PME * n + j]);
+    S.dL[e] = d;
+    dsum += d;
+    double fi[M], fj[M];
+    flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
+    flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
+    double t = cnm / (2.0 * d);
+    double Ub[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      rhs[q] += cnm * fj[q] - d * (Uj[q] - Ui[q]);
+      Fsum[q] += cnm * fj[q];
+      Ub[q] = 0.5 * (Ui[q] + Uj[q]) - t * (fj[q] - fi[q]);
+    }
+    psum += cnm * fj[0] * (P[PR_F * n + j] - f_i);
+    double stb = pow(Ub[0], -D.gamma) * internal_energy<DIM>(Ub);
+    lo = fmin(lo, fmin(Uj[0], Ub[0]));
+    hi = fmax(hi, fmax(Uj[0], Ub[0]));
+    sl = fmin(sl, fmin(P[PR_ST * n + j], stb));
+  }
+  for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+    double nv[DIM], UB[M];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
+    boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
+    double irB = 1.0 / UB[0];
+    double pB = D.gm1 * internal_energy<DIM>(UB);
+    double uL = 0.0, uR = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      uL += Ui[1 + k] * nv[k];
+      uR += UB[1 + k] * nv[k];
+    }
+    const double mnL = uL, mnR = uR;
+    uL *= irho_i;
+    uR *= irB;
+    double cnm = D.bnorm[b];
+    double d = cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, pB, sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
+    S.dB[b] = d;
+    dsum += d;
+    double fi[M], fB[M];
+    flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
+    flux_n<DIM>(UB, nv, mnR, uR, pB, fB);
+    double t = cnm / (2.0 * d);
+    double Ub[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      rhs[q] += cnm * fB[q] - d * (UB[q] - Ui[q]);
+      Ub[q] = 0.5 * (Ui[q] + UB[q]) - t * (fB[q] - fi[q]);
+    }
+    S.bbar[b] = Ub[0];
+    S.bbar[(size_t)D.nb + b] = pow(Ub[0], -D.gamma) * internal_energy<DIM>(Ub);
+  }
+  const double inv_mi = D.inv_mi[i];
+  if (2.0 * tau * dsum * inv_mi > 1.0 + 1e-12) atomicOr(S.flags, (unsigned)GDG_FLAG_CFL);
+  double UL[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
+  if (write_out) {
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+      Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * Ubase[(size_t)q * n + i] + (1.0 - alpha) * UL[q] : UL[q];
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    S.UL[(size_t)q * n + i] = UL[q];
+    S.RHSL[(size_t)q * n + i] = rhs[q];
+  }
+  S.agg[i] = lo;
+  S.agg[n + i] = hi;
+  S.agg[2 * n + i] = sl;
+  // entropy-viscosity indicator: grad Phi_i = rho_i f'(s_i) grad_U s(U_i), f' = f / (gamma + 1),
+  // grad_U s = grad_U p / p - (gamma / rho) e_rho, grad_U p = (gamma - 1)[|v|^2 / 2, -v, 1]
+  double pref = f_i * D.inv_gp1 / irho_i;
+  double ip = 1.0 / p_i;
+  double v2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) v2 += (Ui[1 + k] * irho_i) * (Ui[1 + k] * irho_i);
+  double grad[M];
+  grad[0] = pref * (D.gm1 * 0.5 * v2 * ip - D.gamma * irho_i);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-D.gm1 * (Ui[1 + k] * irho_i) * ip);
+  grad[DIM + 1] = pref * (D.gm1 * ip);
+  double R = psum, Dn = fabs(psum);
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    R -= grad[q] * Fsum[q];
+    Dn += fabs(grad[q]) * fabs(Fsum[q]);
+  }
+  S.N[i] = Dn > 0.0 ? R / Dn : 0.0;
+}
+
+template <int DIM>
+cudaError_t prim_impl(const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
+  if (D.n == 0) return cudaSuccess;
+  k_prim<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U);
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t maxdt_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, cudaStream_t s) {
+  if (D.n == 0) return cudaSuccess;
+  k_maxdt<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U, bdata);
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t low_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
+                     const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
+  if (D.n == 0) return cudaSuccess;
+  int write_out = (D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0)) ? 1 : 0;
+  k_low<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U, bdata, tau, Ubase, alpha, Uout,
+                                                                  write_out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+
+cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
+  GDG_DISPATCH(dim, prim_impl, D, S, U, s);
+}
+
+cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
+                         cudaStream_t s) {
+  GDG_DISPATCH(dim, maxdt_impl, D, S, U, bdata, s);
+}
+
+cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
+                       const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
+  GDG_DISPATCH(dim, low_impl, D, S, U, bdata, tau, Ubase, alpha, Uout, s);
+}
+
+}  // namespace gdg

@@ -1,0 +1,240 @@
+"""Python binding of the gdg C ABI (include/gdg.h): argument marshalling only.
+
+Every computation of a stage runs in the CUDA kernels of libgdg.so; PyTorch provides device memory and
+streams.  There is no CPU fallback: if the library is missing or the GPU is absent, construction fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final")  # GDG_K_* order
+BC_SLIP, BC_DIRICHLET = 0, 1
+FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
+
+_CODES = {0: "GDG_OK", 1: "GDG_EINVAL", 2: "GDG_ENOMEM", 3: "GDG_ECUDA", 4: "GDG_ESETUP", 5: "GDG_EADMISSIBLE",
+          6: "GDG_ECFL", 7: "GDG_ETIMEOUT", 8: "GDG_ENOTSUP"}
+
+
+class GdgError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_CODES.get(code, code)}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("order", C.c_int32), ("limiter_passes", C.c_int32), ("bounds_mode", C.c_int32),
+                ("c_k", C.c_double), ("p_k", C.c_double), ("c_ev", C.c_double), ("c_r", C.c_double),
+                ("p_r", C.c_double), ("ls_tol", C.c_double), ("ls_maxit", C.c_int32)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("degree", C.c_int32), ("n_loc", C.c_int32),
+                ("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("cij", C.c_void_p), ("coloc", C.c_void_p),
+                ("mi", C.c_void_p), ("MK", C.c_void_p), ("b_node", C.c_void_p), ("b_c", C.c_void_p),
+                ("b_type", C.c_void_p), ("gamma", C.c_double), ("omega_measure", C.c_double),
+                ("params", Params)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64), ("dim", C.c_int32), ("n_loc", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libgdg.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libgdg.so not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_2402_04514_gb300.build")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.gdg_default_params.argtypes = [i32, C.POINTER(Params)]
+    L.gdg_setup.argtypes = [C.POINTER(_Problem), C.POINTER(vp)]
+    L.gdg_set_params.argtypes = [vp, C.POINTER(Params)]
+    L.gdg_max_dt.argtypes = [vp, vp, vp, d, C.POINTER(d), vp]
+    L.gdg_stage.argtypes = [vp, vp, vp, d, d, vp, vp, vp]
+    L.gdg_status.argtypes = [vp, C.POINTER(i32), i32, vp]
+    L.gdg_debug_export.argtypes = [vp, C.c_char_p, vp, i64, vp]
+    L.gdg_get_info.argtypes = [vp, C.POINTER(_Info)]
+    L.gdg_profile.argtypes = [vp, i32]
+    L.gdg_profile_read.argtypes = [vp, vp, vp]
+    L.gdg_destroy.argtypes = [vp]
+    L.gdg_error_string.argtypes = [C.c_int]
+    L.gdg_error_string.restype = C.c_char_p
+    for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_status", "gdg_debug_export",
+              "gdg_get_info", "gdg_profile", "gdg_profile_read"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(code, what):
+    if code != 0:
+        raise GdgError(code, what)
+
+
+def default_params(degree: int) -> dict:
+    p = Params()
+    load().gdg_default_params(degree, C.byref(p))
+    return {f: getattr(p, f) for f, _ in Params._fields_}
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """One mesh instance on the current CUDA device (a gdg handle)."""
+
+    def __init__(self, problem, gamma: float = 1.4, params: dict | None = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("gdg needs a CUDA device; there is no CPU fallback")
+        L = load()
+        P = problem
+        self.dim, self.m, self.n = P.dim, P.dim + 2, int(P.n)
+        self.nb = int(P.b_node.shape[0])
+        self.nnz = int(P.col_idx.shape[0])
+        self.gamma = gamma
+        self.has_dirichlet = bool((np.asarray(P.b_type) == BC_DIRICHLET).any())
+        prm = {**default_params(P.degree), **(params or {})}
+        keep = dict(row_ptr=np.ascontiguousarray(P.row_ptr, np.int64),
+                    col_idx=np.ascontiguousarray(P.col_idx, np.int32),
+                    cij=np.ascontiguousarray(P.cij, np.float64), coloc=np.ascontiguousarray(P.coloc, np.uint8),
+                    mi=np.ascontiguousarray(P.mi, np.float64), MK=np.ascontiguousarray(P.MK, np.float64),
+                    b_node=np.ascontiguousarray(P.b_node, np.int32), b_c=np.ascontiguousarray(P.b_c, np.float64),
+                    b_type=np.ascontiguousarray(P.b_type, np.int32))
+
+        def hp(a):
+            return a.ctypes.data if a.size else None
+
+        self._params = Params(**prm)
+        cp = _Problem(P.dim, P.degree, P.n_loc, self.n, self.nnz, self.nb, hp(keep["row_ptr"]), hp(keep["col_idx"]),
+                      hp(keep["cij"]), hp(keep["coloc"]), hp(keep["mi"]), hp(keep["MK"]), hp(keep["b_node"]),
+                      hp(keep["b_c"]), hp(keep["b_type"]), gamma, P.omega_measure, self._params)
+        h = C.c_void_p()
+        _check(L.gdg_setup(C.byref(cp), C.byref(h)), "gdg_setup")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @property
+    def params(self) -> dict:
+        return {f: getattr(self._params, f) for f, _ in Params._fields_}
+
+    def set_params(self, **kw):
+        p = Params(**{**self.params, **kw})
+        _check(load().gdg_set_params(self._h, C.byref(p)), "gdg_set_params")
+        self._params = p
+
+    def _bdata(self, bdata):
+        if bdata is None:
+            if self.has_dirichlet:
+                raise ValueError("Dirichlet boundary entries need bdata")
+            return None
+        assert bdata.is_cuda and bdata.dtype.itemsize == 8 and bdata.is_contiguous()
+        assert tuple(bdata.shape) == (self.m, self.nb)
+        return bdata
+
+    def _check_state(self, U):
+        assert U.is_cuda and U.is_contiguous() and tuple(U.shape) == (self.m, self.n), U.shape
+        import torch
+        assert U.dtype == torch.float64
+
+    def max_dt(self, U, cfl: float, bdata=None, stream=None) -> float:
+        self._check_state(U)
+        bd = self._bdata(bdata)
+        tau = C.c_double()
+        _check(load().gdg_max_dt(self._h, _ptr(U), _ptr(bd), cfl, C.byref(tau), _stream(stream)), "gdg_max_dt")
+        return tau.value
+
+    def stage(self, U_in, tau: float, U_base=None, alpha: float = 0.0, bdata=None, out=None, stream=None):
+        import torch
+
+        self._check_state(U_in)
+        if out is None:
+            out = torch.empty_like(U_in)
+        self._check_state(out)
+        if U_base is not None:
+            self._check_state(U_base)
+        bd = self._bdata(bdata)
+        _check(load().gdg_stage(self._h, _ptr(U_in), _ptr(U_base), alpha, tau, _ptr(bd), _ptr(out),
+                                _stream(stream)), "gdg_stage")
+        return out
+
+    def status(self, clear: bool = False, stream=None) -> int:
+        f = C.c_int32()
+        _check(load().gdg_status(self._h, C.byref(f), 1 if clear else 0, _stream(stream)), "gdg_status")
+        return f.value
+
+    def export(self, name: str, stream=None) -> np.ndarray:
+        m, n, nnz, nb = self.m, self.n, self.nnz, self.nb
+        shapes = dict(dL=(nnz,), dB=(nb,), N=(n,), UL=(m, n), U1=(m, n), A=(m, nnz), rho_min=(n,), rho_max=(n,),
+                      s_min=(n,), l1=(nnz,), l2=(nnz,))
+        out = np.empty(shapes[name])
+        _check(load().gdg_debug_export(self._h, name.encode(), out.ctypes.data if out.size else None, out.size,
+                                       _stream(stream)), f"gdg_debug_export({name})")
+        return out
+
+    def profile(self, enable: bool):
+        """Bracket every kernel launch with CUDA events (on the launching stream) until disabled."""
+        _check(load().gdg_profile(self._h, 1 if enable else 0), "gdg_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel: (total_ms, launches)} accumulated since the last read; synchronises."""
+        ms = np.zeros(len(KERNELS))
+        cnt = np.zeros(len(KERNELS), np.int64)
+        _check(load().gdg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data), "gdg_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+    def info(self) -> dict:
+        i = _Info()
+        _check(load().gdg_get_info(self._h, C.byref(i)), "gdg_get_info")
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def ssprk3_step(self, U, tau: float, bufs, out, bdata_fn=None, t: float = 0.0, stream=None):
+        """Shu-Osher SSPRK3 step from U into out, with two scratch states bufs = (U1, U2).
+        bdata_fn(time) returns the Dirichlet data (device [m][nb]) at a stage time."""
+        bd = (lambda s: None) if bdata_fn is None else bdata_fn
+        U1, U2 = bufs
+        self.stage(U, tau, bdata=bd(t), out=U1, stream=stream)
+        self.stage(U1, tau, U_base=U, alpha=0.75, bdata=bd(t + tau), out=U2, stream=stream)
+        self.stage(U2, tau, U_base=U, alpha=1.0 / 3.0, bdata=bd(t + 0.5 * tau), out=out, stream=stream)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

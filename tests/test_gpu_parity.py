@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerance: per component, max |U_gpu - U_oracle| / max |U_oracle| <= 1e-12 after one stage and <= 1e-10
+after 100 SSP-RK3 steps; invariant-domain checks (rho > 0, eps > 0, local bounds) hold exactly.
+Sizes span several thread blocks with a ragged tail (blocks of 256 nodes, 288 for the element sweep)."""
+import numpy as np
+import pytest
+
+from paper_2402_04514_gb300 import assembly, workloads
+from tests.helpers import dirichlet_vortex_problem, four_quadrant_problem, periodic_vortex_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+STAGE_TOL = 1e-12
+LONG_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_04514_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _pair(P, gamma=1.4, params=None):
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Solver
+
+    return Solver(P, gamma=gamma, params=params), Oracle(P, gamma=gamma, params=dict(params or {}))
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+CASES = [
+    ("sod1d_q1", lambda: (assembly.assemble_1d(200, 1), None)),
+    ("sod1d_q2_ragged", lambda: (assembly.assemble_1d(333, 2), None)),
+    ("vortex_q1_periodic", lambda: periodic_vortex_problem(17, 1)),
+    ("fq_q2_slip", lambda: four_quadrant_problem(13, 2, seed=0)),
+    ("fq_q1_slip", lambda: four_quadrant_problem(19, 1, seed=4)),
+    ("fq_q3_slip", lambda: four_quadrant_problem(7, 3, seed=2)),
+]
+
+
+def _problem(name):
+    P, U = dict(CASES)[name]()
+    if U is None:
+        U = workloads.sod(P.x[0])
+    return P, U
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("order,passes", [(0, 2), (1, 2), (2, 0), (2, 1), (2, 2)])
+def test_stage_parity(torch_cuda, name, order, passes):
+    torch = torch_cuda
+    P, U = _problem(name)
+    prm = dict(order=order, limiter_passes=passes)
+    S, O = _pair(P, params=prm)
+    Ud = _dev(torch, U)
+    tau_g = S.max_dt(Ud, 0.5)
+    tau_o = O.max_dt(U, 0.5)
+    assert abs(tau_g - tau_o) <= 1e-13 * tau_o
+    for alpha, base in ((0.0, None), (0.75, U * 1.01)):
+        out = S.stage(Ud, tau_o, U_base=None if base is None else _dev(torch, base), alpha=alpha)
+        ref, flags = O.stage(U, tau_o, U_base=base, alpha=alpha)
+        torch.cuda.synchronize()
+        assert rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
+        assert S.status() == flags == 0
+
+
+@pytest.mark.parametrize("name", ["fq_q2_slip", "fq_q1_slip", "vortex_q1_periodic"])
+def test_intermediates_parity(torch_cuda, name):
+    """d_ij^L, N_i, U^L, the bounds, A_ij, l (both passes) and U^(1) agree with the oracle's trace."""
+    torch = torch_cuda
+    P, U = _problem(name)
+    S, O = _pair(P)
+    tau = O.max_dt(U, 0.5)
+    S.stage(_dev(torch, U), tau)
+    _, _, tr = O.stage(U, tau, trace=True)
+    assert rel_err(S.export("dL"), tr["dL"]) <= 1e-13
+    if P.nb:
+        assert rel_err(S.export("dB"), tr["dB"]) <= 1e-13
+    assert np.abs(S.export("N") - tr["N"]).max() <= 1e-9
+    assert rel_err(S.export("UL"), tr["UL"]) <= STAGE_TOL
+    for k in ("rho_min", "rho_max", "s_min"):
+        assert rel_err(S.export(k), tr[k]) <= 1e-13
+    assert rel_err(S.export("A"), tr["A"]) <= 1e-11
+    for k in ("l1", "l2"):
+        assert np.abs(S.export(k) - tr[k]).max() <= 1e-9
+    assert rel_err(S.export("U1"), tr["U1"]) <= STAGE_TOL
+
+
+def test_dirichlet_q3_and_bounds_off(torch_cuda):
+    torch = torch_cuda
+    P, U, bdata = dirichlet_vortex_problem(6, 3)
+    g = 5.0 / 3.0
+    for prm in (dict(), dict(bounds_mode=1)):
+        S, O = _pair(P, gamma=g, params=prm)
+        bd = bdata(0.0)
+        tau = O.max_dt(U, 0.5, bdata=bd)
+        assert abs(S.max_dt(_dev(torch, U), 0.5, bdata=_dev(torch, bd)) - tau) <= 1e-13 * tau
+        out = S.stage(_dev(torch, U), tau, bdata=_dev(torch, bd))
+        ref, _ = O.stage(U, tau, bdata=bd)
+        assert rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
+
+
+@pytest.mark.parametrize("name", ["sod1d_q1", "fq_q1_slip"])
+def test_hundred_steps(torch_cuda, name):
+    """100 SSP-RK3 steps of the limited scheme (tau from max_dt each step): <= 1e-10."""
+    torch = torch_cuda
+    P, U = _problem(name)
+    if name == "fq_q1_slip":
+        P, U = four_quadrant_problem(8, 1, seed=4)
+    S, O = _pair(P)
+    Ud = _dev(torch, U)
+    bufs = (torch.empty_like(Ud), torch.empty_like(Ud))
+    out = torch.empty_like(Ud)
+    Uo = U.copy()
+    for _ in range(100):
+        tau = O.max_dt(Uo, 0.5)
+        Uo, flags = O.ssprk3_step(Uo, tau)
+        S.ssprk3_step(Ud, tau, bufs, out)
+        Ud, out = out, Ud
+    got = Ud.cpu().numpy()
+    assert rel_err(got, Uo) <= LONG_TOL
+    rho = got[0]
+    eps = got[-1] - 0.5 * (got[1:-1] ** 2).sum(0) / rho
+    assert (rho > 0).all() and (eps > 0).all()
+    assert S.status() == 0
+
+
+def test_edge_cases(torch_cuda):
+    """One element; an empty mesh; a stage with tau = 0 (identity); a CFL violation is flagged."""
+    torch = torch_cuda
+    P = assembly.assemble_2d(1, 1, 2)
+    U = workloads.four_quadrant(P.x[0], P.x[1], seed=1)
+    S, O = _pair(P)
+    tau = O.max_dt(U, 0.5)
+    out = S.stage(_dev(torch, U), tau)
+    ref, _ = O.stage(U, tau)
+    assert rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
+    out0 = S.stage(_dev(torch, U), 0.0)
+    assert rel_err(out0.cpu().numpy(), U) <= 1e-15
+    S.stage(_dev(torch, U), 3.0 * tau / 0.5)
+    assert S.status(clear=True) & 2
+    assert S.status() == 0
+    E = assembly.assemble_2d(0, 0, 1) if False else None
+    from paper_2402_04514_gb300.assembly import Problem
+    Pe = Problem(dim=2, degree=1, n=0, n_loc=4, row_ptr=np.zeros(1, np.int64), col_idx=np.zeros(0, np.int32),
+                 cij=np.zeros((2, 0)), coloc=np.zeros(0, np.uint8), mi=np.zeros(0), MK=np.zeros((0, 4, 4)),
+                 b_node=np.zeros(0, np.int32), b_c=np.zeros((2, 0)), b_type=np.zeros(0, np.int32),
+                 b_part=np.zeros(0, np.int32), omega_measure=1.0, x=np.zeros((2, 0)))
+    from paper_2402_04514_gb300.gdg import Solver
+    Se = Solver(Pe)
+    Ue = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
+    assert Se.max_dt(Ue, 0.5) == float("inf")
+    Se.stage(Ue, 0.1)
+
+
+def test_inadmissible_input_is_flagged(torch_cuda):
+    torch = torch_cuda
+    P, U = four_quadrant_problem(4, 1)
+    U = U.copy()
+    U[3, 7] = 0.5 * (U[1, 7] ** 2 + U[2, 7] ** 2) / U[0, 7] - 1e-3  # eps < 0
+    S, _ = _pair(P)
+    S.stage(_dev(torch, U), 1e-4)
+    assert S.status() & 1
+
+
+def _patch_problem(nx_full, k, ex0, ex1, ey0, ey1):
+    h = 1.0 / nx_full
+    return assembly.assemble_2d(ex1 - ex0, ey1 - ey0, k, box=(ex0 * h, ex1 * h, ey0 * h, ey1 * h))
+
+
+def test_full_size_bench_configuration_sampled(torch_cuda):
+    """The bench workload (Q2 on 1024^2 quads of [0,1]^2, 9.4M nodes, four-quadrant data, slip walls), one
+    stage at full size in the bench's launch configuration.  Sampled elements are checked against the
+    oracle run on a 15 x 15-element patch around each of them (the stage's dependency radius is below 6
+    elements; interior c_ij, m_i, M_K and |Omega| are those of the full mesh); conservation of rho and E
+    and the local bounds are checked everywhere."""
+    torch = torch_cuda
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Solver
+
+    N, k = 1024, 2
+    P = assembly.assemble_2d(N, N, k)
+    U = workloads.four_quadrant(P.x[0], P.x[1], seed=0)
+    S = Solver(P)
+    Ud = _dev(torch, U)
+    tau = S.max_dt(Ud, 0.5)
+    out = S.stage(Ud, tau).cpu().numpy()
+    assert S.status() == 0
+    tot0, tot1 = (P.mi * U).sum(1), (P.mi * out).sum(1)
+    for c in (0, 3):
+        assert abs(tot1[c] - tot0[c]) <= 1e-12 * abs(tot0[c])
+    rmin, rmax, smin = S.export("rho_min"), S.export("rho_max"), S.export("s_min")
+    rho = out[0]
+    st = rho ** (-1.4) * (out[3] - 0.5 * (out[1] ** 2 + out[2] ** 2) / rho)
+    assert (rho >= rmin * (1 - 1e-13)).all() and (rho <= rmax * (1 + 1e-13)).all()
+    assert (st >= smin * (1 - 1e-12)).all()
+    rng = np.random.default_rng(7)
+    samples = [(512, 512), (511, 511), (0, 0), (1023, 1023), (0, 700), (300, 1023)]
+    samples += [tuple(rng.integers(0, N, 2)) for _ in range(4)]
+    R = 7
+    nl = (k + 1) ** 2
+    for ex, ey in samples:
+        ex0, ex1 = max(0, ex - R), min(N, ex + R + 1)
+        ey0, ey1 = max(0, ey - R), min(N, ey + R + 1)
+        Pp = _patch_problem(N, k, ex0, ex1, ey0, ey1)
+        Pp.omega_measure = P.omega_measure
+        Up = workloads.four_quadrant(Pp.x[0], Pp.x[1], seed=0)
+        O = Oracle(Pp)
+        ref, _ = O.stage(Up, tau)
+        le = (ey - ey0) * (ex1 - ex0) + (ex - ex0)
+        ge = ey * N + ex
+        got = out[:, ge * nl:(ge + 1) * nl]
+        want = ref[:, le * nl:(le + 1) * nl]
+        scale = np.abs(U).max(1, keepdims=True)
+        assert (np.abs(got - want) <= STAGE_TOL * scale).all(), (ex, ey)
