@@ -1,0 +1,84 @@
+"""The pins catch plausible mistakes: each mutant below is a copy of oracle.c with one planted error (a
+dropped term, a flipped sign, a swapped operand or index), compiled on the CPU; the pins of
+test_oracle_pins.py must reject every mutant.  The real oracle is untouched."""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+from oracle import oracle as om
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(om.__file__), "oracle.c")
+
+MUTANTS = {
+    "drop_boundary_viscosity": ("for (int q = 0; q < m; ++q) acc[q] += fv[q] - dB[b] * (Ub[q] - Ui[q]);",
+                                "for (int q = 0; q < m; ++q) acc[q] += fv[q];"),
+    "viscosity_sign": ("acc[q] += fv[q] - dL[e] * (Uj[q] - Ui[q]);", "acc[q] += fv[q] + dL[e] * (Uj[q] - Ui[q]);"),
+    "lambda_swapped_velocities": ("double num = aL + aR - 0.5 * (g - 1.0) * (uR - uL);",
+                                  "double num = aL + aR - 0.5 * (g - 1.0) * (uL - uR);"),
+    "bar_state_sign": ("out[q] = 0.5 * (Ui[q] + Uj[q]) - cn / (2.0 * dij) * (fj[q] - fi[q]);",
+                       "out[q] = 0.5 * (Ui[q] + Uj[q]) + cn / (2.0 * dij) * (fj[q] - fi[q]);"),
+    "mass_term_sign": ("-\n                           mij * (dUH[q * n + j] - dUH[q * n + i]);",
+                       "+\n                           mij * (dUH[q * n + j] - dUH[q * n + i]);"),
+    "limiter_max_instead_of_min": ("lsym[e] = fmin(lraw[e], lraw[transpose_entry(P, i, P->col_idx[e])]);",
+                                   "lsym[e] = fmax(lraw[e], lraw[transpose_entry(P, i, P->col_idx[e])]);"),
+    "line_search_returns_infeasible_end": ("    if (!moved) break;\n  }\n  return a;", "    if (!moved) break;\n  }\n  return b;"),
+    "relaxation_swapped": ("rmin[i] = rm * lo; rmax[i] = rp * hi; smin[i] = rm * sl;",
+                           "rmin[i] = rp * lo; rmax[i] = rm * hi; smin[i] = rm * sl;"),
+    "slip_half_reflection": ("UB[1 + k] = Ui[1 + k] - 2.0 * mn * nrm[k];", "UB[1 + k] = Ui[1 + k] - mn * nrm[k];"),
+    "cfl_factor_dropped": ("if (dii[i] < 0.0) t = fmin(t, -P->mi[i] / (2.0 * dii[i]));",
+                           "if (dii[i] < 0.0) t = fmin(t, -P->mi[i] / dii[i]);"),
+    # solve with the lumped mass instead of the consistent element mass M_K
+    "consistent_mass_dropped": ("element_solve(P->MK + K * nl * nl, nl, m, Bblk);",
+                                "for (int a = 0; a < nl; ++a) for (int q = 0; q < m; ++q) Bblk[a * m + q] /= "
+                                "P->mi[K * nl + a];"),
+    "ev_uses_only_own_residual": ("fmin(P->c_ev * fmax(fabs(N[i]), fabs(N[j])), 1.0);",
+                                  "fmin(P->c_ev * fabs(N[i]), 1.0);"),
+    "entropy_gradient_sign": ("grad[d + 1] = pref * ((g - 1.0) / pi);", "grad[d + 1] = -pref * ((g - 1.0) / pi);"),
+    "bounds_skip_bar_states": ("lo = fmin(lo, fmin(Uk[0], Ubk[0]));", "lo = fmin(lo, Uk[0]);"),
+}
+
+FAST_PINS = [
+    lambda O: pins.test_lambda_max_bounds_exact_wave_speed(O, 1.4),
+    lambda O: pins.test_lambda_max_symmetry(O),
+    lambda O: pins.test_constant_state_preserved(O),
+    lambda O: pins.test_convex_reformulation(O, 2),
+    lambda O: pins.test_low_order_invariants(O, 2),
+    lambda O: [pins.test_conservation(O, order, 2) for order in (0, 1, 2)],
+    lambda O: pins.test_high_low_identity_and_limiter_knobs(O, 2),
+    lambda O: pins.test_limiter_is_identity_when_bounds_are_loose(O),
+    lambda O: pins.test_limited_state_within_local_bounds(O, 2, 4.0),
+    lambda O: pins.test_limited_state_within_local_bounds(O, 2, 0.0),
+    lambda O: pins.test_sod_exact_solution(O),
+]
+
+
+def _vortex_q1_limited(O):
+    tab = pins.load_vortex_tables()
+    e1 = pins._vortex_error(O, 24, 1, O.LIMITED)
+    assert abs(e1 / tab["limited"][1][0] - 1.0) < 0.2, e1
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, monkeypatch):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "oracle.c")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.check_call(["cp", os.path.join(os.path.dirname(SRC), "oracle.h"), d])
+        so = os.path.join(d, "liboracle_mutant.so")
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", c, "-o", so, "-lm"])
+        monkeypatch.setattr(om, "_lib", None)
+        monkeypatch.setattr(om, "build", lambda force=False: so)
+        caught = []
+        for pin in FAST_PINS + [_vortex_q1_limited]:
+            try:
+                pin(om)
+            except (AssertionError, ValueError, FloatingPointError):
+                caught.append(pin)
+                break
+        assert caught, f"no pin rejects mutant {name}"

@@ -70,10 +70,10 @@ def test_constant_state_preserved(oracle_mod):
             assert rel_err(U1, U) < 1e-14
 
 
-def _fq(order, k=2, ne=4, seed=3, passes=2, bounds_mode=0):
+def _fq(order, k=2, ne=4, seed=3, passes=2, bounds_mode=0, **extra):
     from oracle import oracle as om
     P, U = four_quadrant_problem(ne, k, seed=seed)
-    O = om.Oracle(P, params=dict(order=order, limiter_passes=passes, bounds_mode=bounds_mode))
+    O = om.Oracle(P, params=dict(order=order, limiter_passes=passes, bounds_mode=bounds_mode, **extra))
     tau = O.max_dt(U, 0.5)
     U1, flags, tr = O.stage(U, tau, trace=True)
     return P, U, tau, U1, flags, tr
@@ -183,13 +183,16 @@ def test_limiter_is_identity_when_bounds_are_loose(oracle_mod):
     assert rel_err(U1, tr["UH"]) < 1e-14
 
 
+@pytest.mark.parametrize("c_r", [4.0, 0.0])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_limited_state_within_local_bounds(oracle_mod, k):
+def test_limited_state_within_local_bounds(oracle_mod, k, c_r):
     """Sec. 5.4: the final state lies in B_i (eq. (BiSet)): rho_min <= rho <= rho_max, s~ >= s~_min,
-    for the pass-1 and the final states; and the bounds contain U^L (convex combination of bar states)."""
+    for the pass-1 and the final states; and the bounds contain U^L, also unrelaxed (c_r = 0): U^L is a
+    convex combination of U_i and bar states (eq. (ConvexRef)), which is why eq. (eq:local_bounds) is
+    built from bar states."""
     g = 1.4
     for seed in (0, 5):
-        P, U, tau, U1, flags, tr = _fq(oracle_mod.LIMITED, k=k, seed=seed)
+        P, U, tau, U1, flags, tr = _fq(oracle_mod.LIMITED, k=k, seed=seed, c_r=c_r)
         for V in (tr["U1"], U1, tr["UL"]):
             rho = V[0]
             eps = V[-1] - 0.5 * (V[1:-1] ** 2).sum(0) / rho
