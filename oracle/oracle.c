@@ -206,7 +206,8 @@ static double dpsi(const double* U0, const double* Pv, double t, int d, double g
  * B_i.  The paper does not state the line search; the reading taken: the density constraints give l
  * in closed form; for the entropy constraint, keep l_rho if psi(l_rho) >= 0, otherwise bracket the
  * root of psi in [0, l_rho] and iterate with the chord (feasible, psi being concave) and the tangent
- * from the infeasible end (infeasible) until the bracket is at most tol wide; return the feasible end. */
+ * from the infeasible end (infeasible) until the bracket is at most tol wide; when rounding keeps both
+ * points from moving strictly inside the bracket, bisect instead; return the feasible end. */
 static double line_search(const double* U0, const double* Pv, double rmin, double rmax, double smin,
                           int d, double g, double tol, int maxit) {
   double l = 1.0;
@@ -234,7 +235,12 @@ static double line_search(const double* U0, const double* Pv, double rmin, doubl
       if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
       moved = 1;
     }
-    if (!moved) break;
+    if (!moved) {
+      double tm = a + 0.5 * (b - a);
+      if (!(tm > a && tm < b)) break;
+      double fm = psi(U0, Pv, tm, d, g, smin);
+      if (fm >= 0.0) { a = tm; fa = fm; } else { b = tm; fb = fm; }
+    }
   }
   return a;
 }
@@ -359,7 +365,10 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
      * at U_i, grad Phi_i = rho_i f'(s_i) grad_U s(U_i); the free index j in D_i is read as
      *   D_i = |sum_j psi_i(U_j).c_ij| + sum_k |[grad Phi_i]_k| |sum_j f_k(U_j) c_ij|
      * with the shifted entropy flux psi_i(U) = m (f(U) - f(U_i)), so |R_i| <= D_i; N_i = 0 when
-     * D_i = 0; the sums run over I(i) (no boundary terms). */
+     * D_i = 0; the sums run over I(i) (no boundary terms).  The flux sums sum_j f_k(U_j) c_ij are
+     * evaluated as sum_j (f_k(U_j) - f_k(U_i)) c_ij - f_k(U_i) sum_k c_i^{d,k}, equal by the partition
+     * of unity (Lemma LemPart): a node whose stencil holds a single state then gets R_i = D_i = 0
+     * exactly instead of a ratio of rounding errors. */
     for (long i = 0; i < n; ++i) {
       gather(Uin, n, i, m, Ui);
       double pi = pressure(Ui, d, g);
@@ -372,14 +381,20 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
       grad[0] = pref * ((g - 1.0) * 0.5 * v2 / pi - g / Ui[0]);
       for (int k = 0; k < d; ++k) grad[1 + k] = pref * (-(g - 1.0) * (Ui[1 + k] / Ui[0]) / pi);
       grad[d + 1] = pref * ((g - 1.0) / pi);
-      double Fsum[MAXM] = {0}, psum = 0.0;
+      double Fsum[MAXM] = {0}, psum = 0.0, fiv[MAXM];
       for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) {
         if (entry_c(P, e, c, nrm) == 0.0) continue;
         gather(Uin, n, P->col_idx[e], m, Uj);
         double fj = exp(log(pow(Uj[0], -g) * pressure(Uj, d, g)) / (g + 1.0));
         flux_dot(Uj, c, d, g, fv);
-        for (int q = 0; q < m; ++q) Fsum[q] += fv[q];
+        flux_dot(Ui, c, d, g, fiv);
+        for (int q = 0; q < m; ++q) Fsum[q] += fv[q] - fiv[q];
         psum += dot(Uj + 1, c, d) * (fj - fi);
+      }
+      for (long t = bptr[i]; t < bptr[i + 1]; ++t) {
+        for (int k = 0; k < d; ++k) c[k] = P->b_c[k * nb + bidx[t]];
+        flux_dot(Ui, c, d, g, fiv);
+        for (int q = 0; q < m; ++q) Fsum[q] -= fiv[q];
       }
       double R = psum, D = fabs(psum);
       for (int q = 0; q < m; ++q) {

@@ -195,7 +195,8 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
 // Largest l in [0, 1] with U0 + l P in B_i (Sec. 5.4, eq. (ConvexScheme), Lemma ConsInvariants):
 // closed form for the density bounds, then, if the entropy constraint fails at l_rho, a bracketed
 // iteration on the concave psi: the chord root stays feasible, the tangent root from the infeasible end
-// stays infeasible; stops when the bracket is at most ls_tol wide and returns the feasible end.
+// stays infeasible (bisection when rounding keeps both from moving); stops when the bracket is at most
+// ls_tol wide and returns the feasible end.
 template <int DIM>
 __device__ __forceinline__ double line_search(const Dev& D, const double* U0, const double* P, double rmin,
                                               double rmax, double smin) {
@@ -224,7 +225,12 @@ __device__ __forceinline__ double line_search(const Dev& D, const double* U0, co
       if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
       moved = true;
     }
-    if (!moved) break;
+    if (!moved) {  // rounding pinned both points to the bracket ends: bisect
+      double tm = a + 0.5 * (b - a);
+      if (!(tm > a && tm < b)) break;
+      double fm = ls_psi<DIM>(D, U0, P, tm, smin);
+      if (fm >= 0.0) { a = tm; fa = fm; } else { b = tm; fb = fm; }
+    }
   }
   return a;
 }

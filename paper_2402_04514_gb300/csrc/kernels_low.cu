@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
 #pragma unroll
     for (int q = 0; q < M; ++q) {
       rhs[q] += cnm * fj[q] - d * (Uj[q] - Ui[q]);
-      Fsum[q] += cnm * fj[q];
+      Fsum[q] += cnm * (fj[q] - fi[q]);
       Ub[q] = 0.5 * (Ui[q] + Uj[q]) - t * (fj[q] - fi[q]);
     }
     psum += cnm * fj[0] * (P[PR_F * n + j] - f_i);
@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
 #pragma unroll
     for (int q = 0; q < M; ++q) {
       rhs[q] += cnm * fB[q] - d * (UB[q] - Ui[q]);
+      Fsum[q] -= cnm * fi[q];
       Ub[q] = 0.5 * (Ui[q] + UB[q]) - t * (fB[q] - fi[q]);
     }
     S.bbar[b] = Ub[0];
@@ -214,7 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
   S.agg[i] = lo;
   S.agg[n + i] = hi;
   S.agg[2 * n + i] = sl;
-  // entropy-viscosity indicator: grad Phi_i = rho_i f'(s_i) grad_U s(U_i), f' = f / (gamma + 1),
+  // entropy-viscosity indicator: Fsum_k = sum_j (f_k(U_j) - f_k(U_i)) c_ij - f_k(U_i) sum_k c_i^{d,k}, which
+  // equals sum_j f_k(U_j) c_ij by the partition of unity (Lemma LemPart) and vanishes exactly on a
+  // stencil holding one state; grad Phi_i = rho_i f'(s_i) grad_U s(U_i), f' = f / (gamma + 1),
   // grad_U s = grad_U p / p - (gamma / rho) e_rho, grad_U p = (gamma - 1)[|v|^2 / 2, -v, 1]
   double pref = f_i * D.inv_gp1 / irho_i;
   double ip = 1.0 / p_i;

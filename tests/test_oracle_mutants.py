@@ -24,7 +24,8 @@ MUTANTS = {
                        "+\n                           mij * (dUH[q * n + j] - dUH[q * n + i]);"),
     "limiter_max_instead_of_min": ("lsym[e] = fmin(lraw[e], lraw[transpose_entry(P, i, P->col_idx[e])]);",
                                    "lsym[e] = fmax(lraw[e], lraw[transpose_entry(P, i, P->col_idx[e])]);"),
-    "line_search_returns_infeasible_end": ("    if (!moved) break;\n  }\n  return a;", "    if (!moved) break;\n  }\n  return b;"),
+    "line_search_ignores_entropy": ("  double fb = psi(U0, Pv, l, d, g, smin);\n  if (fb >= 0.0) return l;",
+                                    "  double fb = psi(U0, Pv, l, d, g, smin);\n  return l;"),
     "relaxation_swapped": ("rmin[i] = rm * lo; rmax[i] = rp * hi; smin[i] = rm * sl;",
                            "rmin[i] = rp * lo; rmax[i] = rm * hi; smin[i] = rm * sl;"),
     "slip_half_reflection": ("UB[1 + k] = Ui[1 + k] - 2.0 * mn * nrm[k];", "UB[1 + k] = Ui[1 + k] - mn * nrm[k];"),
