@@ -141,7 +141,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-steps", type=int, default=2)
+    ap.add_argument("--fp64-rates", action="store_true", help="print the measured arithmetic rates and exit")
     args = ap.parse_args()
+    if args.fp64_rates:
+        import torch
+
+        from paper_2402_04514_gb300.gdg import fp64_throughput
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"fp64_rates_ops_per_s": fp64_throughput()}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 

@@ -150,6 +150,19 @@ enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIM
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 
+/* Self-test of the FP64 helpers that replace CUDA's division and power on the sweep's hot loops:
+ * fn 0 = reciprocal by Newton-Raphson from an FP32 seed, 1 = x^{-1/q} by Newton-Raphson from an FP32
+ * seed, 2 = CUDA's 1.0 / x, 3 = CUDA's pow(x, -1.0 / q); x, y: device [n]; 1 <= q <= 16.  Asynchronous
+ * on stream.  The tests compare 0 with 2 and 1 with 3 in ulps. */
+int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream);
+
+/* Measured throughput (operations per second over the GPU, timed with CUDA events) of the arithmetic
+ * the sweep is made of: op 0 = FP64 FMA, 1 = FP64 division, 2 = FP64 sqrt, 3 = FP64 pow, 4 = FP32 FMA,
+ * 5 = this library's FP64 reciprocal, 6 = this library's x^{-1/5}, 7 = an FP64 -> FP32 -> FP64
+ * conversion pair.  Allocates and frees a scratch
+ * buffer; synchronises the stream.  Used for the FP64 roofline of the measurement script. */
+int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
+
 int gdg_get_info(gdg_handle* h, gdg_info* out);
 void gdg_destroy(gdg_handle* h);
 const char* gdg_error_string(int code);

@@ -232,7 +232,7 @@ const char* gdg_error_string(int code) {
 int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   if (!out) return GDG_EINVAL;
   *out = nullptr;
-  if (!P || !P->row_ptr || !P->mi || !P->MK) return GDG_EINVAL;
+  if (!P || !P->row_ptr || (P->n > 0 && (!P->mi || !P->MK))) return GDG_EINVAL;
   if (P->nnz > 0 && (!P->col_idx || !P->cij || !P->coloc)) return GDG_EINVAL;
   if (P->nb > 0 && (!P->b_node || !P->b_c || !P->b_type)) return GDG_EINVAL;
   if (P->dim < 1 || P->dim > 3) return GDG_ENOTSUP;
@@ -492,6 +492,15 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   double r = std::round(D.inv_e);
   D.ie = (std::fabs(D.inv_e - r) < 1e-12 * D.inv_e && r >= 1 && r <= 64) ? (int)r : 0;
   D.k13 = (P->gamma + 1.0) / (2.0 * P->gamma);
+  D.gp = D.gq = 0;
+  for (int q = 1; q <= 8 && D.gq == 0; ++q) {
+    double pg = std::round(P->gamma * q);
+    if (std::fabs(P->gamma * q - pg) < 1e-12 * pg && pg <= 64) {
+      D.gp = (int)pg;
+      D.gq = q;
+    }
+  }
+  D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
   D.inv_gp1 = 1.0 / (P->gamma + 1.0);
   h->d_mu = (double*)ptr(o_mu);
   h->d_rminus = (double*)ptr(o_rm);
@@ -533,7 +542,7 @@ int gdg_set_params(gdg_handle* h, const gdg_params* params) {
 }
 
 int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out, void* stream) {
-  if (!h || !U || !tau_out || !(cfl > 0)) return GDG_EINVAL;
+  if (!h || (!U && h->n > 0) || !tau_out || !(cfl > 0)) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
@@ -555,9 +564,9 @@ int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, 
 
 int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double alpha, double tau,
               const double* bdata, double* U_out, void* stream) {
-  if (!h || !U_in || !U_out || !(tau >= 0) || !std::isfinite(tau)) return GDG_EINVAL;
-  if (U_out == U_in || (U_base && U_out == U_base)) return GDG_EINVAL;
-  if (alpha != 0.0 && !U_base) return GDG_EINVAL;
+  if (!h || ((!U_in || !U_out) && h->n > 0) || !(tau >= 0) || !std::isfinite(tau)) return GDG_EINVAL;
+  if (h->n > 0 && (U_out == U_in || (U_base && U_out == U_base))) return GDG_EINVAL;
+  if (alpha != 0.0 && !U_base && h->n > 0) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int dim = h->dim;

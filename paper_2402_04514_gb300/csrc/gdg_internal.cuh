@@ -11,7 +11,7 @@
 namespace gdg {
 
 // Per-node primitive record written by k_prim and read for every neighbour in the sweeps.
-enum { PR_IRHO = 0, PR_P, PR_A, PR_PME, PR_F, PR_ST, NPRIM };
+enum { PR_IRHO = 0, PR_P, PR_A, PR_PME, PR_F, PR_ST, PR_IP, NPRIM };
 
 // Per-entry flag bits.
 enum { EF_STENCIL = 1, EF_COLOC = 2, EF_SAME_ELEM = 4 };
@@ -48,6 +48,8 @@ struct Dev {
   double inv_e;         // 1 / e
   int ie;               // 1 / e when it is an integer (7 for gamma = 1.4, 5 for gamma = 5/3), else 0
   double k13;           // (gamma + 1) / (2 gamma)
+  int gp, gq;           // gamma = gp / gq with gq <= 8 (7/5, 5/3, ...); gq = 0 when gamma is not such a ratio
+  int ie_root;          // 1 / e when it is an integer <= 16 (p^{-e} by a Newton root), else 0
   double inv_gp1;       // 1 / (gamma + 1)
   double c_ev;
   int order, passes, bounds_mode;
@@ -111,18 +113,86 @@ __device__ __forceinline__ double ipow(double x, int k) {
   return r;
 }
 
+// FP64 reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (Muller et al., Handbook of
+// Floating-Point Arithmetic, ch. 5) started from the FP32 reciprocal: the relative error squares at
+// each step (2^-23 -> 2^-46 -> below FP64 rounding), and the last step is a fused update, so the result
+// is within 2 ulp of 1/x.  Costs 4 FP64 FMAs instead of a full FP64 division on a chip whose FP64 pipe is
+// the bottleneck.  Arguments outside the FP32 normal range take the IEEE division.
+__device__ __forceinline__ double rcp64(double x) {
+  float xf = (float)x;
+  float ax = fabsf(xf);
+  if (!(ax > 1e-37f && ax < 1e37f)) return 1.0 / x;
+  double y = (double)__frcp_rn(xf);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// y = x^{-1/q} for x > 0 and 1 <= q <= 16, by the Newton-Raphson iteration for f(y) = y^{-q} - x,
+// y <- y + y (1 - x y^q) / q, from the FP32 seed exp2(-log2(x) / q); two steps take the seed's 2^-22
+// relative error below FP64 rounding (the error contracts as (q+1)/2 e^2).  Arguments outside the FP32
+// normal range use pow.
+__device__ __forceinline__ double rootinv(double x, int q) {
+  float xf = (float)x;
+  if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -1.0 / q);
+  double y = (double)exp2f(-log2f(xf) / (float)q);
+  const double iq = 1.0 / q;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    double t = fma(-x, ipow(y, q), 1.0);
+    y = fma(y * t, iq, y);
+  }
+  return y;
+}
+
+// rho^{-gamma} and 1/rho together.  With gamma = p/q: y = rho^{-1/q}, rho^{-gamma} = y^p, 1/rho = y^q.
+__device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double* inv_rho) {
+  if (D.gq > 0) {
+    double y = rootinv(rho, D.gq);
+    *inv_rho = ipow(y, D.gq);
+    return ipow(y, D.gp);
+  }
+  *inv_rho = rcp64(rho);
+  return pow(rho, -D.gamma);
+}
+
+// rho^gamma and 1/rho together.  With gamma = p/q and k = ceil(p/q): rho^gamma = rho^k y^{kq - p}.
+__device__ __forceinline__ double rho_pow_gamma(const Dev& D, double rho, double* inv_rho) {
+  if (D.gq > 0) {
+    double y = rootinv(rho, D.gq);
+    *inv_rho = ipow(y, D.gq);
+    int k = (D.gp + D.gq - 1) / D.gq;
+    return ipow(rho, k) * ipow(y, k * D.gq - D.gp);
+  }
+  *inv_rho = rcp64(rho);
+  return pow(rho, D.gamma);
+}
+
+// min / max of positive doubles through their bit patterns (IEEE order of positive numbers is the
+// integer order), which keeps the bound aggregates off the FP64 pipe.
+__device__ __forceinline__ double pmin(double a, double b) {
+  long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x < y ? x : y);
+}
+__device__ __forceinline__ double pmax(double a, double b) {
+  long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
 // lambda_max^+ of the Riemann problem along n (Sec. 3.1, eq. (eq:dij_low_order)), from the normal
-// velocities u, pressures p, sound speeds a and p^{-e} of both states: the two-rarefaction pressure
+// velocities u, pressures p (and 1/p), sound speeds a and p^{-e} of both states: the two-rarefaction pressure
 // p~ bounds the star pressure from above for 1 < gamma <= 5/3; the outer wave speeds at p~ bound the
 // exact ones.
-__device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL, double aL, double pmeL,
-                                             double uR, double pR, double aR, double pmeR) {
+__device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL, double ipL, double aL,
+                                             double pmeL, double uR, double pR, double ipR, double aR,
+                                             double pmeR) {
   double num = fmax(aL + aR - 0.5 * D.gm1 * (uR - uL), 0.0);
-  double r = num / (aL * pmeL + aR * pmeR);
+  double r = num * rcp64(aL * pmeL + aR * pmeR);
   double pt = D.ie > 0 ? ipow(r, D.ie) : pow(r, D.inv_e);
   double xL = pt - pL, xR = pt - pR;
-  double sL = xL > 0.0 ? sqrt(1.0 + D.k13 * xL / pL) : 1.0;
-  double sR = xR > 0.0 ? sqrt(1.0 + D.k13 * xR / pR) : 1.0;
+  double sL = xL > 0.0 ? sqrt(1.0 + D.k13 * xL * ipL) : 1.0;
+  double sR = xR > 0.0 ? sqrt(1.0 + D.k13 * xR * ipR) : 1.0;
   double l1 = uL - aL * sL;
   double l3 = uR + aR * sR;
   return fmax(fmax(-l1, 0.0), fmax(l3, 0.0));
@@ -174,7 +244,12 @@ __device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const d
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
   if (!(V[0] > 0.0)) return -1.0;
-  return internal_energy<DIM>(V) - smin * pow(V[0], D.gamma);
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += V[1 + k] * V[1 + k];
+  double irho;
+  double rg = rho_pow_gamma(D, V[0], &irho);
+  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
 }
 
 template <int DIM>
@@ -182,32 +257,99 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
   double V[DIM + 2];
 #pragma unroll
   for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
-  double rho = V[0], mP = 0.0, m2 = 0.0;
+  double mP = 0.0, m2 = 0.0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     mP += V[1 + k] * P[1 + k];
     m2 += V[1 + k] * V[1 + k];
   }
-  double deps = P[DIM + 1] - mP / rho + 0.5 * m2 * P[0] / (rho * rho);
-  return deps - smin * D.gamma * pow(rho, D.gamma - 1.0) * P[0];
+  double irho;
+  double rg = rho_pow_gamma(D, V[0], &irho);
+  double deps = P[DIM + 1] - mP * irho + 0.5 * m2 * P[0] * irho * irho;
+  return deps - smin * D.gamma * rg * irho * P[0];
+}
+
+// Per-row context of the line searches from one state U0 (the row's U^L or U^(1)) against the row's
+// bounds: psi(0) in FP64 once per row, and FP32 copies of U0's parts for the increment certificate.
+template <int DIM>
+struct LsRow {
+  double U0[DIM + 2];
+  double rmin, rmax, smin, psi0;
+  float r0, m0[DIM], m0sq, sg0;
+};
+
+template <int DIM>
+__device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double* U0, double rmin, double rmax,
+                                       double smin) {
+  double m2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) c.U0[q] = U0[q];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += U0[1 + k] * U0[1 + k];
+  c.rmin = rmin;
+  c.rmax = rmax;
+  c.smin = smin;
+  double ir;
+  double rg = (U0[0] > 0.0) ? rho_pow_gamma(D, U0[0], &ir) : 0.0;
+  c.psi0 = (U0[0] > 0.0) ? U0[DIM + 1] - 0.5 * m2 * ir - smin * rg : -1.0;
+  c.r0 = (float)U0[0];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) c.m0[k] = (float)U0[1 + k];
+  c.m0sq = (float)m2;
+  c.sg0 = (float)(smin * rg);
+}
+
+// Certifies psi(t) >= 0 from psi(0) (FP64) and the increment dpsi = psi(t) - psi(0) evaluated in FP32 in
+// differenced form, so that its error scales with |t P| rather than with |U0|:
+//   dpsi = t P_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
+//   dG = s_min rho0^gamma expm1(gamma log1p(a / rho0)),   a = t P_rho, b = t P_m.
+// Every FP32 operation and conversion has relative error <= 2^-23 and log1pf / expm1f a few ulp, so the
+// FP32 dpsi is within 1e-6 (|t P_E| + S_K + |dG|) of the exact increment, S_K the magnitude of dK's
+// terms; certifying only when psi(0) + dpsi > 1e-4 times that scale leaves a factor 100.  Requires
+// a > -rho0 / 2 (otherwise the caller evaluates psi in FP64).
+template <int DIM>
+__device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* P, double t) {
+  float tf = (float)t;
+  float a = tf * (float)P[0];
+  if (!(a > -0.5f * c.r0)) return false;
+  float mb = 0.f, bb = 0.f, nb2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    float b = tf * (float)P[1 + k];
+    mb = fmaf(c.m0[k], b, mb);
+    bb = fmaf(b, b, bb);
+    nb2 = fmaf(fabsf(c.m0[k]), fabsf(b), nb2);
+  }
+  float eE = tf * (float)P[DIM + 1];
+  float r1 = c.r0 + a;
+  float den = 2.f * c.r0 * r1;
+  float dK = (c.r0 * (2.f * mb + bb) - a * c.m0sq) / den;
+  float SK = (c.r0 * (2.f * nb2 + bb) + fabsf(a) * c.m0sq) / den;
+  float dG = c.sg0 * expm1f((float)D.gamma * log1pf(a / c.r0));
+  float dpsi = eE - dK - dG;
+  float scale = fabsf(eE) + SK + fabsf(dG);
+  return c.psi0 + (double)dpsi > 1e-4 * (double)scale && c.psi0 + (double)dpsi > 0.0;
 }
 
 // Largest l in [0, 1] with U0 + l P in B_i (Sec. 5.4, eq. (ConvexScheme), Lemma ConsInvariants):
 // closed form for the density bounds, then, if the entropy constraint fails at l_rho, a bracketed
 // iteration on the concave psi: the chord root stays feasible, the tangent root from the infeasible end
 // stays infeasible (bisection when rounding keeps both from moving); stops when the bracket is at most
-// ls_tol wide and returns the feasible end.
+// ls_tol wide and returns the feasible end.  The FP32 certificate only skips FP64 evaluations whose
+// outcome it proves; the result is that of the FP64 search.
 template <int DIM>
-__device__ __forceinline__ double line_search(const Dev& D, const double* U0, const double* P, double rmin,
-                                              double rmax, double smin) {
+__device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c, const double* P) {
+  const double* U0 = c.U0;
+  const double smin = c.smin;
   double l = 1.0;
-  if (U0[0] + P[0] < rmin) l = (rmin - U0[0]) / P[0];
-  if (U0[0] + P[0] > rmax) l = (rmax - U0[0]) / P[0];
+  if (U0[0] + P[0] < c.rmin) l = (c.rmin - U0[0]) / P[0];
+  if (U0[0] + P[0] > c.rmax) l = (c.rmax - U0[0]) / P[0];
   if (!(l > 0.0)) l = 0.0;
   if (l > 1.0) l = 1.0;
+  if (ls_certified<DIM>(D, c, P, l)) return l;
   double fb = ls_psi<DIM>(D, U0, P, l, smin);
   if (fb >= 0.0) return l;
-  double fa = ls_psi<DIM>(D, U0, P, 0.0, smin);
+  double fa = c.psi0;
   if (fa < 0.0) return 0.0;
   double a = 0.0, b = l;
   for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {

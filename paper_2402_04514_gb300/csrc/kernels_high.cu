@@ -102,16 +102,16 @@ __global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const doub
   // relaxed local bounds
   double lo = S.agg[i], hi = S.agg[n + i], sl = S.agg[2 * n + i];
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    lo = fmin(lo, S.bbar[b]);
-    hi = fmax(hi, S.bbar[b]);
-    sl = fmin(sl, S.bbar[(size_t)D.nb + b]);
+    lo = pmin(lo, S.bbar[b]);
+    hi = pmax(hi, S.bbar[b]);
+    sl = pmin(sl, S.bbar[(size_t)D.nb + b]);
   }
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     if (D.cnorm[e] == 0.0) continue;
     int j = D.col[e];
-    lo = fmin(lo, S.agg[j]);
-    hi = fmax(hi, S.agg[n + j]);
-    sl = fmin(sl, S.agg[2 * n + j]);
+    lo = pmin(lo, S.agg[j]);
+    hi = pmax(hi, S.agg[n + j]);
+    sl = pmin(sl, S.agg[2 * n + j]);
   }
   double rmin, rmax, smin;
   if (D.bounds_mode == 0) {
@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const doub
   double UL[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) UL[q] = S.UL[(size_t)q * n + i];
+  LsRow<DIM> ls;
+  ls_row<DIM>(D, ls, UL, rmin, rmax, smin);
   const double ikm = D.inv_km[i];
   const int nl = D.n_loc;
   const int elem = i / nl;
@@ -148,13 +150,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const doub
       S.A[(size_t)q * D.nnz + e] = a;
       Pv[q] = a * ikm;
     }
-    S.l1[e] = line_search<DIM>(D, UL, Pv, rmin, rmax, smin);
+    S.l1[e] = line_search<DIM>(D, ls, Pv);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double Pv[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) Pv[q] = S.AB[(size_t)q * D.nb + b] * ikm;
-    S.l1B[b] = line_search<DIM>(D, UL, Pv, rmin, rmax, smin);
+    S.l1B[b] = line_search<DIM>(D, ls, Pv);
   }
 }
 

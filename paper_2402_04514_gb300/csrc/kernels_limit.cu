@@ -44,21 +44,33 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
   }
 #pragma unroll
   for (int q = 0; q < M; ++q) S.U1[q * n + i] = U1[q];
-  const double rmin = S.bounds[i], rmax = S.bounds[n + i], smin = S.bounds[2 * n + i];
+  LsRow<DIM> ls;
+  ls_row<DIM>(D, ls, U1, S.bounds[i], S.bounds[n + i], S.bounds[2 * n + i]);
   const double ikm = D.inv_km[i];
+  // an entry with l1 = 1 has no remainder: its l2 multiplies zero and is set to 1 without a search
   for (int e = r0; e < r1; ++e) {
-    double w = (1.0 - fmin(S.l1[e], S.l1[D.tr[e]])) * ikm;
+    double rem = 1.0 - fmin(S.l1[e], S.l1[D.tr[e]]);
+    if (rem == 0.0) {
+      S.l2[e] = 1.0;
+      continue;
+    }
+    double w = rem * ikm;
     double Pv[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) Pv[q] = S.A[q * nnz + e] * w;
-    S.l2[e] = line_search<DIM>(D, U1, Pv, rmin, rmax, smin);
+    S.l2[e] = line_search<DIM>(D, ls, Pv);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    double w = (1.0 - S.l1B[b]) * ikm;
+    double rem = 1.0 - S.l1B[b];
+    if (rem == 0.0) {
+      S.l2B[b] = 1.0;
+      continue;
+    }
+    double w = rem * ikm;
     double Pv[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) Pv[q] = S.AB[q * nb + b] * w;
-    S.l2B[b] = line_search<DIM>(D, U1, Pv, rmin, rmax, smin);
+    S.l2B[b] = line_search<DIM>(D, ls, Pv);
   }
 }
 

@@ -8,7 +8,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Per-node primitives (Sec. 2.2): 1/rho, p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
+// Per-node primitives (Sec. 2.2): 1/rho, p, 1/p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
 // f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
 // Flags a state outside the admissible set of eq. (AddSet).
 template <int DIM>
@@ -24,14 +24,18 @@ __global__ void __launch_bounds__(kThreads) k_prim(Dev D, Scratch S, const doubl
   double eps = Ui[DIM + 1] - 0.5 * m2 * irho;
   if (!(Ui[0] > 0.0) || !(eps > 0.0)) atomicOr(S.flags, (unsigned)GDG_FLAG_INADMISSIBLE);
   double p = D.gm1 * eps;
-  double st = pow(Ui[0], -D.gamma) * eps;
+  double ir;
+  double st = rho_neg_gamma(D, Ui[0], &ir) * eps;
   double* P = S.prim;
   size_t n = D.n;
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
+  P[PR_IP * n + i] = 1.0 / p;
   P[PR_A * n + i] = sqrt(D.gamma * p * irho);
-  P[PR_PME * n + i] = pow(p, -D.e_exp);
-  P[PR_F * n + i] = pow(D.gm1 * st, D.inv_gp1);
+  P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.ie_root) : pow(p, -D.e_exp);
+  // f = (gm1 s~)^{1/(gamma+1)} = x^{q/(p+q)} = x (x^{-1/(p+q)})^p for gamma = p/q
+  double x = D.gm1 * st;
+  P[PR_F * n + i] = (D.gq > 0 && D.gp + D.gq <= 16) ? x * ipow(rootinv(x, D.gp + D.gq), D.gp) : pow(x, D.inv_gp1);
   P[PR_ST * n + i] = st;
 }
 
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
     double Ui[M];
     load_state<DIM>(U, D.n, i, Ui);
     const double* P = S.prim;
-    double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], a_i = P[PR_A * n + i],
+    double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], ip_i = P[PR_IP * n + i], a_i = P[PR_A * n + i],
            pme_i = P[PR_PME * n + i];
     double dsum = 0.0;
     for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
@@ -64,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
       }
       uL *= irho_i;
       uR *= P[PR_IRHO * n + j];
-      dsum += cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, P[PR_P * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
+      dsum += cnm * lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], P[PR_IP * n + j], P[PR_A * n + j],
+                               P[PR_PME * n + j]);
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
       double nv[DIM], UB[M];
@@ -79,8 +84,8 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
         uL += Ui[1 + k] * nv[k];
         uR += UB[1 + k] * nv[k];
       }
-      dsum += D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, a_i, pme_i, uR * irB, pB, sqrt(D.gamma * pB * irB),
-                                      pow(pB, -D.e_exp));
+      dsum += D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, ip_i, a_i, pme_i, uR * irB, pB, 1.0 / pB,
+                                      sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
     }
     if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
   }
@@ -118,8 +123,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
   const double* P = S.prim;
   double Ui[M];
   load_state<DIM>(U, D.n, i, Ui);
-  const double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], a_i = P[PR_A * n + i],
-               pme_i = P[PR_PME * n + i], f_i = P[PR_F * n + i], st_i = P[PR_ST * n + i];
+  const double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], ip_i = P[PR_IP * n + i],
+               a_i = P[PR_A * n + i], pme_i = P[PR_PME * n + i], f_i = P[PR_F * n + i], st_i = P[PR_ST * n + i];
   double rhs[M], Fsum[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) rhs[q] = Fsum[q] = 0.0;
@@ -142,13 +147,15 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
     uL *= irho_i;
     const double irho_j = P[PR_IRHO * n + j], p_j = P[PR_P * n + j];
     uR *= irho_j;
-    double d = cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, p_j, P[PR_A * n + j], P[PR_PME * n + j]);
+    double lam = lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, p_j, P[PR_IP * n + j], P[PR_A * n + j],
+                            P[PR_PME * n + j]);
+    double d = cnm * lam;
     S.dL[e] = d;
     dsum += d;
     double fi[M], fj[M];
     flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
     flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
-    double t = cnm / (2.0 * d);
+    double t = 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
     double Ub[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) {
@@ -157,10 +164,14 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
       Ub[q] = 0.5 * (Ui[q] + Uj[q]) - t * (fj[q] - fi[q]);
     }
     psum += cnm * fj[0] * (P[PR_F * n + j] - f_i);
-    double stb = pow(Ub[0], -D.gamma) * internal_energy<DIM>(Ub);
-    lo = fmin(lo, fmin(Uj[0], Ub[0]));
-    hi = fmax(hi, fmax(Uj[0], Ub[0]));
-    sl = fmin(sl, fmin(P[PR_ST * n + j], stb));
+    double irb, mb2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) mb2 += Ub[1 + k] * Ub[1 + k];
+    double rg = rho_neg_gamma(D, Ub[0], &irb);
+    double stb = rg * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+    lo = pmin(lo, pmin(Uj[0], Ub[0]));
+    hi = pmax(hi, pmax(Uj[0], Ub[0]));
+    sl = pmin(sl, pmin(P[PR_ST * n + j], stb));
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double nv[DIM], UB[M];
@@ -179,7 +190,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
     uL *= irho_i;
     uR *= irB;
     double cnm = D.bnorm[b];
-    double d = cnm * lambda_max(D, uL, p_i, a_i, pme_i, uR, pB, sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
+    double d = cnm * lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, pB, 1.0 / pB, sqrt(D.gamma * pB * irB),
+                                pow(pB, -D.e_exp));
     S.dB[b] = d;
     dsum += d;
     double fi[M], fB[M];

@@ -1,0 +1,114 @@
+// Device self-test of the FP64 helpers the sweep uses in place of CUDA's division and power
+// (gdg_math_selftest): runs one helper, or CUDA's own reference operation, over a device array.
+#include "gdg_internal.cuh"
+
+namespace gdg {
+namespace {
+
+__global__ void k_math(int fn, int q, const double* __restrict__ x, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = x[i];
+  switch (fn) {
+    case 0: y[i] = rcp64(v); break;
+    case 1: y[i] = rootinv(v, q); break;
+    case 2: y[i] = 1.0 / v; break;
+    case 3: y[i] = pow(v, -1.0 / q); break;
+    default: y[i] = 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace gdg
+
+extern "C" int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream) {
+  if (fn < 0 || fn > 3 || q < 1 || q > 16 || n < 0 || (n > 0 && (!x || !y))) return GDG_EINVAL;
+  if (n == 0) return GDG_OK;
+  int threads = 256;
+  long long blocks = (n + threads - 1) / threads;
+  gdg::k_math<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(fn, q, x, y, n);
+  return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Throughput of the arithmetic the sweep is made of (gdg_fp64_throughput): every thread runs ILP
+// independent chains of one operation; the result is operations per second over the whole GPU.
+namespace gdg {
+namespace {
+
+constexpr int kIlp = 8;
+
+template <int OP>
+__global__ void k_rate(double* out, int iters, double a, double b) {
+  double x[kIlp];
+#pragma unroll
+  for (int k = 0; k < kIlp; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x & 63) + 0.01 * k;
+  float xf[kIlp];
+#pragma unroll
+  for (int k = 0; k < kIlp; ++k) xf[k] = (float)x[k];
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+      if (OP == 0) x[k] = fma(x[k], a, b);                 // DFMA
+      if (OP == 1) x[k] = a / x[k] + b;                    // FP64 division
+      if (OP == 2) x[k] = sqrt(x[k]) + b;                  // FP64 square root
+      if (OP == 3) x[k] = pow(x[k], a) + b;                // FP64 power
+      if (OP == 4) xf[k] = fmaf(xf[k], (float)a, (float)b);  // FFMA
+      if (OP == 5) x[k] = rcp64(x[k]) + b;                 // reciprocal of this library
+      if (OP == 6) x[k] = rootinv(x[k], 5) + b;            // x^{-1/5} of this library
+      if (OP == 7) x[k] = (double)((float)x[k] * 0.5f) + b;  // FP64 -> FP32 -> FP64 conversion pair
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kIlp; ++k) s += x[k] + xf[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int OP>
+cudaError_t run_rate(int blocks, int threads, int iters, double* buf, cudaStream_t s, float* ms) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double a = (OP == 3) ? 0.3 : 0.999, b = (OP == 0 || OP == 4) ? 1e-3 : 0.5;
+  k_rate<OP><<<blocks, threads, 0, s>>>(buf, iters, a, b);  // warm-up
+  cudaEventRecord(e0, s);
+  k_rate<OP><<<blocks, threads, 0, s>>>(buf, iters, a, b);
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err == cudaSuccess ? cudaGetLastError() : err;
+}
+
+}  // namespace
+}  // namespace gdg
+
+extern "C" int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream) {
+  if (op < 0 || op > 7 || !ops_per_s) return GDG_EINVAL;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8;
+  const int iters[8] = {4096, 256, 256, 32, 16384, 512, 128, 1024};
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess) return GDG_ENOMEM;
+  float ms = 0.f;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (op) {
+    case 0: e = gdg::run_rate<0>(blocks, threads, iters[0], buf, s, &ms); break;
+    case 1: e = gdg::run_rate<1>(blocks, threads, iters[1], buf, s, &ms); break;
+    case 2: e = gdg::run_rate<2>(blocks, threads, iters[2], buf, s, &ms); break;
+    case 3: e = gdg::run_rate<3>(blocks, threads, iters[3], buf, s, &ms); break;
+    case 4: e = gdg::run_rate<4>(blocks, threads, iters[4], buf, s, &ms); break;
+    case 5: e = gdg::run_rate<5>(blocks, threads, iters[5], buf, s, &ms); break;
+    case 6: e = gdg::run_rate<6>(blocks, threads, iters[6], buf, s, &ms); break;
+    default: e = gdg::run_rate<7>(blocks, threads, iters[7], buf, s, &ms); break;
+  }
+  cudaFree(buf);
+  if (e != cudaSuccess) return GDG_ECUDA;
+  *ops_per_s = (double)blocks * threads * gdg::kIlp * iters[op] / (ms * 1e-3);
+  return GDG_OK;
+}

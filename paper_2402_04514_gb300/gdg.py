@@ -76,12 +76,14 @@ def load(build_if_missing: bool = False):
     L.gdg_debug_export.argtypes = [vp, C.c_char_p, vp, i64, vp]
     L.gdg_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.gdg_profile.argtypes = [vp, i32]
+    L.gdg_math_selftest.argtypes = [i32, i32, vp, vp, i64, vp]
+    L.gdg_fp64_throughput.argtypes = [i32, C.POINTER(d), vp]
     L.gdg_profile_read.argtypes = [vp, vp, vp]
     L.gdg_destroy.argtypes = [vp]
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_status", "gdg_debug_export",
-              "gdg_get_info", "gdg_profile", "gdg_profile_read"):
+              "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -107,6 +109,28 @@ def _stream(stream):
 
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def math_selftest(fn: int, q: int, x, stream=None):
+    """Runs gdg_math_selftest on the device tensor x (float64) and returns the result tensor."""
+    import torch
+
+    y = torch.empty_like(x)
+    _check(load().gdg_math_selftest(fn, q, _ptr(x), _ptr(y), x.numel(), _stream(stream)), "gdg_math_selftest")
+    return y
+
+
+RATE_OPS = ("dfma", "ddiv", "dsqrt", "dpow", "ffma", "rcp64", "rootinv5", "f2f_pair")
+
+
+def fp64_throughput(stream=None) -> dict:
+    """{operation: operations per second} measured on the current GPU (gdg_fp64_throughput)."""
+    out = {}
+    for i, name in enumerate(RATE_OPS):
+        v = C.c_double()
+        _check(load().gdg_fp64_throughput(i, C.byref(v), _stream(stream)), "gdg_fp64_throughput")
+        out[name] = v.value
+    return out
 
 
 class Solver:

@@ -86,13 +86,23 @@ def test_intermediates_parity(torch_cuda, name):
     assert rel_err(S.export("dL"), tr["dL"]) <= 1e-13
     if P.nb:
         assert rel_err(S.export("dB"), tr["dB"]) <= 1e-13
-    assert np.abs(S.export("N") - tr["N"]).max() <= 1e-9
+    # N_i = R_i / D_i loses relative accuracy where the stencil's states differ by little more than
+    # rounding; it only ever multiplies those differences (through d^H), so what is bounded is
+    # |dN_i| times the largest relative state difference over the stencil of i.
+    rows = np.repeat(np.arange(P.n), np.diff(P.row_ptr))
+    stencil = np.abs(P.cij).sum(0) > 0
+    scale = np.abs(U).max(1, keepdims=True)
+    var = np.zeros(P.n)
+    np.maximum.at(var, rows[stencil], (np.abs(U[:, P.col_idx[stencil]] - U[:, rows[stencil]]) / scale).max(0))
+    assert (np.abs(S.export("N") - tr["N"]) * var).max() <= 1e-12
     assert rel_err(S.export("UL"), tr["UL"]) <= STAGE_TOL
     for k in ("rho_min", "rho_max", "s_min"):
         assert rel_err(S.export(k), tr[k]) <= 1e-13
     assert rel_err(S.export("A"), tr["A"]) <= 1e-11
-    for k in ("l1", "l2"):
-        assert np.abs(S.export(k) - tr[k]).max() <= 1e-9
+    l1 = S.export("l1")
+    assert np.abs(l1 - tr["l1"]).max() <= 1e-12
+    rem = l1 < 1.0  # where l1 = 1 the pass-2 coefficient multiplies a zero remainder
+    assert np.abs(S.export("l2")[rem] - tr["l2"][rem]).max(initial=0.0) <= 1e-12
     assert rel_err(S.export("U1"), tr["U1"]) <= STAGE_TOL
 
 
@@ -140,7 +150,7 @@ def test_edge_cases(torch_cuda):
     torch = torch_cuda
     P = assembly.assemble_2d(1, 1, 2)
     U = workloads.four_quadrant(P.x[0], P.x[1], seed=1)
-    S, O = _pair(P)
+    S, O = _pair(P, params=dict(c_r=0.5))  # one element: h_i is O(1), c_r = 4 would make r_h^- < 0
     tau = O.max_dt(U, 0.5)
     out = S.stage(_dev(torch, U), tau)
     ref, _ = O.stage(U, tau)
@@ -150,7 +160,6 @@ def test_edge_cases(torch_cuda):
     S.stage(_dev(torch, U), 3.0 * tau / 0.5)
     assert S.status(clear=True) & 2
     assert S.status() == 0
-    E = assembly.assemble_2d(0, 0, 1) if False else None
     from paper_2402_04514_gb300.assembly import Problem
     Pe = Problem(dim=2, degree=1, n=0, n_loc=4, row_ptr=np.zeros(1, np.int64), col_idx=np.zeros(0, np.int32),
                  cij=np.zeros((2, 0)), coloc=np.zeros(0, np.uint8), mi=np.zeros(0), MK=np.zeros((0, 4, 4)),
@@ -223,3 +232,29 @@ def test_full_size_bench_configuration_sampled(torch_cuda):
         want = ref[:, le * nl:(le + 1) * nl]
         scale = np.abs(U).max(1, keepdims=True)
         assert (np.abs(got - want) <= STAGE_TOL * scale).all(), (ex, ey)
+
+
+@pytest.mark.parametrize("q", [1, 3, 5, 7, 12])
+def test_fp64_helpers_against_cuda(torch_cuda, q):
+    """The Newton-Raphson reciprocal and inverse root used in the sweep: the reciprocal is within 2 ulp
+    of CUDA's 1.0 / x; the root is within 2 ulp of x^{-1/q} computed in extended precision (numpy's
+    long double), as accurate as CUDA's pow(x, -1.0/q), whose rounded exponent costs it up to a few ulp
+    when |log x| is large."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import math_selftest
+
+    rng = np.random.default_rng(q)
+    x = np.concatenate([np.exp(rng.uniform(np.log(1e-12), np.log(1e12), 200000)), [1.0, 2.0, 0.5, 3.0]])
+    xd = torch.from_numpy(x).cuda()
+    mine_r, ref_r = math_selftest(0, q, xd).cpu().numpy(), math_selftest(2, q, xd).cpu().numpy()
+    mine_q, cuda_q = math_selftest(1, q, xd).cpu().numpy(), math_selftest(3, q, xd).cpu().numpy()
+    assert (np.abs(mine_r - ref_r) <= 2 * np.spacing(np.abs(ref_r))).all()
+    xl = x.astype(np.longdouble)
+    exact = np.power(xl, -np.longdouble(1) / np.longdouble(q))
+    ulp = np.spacing(np.abs(exact.astype(np.float64)))
+    err_mine = np.abs(mine_q.astype(np.longdouble) - exact).astype(np.float64) / ulp
+    err_cuda = np.abs(cuda_q.astype(np.longdouble) - exact).astype(np.float64) / ulp
+    if np.finfo(np.longdouble).eps < 1e-18:  # a long double wider than double
+        assert err_mine.max() <= max(2.0, err_cuda.max())
+    else:
+        assert (np.abs(mine_q - cuda_q) <= 8 * np.spacing(np.abs(cuda_q))).all()
