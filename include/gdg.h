@@ -163,6 +163,48 @@ int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t
  * buffer; synchronises the stream.  Used for the FP64 roofline of the measurement script. */
 int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
 
+/* Time step without any device allocation.  The paper has no counterpart: this is a service for
+ * callers that may not allocate device memory themselves.  Examples are:
+ *   - code that runs while a CUDA stream is being captured into a graph, where cudaMalloc and
+ *     cudaFree are not allowed;
+ *   - plug-ins inside an application whose device memory belongs to its own pool or budget (a caching
+ *     allocator, a serving process with a fixed HBM share), where a private cudaMalloc bypasses that
+ *     accounting and can fail or fragment the pool;
+ *   - latency-sensitive paths that cannot afford the implicit synchronisation of cudaMalloc.
+ * Such callers cannot create a gdg_handle (gdg_setup allocates), so this entry takes the mesh as device
+ * arrays they own and computes the same tau as gdg_max_dt: cfl * min_i (-m_i / (2 d_ii)).
+ *
+ * Inputs (device pointers owned by the caller, read only):
+ *   row_ptr [n+1] and col_idx [nnz] (int32 CSR, as in gdg_problem), cij [dim][nnz], mi [n];
+ *   boundary entries ordered by node: those of node i are b_ptr[i] .. b_ptr[i+1]-1 (int32 [n+1]), with
+ *   b_c [dim][nb] and b_type [nb] in that order, and bdata [m][nb] (Dirichlet data in the same order;
+ *   may be NULL when no entry is Dirichlet: a Dirichlet entry without data makes the result NaN).
+ * Output: *tau_out, a device double, written on stream (asynchronous; the call does not synchronise).
+ *
+ * Scratch: a fixed array of GDG_NOALLOC_MAX_NODES / 256 doubles (128 KB) in the library's own device
+ * memory, which every GPU that loads the library holds until the process exits.  Meshes with more than
+ * GDG_NOALLOC_MAX_NODES nodes are rejected with GDG_ENOTSUP before any work.  All calls share that
+ * array, so calls whose kernels overlap on the GPU (on different streams, or from several threads)
+ * race and must be serialised by the caller.  The array needs no clearing: each call writes every
+ * slot it reads.  The first call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ * Errors: GDG_EINVAL (NULL pointer, cfl <= 0, gamma <= 1), GDG_ENOTSUP (dim, sizes), GDG_ECUDA. */
+#define GDG_NOALLOC_MAX_NODES 4194304
+typedef struct {
+  int32_t dim;
+  int64_t n, nnz, nb;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* cij;
+  const double* mi;
+  const int32_t* b_ptr;
+  const double* b_c;
+  const int32_t* b_type;
+  double gamma;
+} gdg_dev_mesh;
+int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, const double* bdata, double cfl,
+                       double* tau_out, void* stream);
+
 int gdg_get_info(gdg_handle* h, gdg_info* out);
 void gdg_destroy(gdg_handle* h);
 const char* gdg_error_string(int code);

@@ -42,6 +42,14 @@ class _Problem(C.Structure):
                 ("params", Params)]
 
 
+class DevMesh(C.Structure):
+    """gdg_dev_mesh: a mesh held in caller-owned device arrays (for gdg_max_dt_noalloc)."""
+
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("cij", C.c_void_p), ("mi", C.c_void_p),
+                ("b_ptr", C.c_void_p), ("b_c", C.c_void_p), ("b_type", C.c_void_p), ("gamma", C.c_double)]
+
+
 class _Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nb", C.c_int64), ("dim", C.c_int32), ("n_loc", C.c_int32),
                 ("device_bytes", C.c_int64)]
@@ -78,12 +86,14 @@ def load(build_if_missing: bool = False):
     L.gdg_profile.argtypes = [vp, i32]
     L.gdg_math_selftest.argtypes = [i32, i32, vp, vp, i64, vp]
     L.gdg_fp64_throughput.argtypes = [i32, C.POINTER(d), vp]
+    L.gdg_max_dt_noalloc.argtypes = [C.POINTER(DevMesh), vp, vp, d, vp, vp]
     L.gdg_profile_read.argtypes = [vp, vp, vp]
     L.gdg_destroy.argtypes = [vp]
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_status", "gdg_debug_export",
-              "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput"):
+              "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
+              "gdg_max_dt_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -118,6 +128,12 @@ def math_selftest(fn: int, q: int, x, stream=None):
     y = torch.empty_like(x)
     _check(load().gdg_math_selftest(fn, q, _ptr(x), _ptr(y), x.numel(), _stream(stream)), "gdg_math_selftest")
     return y
+
+
+def max_dt_noalloc(mesh: DevMesh, U, cfl: float, tau_out, bdata=None, stream=None) -> int:
+    """gdg_max_dt_noalloc: writes tau into the device tensor tau_out (one float64) without allocating;
+    returns the status code (0 on success)."""
+    return load().gdg_max_dt_noalloc(C.byref(mesh), _ptr(U), _ptr(bdata), cfl, _ptr(tau_out), _stream(stream))
 
 
 RATE_OPS = ("dfma", "ddiv", "dsqrt", "dpow", "ffma", "rcp64", "rootinv5", "f2f_pair")
