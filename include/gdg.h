@@ -146,7 +146,7 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t 
  * (indices GDG_K_*) into total_ms[GDG_NKERNELS] and launches[GDG_NKERNELS], and clears the records.
  * gdg_profile(h, 0) stops recording and drops pending records. */
 enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIMIT2 = 4, GDG_K_FINAL = 5,
-       GDG_NKERNELS = 6 };
+       GDG_K_EDGE = 6, GDG_NKERNELS = 7 };
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final")
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge")
 
 
 @dataclass
@@ -46,7 +46,9 @@ def bytes_per_launch(c: Counts) -> dict:
     return dict(
         prim=8 * m * n + 8 * NPRIM * n,
         maxdt=8 * m * n + 8 * 4 * n + rowptr + ent_geom + 8 * n,
-        low=8 * m * n + 8 * NPRIM * n + rowptr + ent_geom + 8 * s + 8 * (2 * m + 1 + 3) * n + 8 * 3 * nb,
+        edge=(s // 2) * (4 * 2 + 4 + 4) + s * 8 * (1 + d) + 8 * (m + 5) * n + s * 8 * (m + 3),
+        low=8 * m * n + 8 * 3 * n + rowptr + nnz * (4 + 8) + s * (4 + 8 * (m + 3) + 8 * m)
+        + 8 * (2 * m + 1 + 3) * n + 8 * 3 * nb,
         high=8 * m * n * 2 + 8 * n + rowptr + nnz * (4 + 8 + 8 + 8) + 8 * s * 2 + 8 * n * nl
         + 8 * 3 * n * 2 + 8 * m * n + 8 * n * 3 + 8 * (m + 1) * nnz + 8 * (m + 1) * nb,
         limit2=rowptr + nnz * (4 + 8 + 8 * m) + 8 * m * n * 2 + 8 * 3 * n + 8 * 2 * n + 8 * nnz,
@@ -60,12 +62,14 @@ def flops_per_launch(c: Counts) -> dict:
     vel = 2 * (2 * d) + 2  # two normal velocities
     flux = 2 * (3 * d + 2)  # f(U_i) n and f(U_j) n
     ls = 2 * m + (3 * d + 3) + 3  # U0 + l P, eps, s_min rho^gamma (one psi evaluation)
-    low_entry = vel + lam + 2 + flux + 2 + 11 * m + 4 + (3 * d + 3 + 2)
+    edge_pair = vel + lam + 2 + flux + 2 + m + 4 * m + (3 * d + 3 + 2)  # per undirected stencil edge
+    low_entry = 1 + 4 * m + 3  # row sums of d, G and the entropy flux
     low_node = 3 * m + 3 + 3 + 1 + 3 * d + 4 * m + 5 * m + 1
     return dict(
+        edge=(s // 2) * edge_pair,
         prim=n * (1 + 3 * d + 3 + 1 + 2 + 3 + 1 + 2),
         maxdt=s * (vel + lam + 2) + n * 3 + nb * (lam + vel + 10),
-        low=s * low_entry + n * low_node + nb * (low_entry + 6),
+        low=s * low_entry + n * low_node + nb * (vel + lam + flux + 11 * m + 10),
         high=s * (4 + 3 * m) + n * (2 * nl * m + m + 3) + nnz * (4 * m + m + ls) + nb * (3 * m + ls),
         limit2=nnz * (2 * m + 2 + m + ls) + n * 2 * m + nb * (2 * m + m + 2 + ls),
         final=nnz * (2 + 2 * m) + n * 3 * m + nb * (2 + 2 * m),

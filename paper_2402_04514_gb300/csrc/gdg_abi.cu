@@ -399,6 +399,17 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     double terms = (h->row_ptr[i + 1] - h->row_ptr[i]) + (b_ptr[i + 1] - b_ptr[i]);
     inv_km[i] = terms > 0 ? terms / h->mi[i] : 0.0;
   }
+  // canonical stencil edges (i < j, c_ij != 0) in entry order
+  std::vector<int> edge_e, edge_i;
+  edge_e.reserve(nnz / 2 + 1);
+  edge_i.reserve(nnz / 2 + 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q)
+      if (cnorm[q] > 0.0 && h->col[q] > i) {
+        edge_e.push_back(q);
+        edge_i.push_back((int)i);
+      }
+  const int64_t ne = (int64_t)edge_e.size();
   std::vector<double> bnorm(nb), bn((size_t)dim * nb);
   std::vector<int> btype(nb);
   for (int64_t t = 0; t < nb; ++t) {
@@ -423,9 +434,11 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   size_t o_bptr = ar.take<int>(n + 1), o_bnorm = ar.take<double>(nb), o_bn = ar.take<double>((size_t)dim * nb);
   size_t o_btype = ar.take<int>(nb), o_borig = ar.take<int>(nb);
   size_t o_minv = ar.take<double>((size_t)nel * nl * nl);
+  size_t o_ee = ar.take<int>(ne), o_ei = ar.take<int>(ne);
+  size_t o_G = ar.take<double>((size_t)m * nnz), o_barR = ar.take<double>(nnz), o_barS = ar.take<double>(nnz);
   size_t o_prim = ar.take<double>((size_t)gdg::NPRIM * n), o_dL = ar.take<double>(nnz), o_dB = ar.take<double>(nb);
   size_t o_bbar = ar.take<double>(2 * nb), o_UL = ar.take<double>((size_t)m * n), o_RHSL = ar.take<double>((size_t)m * n);
-  size_t o_N = ar.take<double>(n), o_agg = ar.take<double>(3 * n), o_dd = ar.take<double>(nnz);
+  size_t o_N = ar.take<double>(n), o_agg = ar.take<double>(3 * n);
   size_t o_A = ar.take<double>((size_t)m * nnz), o_AB = ar.take<double>((size_t)m * nb);
   size_t o_bounds = ar.take<double>(3 * n), o_l1 = ar.take<double>(nnz), o_l1B = ar.take<double>(nb);
   size_t o_l2 = ar.take<double>(nnz), o_l2B = ar.take<double>(nb), o_U1 = ar.take<double>((size_t)m * n);
@@ -437,6 +450,8 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     cudaGetLastError();
     return fail(cuda_fail(ce));
   }
+  // zero the whole arena once: entries no kernel writes (d^L, A of m_ij-only entries) read as 0
+  if ((ce = cudaMemset(h->arena, 0, h->arena_bytes)) != cudaSuccess) return fail(cuda_fail(ce));
   char* base = (char*)h->arena;
   auto ptr = [&](size_t o) { return (void*)(base + o); };
   auto up = [&](size_t o, const void* src, size_t bytes) {
@@ -458,6 +473,8 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
       (ce = up(o_btype, btype.data(), sizeof(int) * nb)) != cudaSuccess ||
       (ce = up(o_borig, border.data(), sizeof(int) * nb)) != cudaSuccess ||
       (ce = up(o_minv, MKinv.data(), sizeof(double) * MKinv.size())) != cudaSuccess ||
+      (ce = up(o_ee, edge_e.data(), sizeof(int) * ne)) != cudaSuccess ||
+      (ce = up(o_ei, edge_i.data(), sizeof(int) * ne)) != cudaSuccess ||
       (ce = cudaMemset(ptr(o_flags), 0, 16)) != cudaSuccess)
     return fail(cuda_fail(ce));
 
@@ -485,6 +502,9 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   D.btype = (const int*)ptr(o_btype);
   D.borig = (const int*)ptr(o_borig);
   D.MKinv = (const double*)ptr(o_minv);
+  D.ne = (int)ne;
+  D.edge_e = (const int*)ptr(o_ee);
+  D.edge_i = (const int*)ptr(o_ei);
   D.gamma = P->gamma;
   D.gm1 = P->gamma - 1.0;
   D.e_exp = (P->gamma - 1.0) / (2.0 * P->gamma);
@@ -510,13 +530,15 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   Scratch& S = h->S;
   S.prim = (double*)ptr(o_prim);
   S.dL = (double*)ptr(o_dL);
+  S.G = (double*)ptr(o_G);
+  S.barR = (double*)ptr(o_barR);
+  S.barS = (double*)ptr(o_barS);
   S.dB = (double*)ptr(o_dB);
   S.bbar = (double*)ptr(o_bbar);
   S.UL = (double*)ptr(o_UL);
   S.RHSL = (double*)ptr(o_RHSL);
   S.N = (double*)ptr(o_N);
   S.agg = (double*)ptr(o_agg);
-  S.ddiff = (double*)ptr(o_dd);
   S.A = (double*)ptr(o_A);
   S.AB = (double*)ptr(o_AB);
   S.bounds = (double*)ptr(o_bounds);
@@ -574,6 +596,8 @@ int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double al
   cudaError_t e;
   const Scratch& S = h->S;
   if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_prim(dim, D, S, U_in, s); })) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = timed(h, GDG_K_EDGE, s, [&] { return gdg::launch_edge(dim, D, S, U_in, s); })) != cudaSuccess)
     return cuda_fail(e);
   if ((e = timed(h, GDG_K_LOW, s, [&] {
          return gdg::launch_low(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);

@@ -42,6 +42,10 @@ struct Dev {
   const int* btype;     // [nb]
   const int* borig;     // [nb] index of the entry in the caller's order (for Dirichlet data)
   const double* MKinv;  // [n / n_loc][n_loc][n_loc]
+  // canonical stencil edges: entries (i, j) with c_ij != 0 and i < j, in entry order
+  int ne;
+  const int* edge_e;    // [ne] entry index of (i, j)
+  const int* edge_i;    // [ne] row i
   // equation of state and method constants
   double gamma, gm1;    // gamma, gamma - 1
   double e_exp;         // e = (gamma - 1) / (2 gamma)
@@ -60,13 +64,15 @@ struct Dev {
 struct Scratch {
   double* prim;    // [NPRIM][n]
   double* dL;      // [nnz]
+  double* G;       // [m][nnz] f(U_j) c_ij of stencil entries (from the edge sweep)
+  double* barR;    // [nnz] rho of the bar state Ubar_ij (symmetric in i, j)
+  double* barS;    // [nnz] s~ of the bar state
   double* dB;      // [nb]
   double* bbar;    // [2][nb] rho and s~ of the boundary bar states
   double* UL;      // [m][n]
   double* RHSL;    // [m][n] low-order right-hand side (sum of fluxes and viscous terms)
   double* N;       // [n]
   double* agg;     // [3][n] one-hop aggregates (rho min, rho max, s~ min)
-  double* ddiff;   // [nnz] d^H - d^L
   double* A;       // [m][nnz]
   double* AB;      // [m][nb]
   double* bounds;  // [3][n] rho_min, rho_max, s~_min
@@ -91,6 +97,7 @@ struct Scratch {
 cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s);
 cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
                          cudaStream_t s);
+cudaError_t launch_edge(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s);
 cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
                        double tau, const double* Ubase, double alpha, double* Uout, cudaStream_t s);
 cudaError_t launch_high(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
@@ -113,16 +120,36 @@ __device__ __forceinline__ double ipow(double x, int k) {
   return r;
 }
 
+// FP64 -> FP32 by integer operations on the bit pattern (exponent rebias, significand truncated to 23
+// bits: relative error < 2^-23), which keeps the conversion off the FP64 pipe where the hardware
+// conversion costs about 1.6 FMA issue slots.  Values outside the FP32 normal range take the hardware
+// conversion.
+__device__ __forceinline__ float d2f_fast(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return (float)x;
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// FP32 -> FP64 by integer operations on the bit pattern (exact for normal numbers).
+__device__ __forceinline__ double f2d_fast(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+
 // FP64 reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (Muller et al., Handbook of
 // Floating-Point Arithmetic, ch. 5) started from the FP32 reciprocal: the relative error squares at
 // each step (2^-23 -> 2^-46 -> below FP64 rounding), and the last step is a fused update, so the result
 // is within 2 ulp of 1/x.  Costs 4 FP64 FMAs instead of a full FP64 division on a chip whose FP64 pipe is
 // the bottleneck.  Arguments outside the FP32 normal range take the IEEE division.
 __device__ __forceinline__ double rcp64(double x) {
-  float xf = (float)x;
+  float xf = d2f_fast(x);
   float ax = fabsf(xf);
   if (!(ax > 1e-37f && ax < 1e37f)) return 1.0 / x;
-  double y = (double)__frcp_rn(xf);
+  double y = f2d_fast(__frcp_rn(xf));
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
@@ -134,9 +161,9 @@ __device__ __forceinline__ double rcp64(double x) {
 // relative error below FP64 rounding (the error contracts as (q+1)/2 e^2).  Arguments outside the FP32
 // normal range use pow.
 __device__ __forceinline__ double rootinv(double x, int q) {
-  float xf = (float)x;
+  float xf = d2f_fast(x);
   if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -1.0 / q);
-  double y = (double)exp2f(-log2f(xf) / (float)q);
+  double y = f2d_fast(exp2f(-log2f(xf) / (float)q));
   const double iq = 1.0 / q;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -236,41 +263,10 @@ __device__ __forceinline__ void boundary_state(const Dev& D, int b, const double
   }
 }
 
-// psi(t) = eps(U0 + t P) - s_min rho(t)^gamma (the entropy constraint of the set B_i, Sec. 5.4,
-// eq. (BiSet), times rho^gamma); concave in t.
-template <int DIM>
-__device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const double* P, double t, double smin) {
-  double V[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
-  if (!(V[0] > 0.0)) return -1.0;
-  double m2 = 0.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) m2 += V[1 + k] * V[1 + k];
-  double irho;
-  double rg = rho_pow_gamma(D, V[0], &irho);
-  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
-}
-
-template <int DIM>
-__device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const double* P, double t, double smin) {
-  double V[DIM + 2];
-#pragma unroll
-  for (int q = 0; q < DIM + 2; ++q) V[q] = U0[q] + t * P[q];
-  double mP = 0.0, m2 = 0.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    mP += V[1 + k] * P[1 + k];
-    m2 += V[1 + k] * V[1 + k];
-  }
-  double irho;
-  double rg = rho_pow_gamma(D, V[0], &irho);
-  double deps = P[DIM + 1] - mP * irho + 0.5 * m2 * P[0] * irho * irho;
-  return deps - smin * D.gamma * rg * irho * P[0];
-}
-
 // Per-row context of the line searches from one state U0 (the row's U^L or U^(1)) against the row's
 // bounds: psi(0) in FP64 once per row, and FP32 copies of U0's parts for the increment certificate.
+// The searches run along P = w A (w = the row's 1 / (kappa_i m_i), times 1 - l1 in pass 2), so a point
+// t of the search is U0 + (t w) A.
 template <int DIM>
 struct LsRow {
   double U0[DIM + 2];
@@ -292,35 +288,69 @@ __device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double
   double ir;
   double rg = (U0[0] > 0.0) ? rho_pow_gamma(D, U0[0], &ir) : 0.0;
   c.psi0 = (U0[0] > 0.0) ? U0[DIM + 1] - 0.5 * m2 * ir - smin * rg : -1.0;
-  c.r0 = (float)U0[0];
+  c.r0 = d2f_fast(U0[0]);
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) c.m0[k] = (float)U0[1 + k];
-  c.m0sq = (float)m2;
-  c.sg0 = (float)(smin * rg);
+  for (int k = 0; k < DIM; ++k) c.m0[k] = d2f_fast(U0[1 + k]);
+  c.m0sq = d2f_fast(m2);
+  c.sg0 = d2f_fast(smin * rg);
 }
 
-// Certifies psi(t) >= 0 from psi(0) (FP64) and the increment dpsi = psi(t) - psi(0) evaluated in FP32 in
-// differenced form, so that its error scales with |t P| rather than with |U0|:
-//   dpsi = t P_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
-//   dG = s_min rho0^gamma expm1(gamma log1p(a / rho0)),   a = t P_rho, b = t P_m.
+// psi(s) = eps(U0 + s A) - s_min rho(s)^gamma (the entropy constraint of the set B_i, Sec. 5.4,
+// eq. (BiSet), times rho^gamma); concave in s.
+template <int DIM>
+__device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const double* A, double s, double smin) {
+  double V[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) V[q] = fma(s, A[q], U0[q]);
+  if (!(V[0] > 0.0)) return -1.0;
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += V[1 + k] * V[1 + k];
+  double irho;
+  double rg = rho_pow_gamma(D, V[0], &irho);
+  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
+}
+
+// d psi / d s
+template <int DIM>
+__device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const double* A, double s, double smin) {
+  double V[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) V[q] = fma(s, A[q], U0[q]);
+  double mA = 0.0, m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    mA += V[1 + k] * A[1 + k];
+    m2 += V[1 + k] * V[1 + k];
+  }
+  double irho;
+  double rg = rho_pow_gamma(D, V[0], &irho);
+  double deps = A[DIM + 1] - mA * irho + 0.5 * m2 * A[0] * irho * irho;
+  return deps - smin * D.gamma * rg * irho * A[0];
+}
+
+// Certifies psi(s) >= 0 from psi(0) (FP64) and the increment dpsi = psi(s) - psi(0) evaluated in FP32 in
+// differenced form, so that its error scales with |s A| rather than with |U0|:
+//   dpsi = s A_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
+//   dG = s_min rho0^gamma expm1(gamma log1p(a / rho0)),   a = s A_rho, b = s A_m.
 // Every FP32 operation and conversion has relative error <= 2^-23 and log1pf / expm1f a few ulp, so the
-// FP32 dpsi is within 1e-6 (|t P_E| + S_K + |dG|) of the exact increment, S_K the magnitude of dK's
+// FP32 dpsi is within 1e-6 (|s A_E| + S_K + |dG|) of the exact increment, S_K the magnitude of dK's
 // terms; certifying only when psi(0) + dpsi > 1e-4 times that scale leaves a factor 100.  Requires
 // a > -rho0 / 2 (otherwise the caller evaluates psi in FP64).
 template <int DIM>
-__device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* P, double t) {
-  float tf = (float)t;
-  float a = tf * (float)P[0];
+__device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* A, double s) {
+  float sf = d2f_fast(s);
+  float a = sf * d2f_fast(A[0]);
   if (!(a > -0.5f * c.r0)) return false;
   float mb = 0.f, bb = 0.f, nb2 = 0.f;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    float b = tf * (float)P[1 + k];
+    float b = sf * d2f_fast(A[1 + k]);
     mb = fmaf(c.m0[k], b, mb);
     bb = fmaf(b, b, bb);
     nb2 = fmaf(fabsf(c.m0[k]), fabsf(b), nb2);
   }
-  float eE = tf * (float)P[DIM + 1];
+  float eE = sf * d2f_fast(A[DIM + 1]);
   float r1 = c.r0 + a;
   float den = 2.f * c.r0 * r1;
   float dK = (c.r0 * (2.f * mb + bb) - a * c.m0sq) / den;
@@ -328,26 +358,28 @@ __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, 
   float dG = c.sg0 * expm1f((float)D.gamma * log1pf(a / c.r0));
   float dpsi = eE - dK - dG;
   float scale = fabsf(eE) + SK + fabsf(dG);
-  return c.psi0 + (double)dpsi > 1e-4 * (double)scale && c.psi0 + (double)dpsi > 0.0;
+  double tot = c.psi0 + f2d_fast(dpsi);
+  return tot > 1e-4 * f2d_fast(scale) && tot > 0.0;
 }
 
-// Largest l in [0, 1] with U0 + l P in B_i (Sec. 5.4, eq. (ConvexScheme), Lemma ConsInvariants):
-// closed form for the density bounds, then, if the entropy constraint fails at l_rho, a bracketed
-// iteration on the concave psi: the chord root stays feasible, the tangent root from the infeasible end
-// stays infeasible (bisection when rounding keeps both from moving); stops when the bracket is at most
-// ls_tol wide and returns the feasible end.  The FP32 certificate only skips FP64 evaluations whose
-// outcome it proves; the result is that of the FP64 search.
+// Largest l in [0, 1] with U0 + l P in B_i, P = w A (Sec. 5.4, eq. (ConvexScheme), Lemma
+// ConsInvariants): closed form for the density bounds, then, if the entropy constraint fails at
+// l_rho, a bracketed iteration on the concave psi: the chord root stays feasible, the tangent root
+// from the infeasible end stays infeasible (bisection when rounding keeps both from moving); stops
+// when the bracket is at most ls_tol wide and returns the feasible end.  The FP32 certificate only
+// skips FP64 evaluations whose outcome it proves; the result is that of the FP64 search.
 template <int DIM>
-__device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c, const double* P) {
+__device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c, const double* A, double w) {
   const double* U0 = c.U0;
   const double smin = c.smin;
+  const double Pr = w * A[0];
   double l = 1.0;
-  if (U0[0] + P[0] < c.rmin) l = (c.rmin - U0[0]) / P[0];
-  if (U0[0] + P[0] > c.rmax) l = (c.rmax - U0[0]) / P[0];
+  if (U0[0] + Pr < c.rmin) l = (c.rmin - U0[0]) / Pr;
+  if (U0[0] + Pr > c.rmax) l = (c.rmax - U0[0]) / Pr;
   if (!(l > 0.0)) l = 0.0;
   if (l > 1.0) l = 1.0;
-  if (ls_certified<DIM>(D, c, P, l)) return l;
-  double fb = ls_psi<DIM>(D, U0, P, l, smin);
+  if (ls_certified<DIM>(D, c, A, l * w)) return l;
+  double fb = ls_psi<DIM>(D, U0, A, l * w, smin);
   if (fb >= 0.0) return l;
   double fa = c.psi0;
   if (fa < 0.0) return 0.0;
@@ -355,22 +387,22 @@ __device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c,
   for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {
     bool moved = false;
     double ts = a + (b - a) * fa / (fa - fb);
-    double dfb = ls_dpsi<DIM>(D, U0, P, b, smin);
+    double dfb = w * ls_dpsi<DIM>(D, U0, A, b * w, smin);
     double tn = dfb < 0.0 ? b - fb / dfb : b;
     if (ts > a && ts < b) {
-      double fs = ls_psi<DIM>(D, U0, P, ts, smin);
+      double fs = ls_psi<DIM>(D, U0, A, ts * w, smin);
       if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; }
       moved = true;
     }
     if (tn > a && tn < b) {
-      double fn = ls_psi<DIM>(D, U0, P, tn, smin);
+      double fn = ls_psi<DIM>(D, U0, A, tn * w, smin);
       if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
       moved = true;
     }
     if (!moved) {  // rounding pinned both points to the bracket ends: bisect
       double tm = a + 0.5 * (b - a);
       if (!(tm > a && tm < b)) break;
-      double fm = ls_psi<DIM>(D, U0, P, tm, smin);
+      double fm = ls_psi<DIM>(D, U0, A, tm * w, smin);
       if (fm >= 0.0) { a = tm; fa = fm; } else { b = tm; fb = fm; }
     }
   }

@@ -7,7 +7,7 @@ namespace gdg {
 
 namespace {
 
-constexpr int kMaxBlock = 288;
+constexpr int kMaxBlock = 160;
 
 // Per node i of the block:
 //  1. d_ij^H = max(d^min, d^ev) (Sec. 5, eq. (HighOrderViscosity); Sec. 5.1, eq. (ViscMin); Sec. 5.2),
@@ -22,7 +22,7 @@ constexpr int kMaxBlock = 288;
 //     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i).
 // With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
 template <int DIM>
-__global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const double* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const double* __restrict__ U,
                                                     const double* __restrict__ bdata, double tau,
                                                     const double* __restrict__ Ubase, double alpha,
                                                     double* __restrict__ Uout, int nodes_per_block) {
@@ -49,9 +49,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const doub
       double dev = dl * fmin(D.c_ev * fmax(Ni, Nj), 1.0);
       double dh = fmax(D.mu[e] * dl, dev);
       double dd = dh - dl;
-      S.ddiff[e] = dd;
 #pragma unroll
-      for (int q = 0; q < M; ++q) rhs[q] -= dd * (U[(size_t)q * n + j] - Ui[q]);
+      for (int q = 0; q < M; ++q) {
+        double v = dd * (U[(size_t)q * n + j] - Ui[q]);
+        rhs[q] -= v;
+        S.A[(size_t)q * D.nnz + e] = tau * v;  // viscous part of A_ij, completed below
+      }
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
       double nv[DIM], UB[M];
@@ -138,25 +141,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_high(Dev D, Scratch S, const doub
   const int t0 = t - (i % nl);
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int j = D.col[e];
-    double A[M], Pv[M];
-    double vis = D.cnorm[e] != 0.0 ? tau * S.ddiff[e] : 0.0;
-    bool same = (j / nl) == elem;
-    double mij = same ? D.mij[e] : 0.0;
+    double A[M];
+    const bool stencil = D.cnorm[e] != 0.0;
+    const bool same = (j / nl) == elem;
+    const double mij = same ? D.mij[e] : 0.0;
+    const int tj = t0 + (j % nl);
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      double a = vis != 0.0 ? vis * (U[(size_t)q * n + j] - Ui[q]) : 0.0;
-      if (same) a -= mij * (sdU[q][t0 + (j % nl)] - dUi[q]);
+      double a = stencil ? S.A[(size_t)q * D.nnz + e] : 0.0;
+      if (same) a = fma(-mij, sdU[q][tj] - dUi[q], a);
       A[q] = a;
       S.A[(size_t)q * D.nnz + e] = a;
-      Pv[q] = a * ikm;
     }
-    S.l1[e] = line_search<DIM>(D, ls, Pv);
+    S.l1[e] = line_search<DIM>(D, ls, A, ikm);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    double Pv[M];
+    double A[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) Pv[q] = S.AB[(size_t)q * D.nb + b] * ikm;
-    S.l1B[b] = line_search<DIM>(D, ls, Pv);
+    for (int q = 0; q < M; ++q) A[q] = S.AB[(size_t)q * D.nb + b];
+    S.l1B[b] = line_search<DIM>(D, ls, A, ikm);
   }
 }
 

@@ -54,11 +54,10 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
       S.l2[e] = 1.0;
       continue;
     }
-    double w = rem * ikm;
-    double Pv[M];
+    double A[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) Pv[q] = S.A[q * nnz + e] * w;
-    S.l2[e] = line_search<DIM>(D, ls, Pv);
+    for (int q = 0; q < M; ++q) A[q] = S.A[q * nnz + e];
+    S.l2[e] = line_search<DIM>(D, ls, A, rem * ikm);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double rem = 1.0 - S.l1B[b];
@@ -66,11 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
       S.l2B[b] = 1.0;
       continue;
     }
-    double w = rem * ikm;
-    double Pv[M];
+    double A[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) Pv[q] = S.AB[q * nb + b] * w;
-    S.l2B[b] = line_search<DIM>(D, ls, Pv);
+    for (int q = 0; q < M; ++q) A[q] = S.AB[q * nb + b];
+    S.l2B[b] = line_search<DIM>(D, ls, A, rem * ikm);
   }
 }
 

@@ -102,9 +102,65 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
   }
 }
 
-// Sweep A, one thread per row i:
-//  - d_ij^L = |c_ij| lambda_max^+(U_i, U_j, n_ij) (Sec. 3.1, eq. (eq:dij_low_order)), boundary states
-//    and viscosities (Sec. 4.1; Sec. 4.2, eq. (eq:dij_low_order_modified));
+// Edge sweep, one thread per undirected stencil edge {i, j} (i < j): the quantities of a pair that are
+// symmetric in i and j are computed once and written to both entries (i, j) and (j, i):
+//  - d_ij^L = d_ji^L = |c_ij| lambda_max^+(U_i, U_j, n_ij) (Sec. 3.1, eq. (eq:dij_low_order); the bound
+//    is symmetric under (U_i, U_j, n) -> (U_j, U_i, -n), which is also what makes d^L symmetric);
+//  - the bar state Ubar_ij = Ubar_ji (eq. (UsualBarState)), of which only rho and s~ are kept (for the
+//    local bounds of eq. (eq:local_bounds));
+//  - G_ij = f(U_j) c_ij and G_ji = f(U_i) c_ji = -|c_ij| f(U_i) n_ij for the row sums of sweep A.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_edge(Dev D, Scratch S, const double* __restrict__ U) {
+  constexpr int M = DIM + 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= D.ne) return;
+  const size_t n = D.n, nnz = D.nnz;
+  const int e = D.edge_e[k], i = D.edge_i[k];
+  const int j = D.col[e], t = D.tr[e];
+  const double* P = S.prim;
+  double Ui[M], Uj[M], nv[DIM];
+  load_state<DIM>(U, D.n, i, Ui);
+  load_state<DIM>(U, D.n, j, Uj);
+  const double cnm = D.cnorm[e];
+  double mnL = 0.0, mnR = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    nv[q] = D.cn[(size_t)q * nnz + e];
+    mnL += Ui[1 + q] * nv[q];
+    mnR += Uj[1 + q] * nv[q];
+  }
+  const double p_i = P[PR_P * n + i], p_j = P[PR_P * n + j];
+  const double uL = mnL * P[PR_IRHO * n + i], uR = mnR * P[PR_IRHO * n + j];
+  const double lam = lambda_max(D, uL, p_i, P[PR_IP * n + i], P[PR_A * n + i], P[PR_PME * n + i], uR, p_j,
+                                P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
+  const double d = cnm * lam;
+  S.dL[e] = d;
+  S.dL[t] = d;
+  double fi[M], fj[M];
+  flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
+  flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
+  const double h = 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
+  double Ub[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    S.G[q * nnz + e] = cnm * fj[q];
+    S.G[q * nnz + t] = -(cnm * fi[q]);
+    Ub[q] = 0.5 * (Ui[q] + Uj[q]) - h * (fj[q] - fi[q]);
+  }
+  double mb2 = 0.0, irb;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) mb2 += Ub[1 + q] * Ub[1 + q];
+  const double rgb = rho_neg_gamma(D, Ub[0], &irb);  // sets irb = 1 / rho(Ubar) before its use below
+  const double stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+  S.barR[e] = Ub[0];
+  S.barR[t] = Ub[0];
+  S.barS[e] = stb;
+  S.barS[t] = stb;
+}
+
+// Sweep A, one thread per row i, after the edge sweep:
+//  - the row sums of d_ij^L and f(U_j) c_ij from the edge sweep; boundary states and viscosities (Sec. 4.1;
+//    Sec. 4.2, eq. (eq:dij_low_order_modified));
 //  - the low-order update of Sec. 4.2, eq. (cijdijschememodified), and the CFL check (CFLcond);
 //  - the entropy-viscosity indicator N_i = R_i / D_i (Sec. 5.2);
 //  - the one-hop aggregates of the local bounds (Sec. 5.4, eq. (eq:local_bounds)): min/max of rho_j,
@@ -130,48 +186,24 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
   for (int q = 0; q < M; ++q) rhs[q] = Fsum[q] = 0.0;
   double psum = 0.0, dsum = 0.0;
   double lo = Ui[0], hi = Ui[0], sl = st_i;
+  const size_t nnz = D.nnz;
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-    double cnm = D.cnorm[e];
-    if (cnm == 0.0) continue;  // m_ij-only entry: not in I(i)
-    int j = D.col[e];
-    double Uj[M], nv[DIM];
-    load_state<DIM>(U, D.n, j, Uj);
-    double uL = 0.0, uR = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      nv[k] = D.cn[(size_t)k * D.nnz + e];
-      uL += Ui[1 + k] * nv[k];
-      uR += Uj[1 + k] * nv[k];
-    }
-    const double mnL = uL, mnR = uR;
-    uL *= irho_i;
-    const double irho_j = P[PR_IRHO * n + j], p_j = P[PR_P * n + j];
-    uR *= irho_j;
-    double lam = lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, p_j, P[PR_IP * n + j], P[PR_A * n + j],
-                            P[PR_PME * n + j]);
-    double d = cnm * lam;
-    S.dL[e] = d;
+    if (D.cnorm[e] == 0.0) continue;  // m_ij-only entry: not in I(i)
+    const int j = D.col[e], t = D.tr[e];
+    const double d = S.dL[e];
     dsum += d;
-    double fi[M], fj[M];
-    flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
-    flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
-    double t = 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
-    double Ub[M];
+    double Uj[M];
+    load_state<DIM>(U, D.n, j, Uj);
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      rhs[q] += cnm * fj[q] - d * (Uj[q] - Ui[q]);
-      Fsum[q] += cnm * (fj[q] - fi[q]);
-      Ub[q] = 0.5 * (Ui[q] + Uj[q]) - t * (fj[q] - fi[q]);
+      const double ge = S.G[q * nnz + e];
+      rhs[q] += ge - d * (Uj[q] - Ui[q]);
+      Fsum[q] += ge + S.G[q * nnz + t];  // (f(U_j) - f(U_i)) c_ij
     }
-    psum += cnm * fj[0] * (P[PR_F * n + j] - f_i);
-    double irb, mb2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) mb2 += Ub[1 + k] * Ub[1 + k];
-    double rg = rho_neg_gamma(D, Ub[0], &irb);
-    double stb = rg * (Ub[DIM + 1] - 0.5 * mb2 * irb);
-    lo = pmin(lo, pmin(Uj[0], Ub[0]));
-    hi = pmax(hi, pmax(Uj[0], Ub[0]));
-    sl = pmin(sl, pmin(P[PR_ST * n + j], stb));
+    psum += S.G[e] * (P[PR_F * n + j] - f_i);  // (m_j . c_ij) (f_j - f_i)
+    lo = pmin(lo, pmin(Uj[0], S.barR[e]));
+    hi = pmax(hi, pmax(Uj[0], S.barR[e]));
+    sl = pmin(sl, pmin(P[PR_ST * n + j], S.barS[e]));
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double nv[DIM], UB[M];
@@ -265,6 +297,13 @@ cudaError_t maxdt_impl(const Dev& D, const Scratch& S, const double* U, const do
 }
 
 template <int DIM>
+cudaError_t edge_impl(const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
+  if (D.ne == 0) return cudaSuccess;
+  k_edge<DIM><<<(D.ne + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U);
+  return cudaGetLastError();
+}
+
+template <int DIM>
 cudaError_t low_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
                      const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
   if (D.n == 0) return cudaSuccess;
@@ -284,6 +323,10 @@ cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U
 cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
                          cudaStream_t s) {
   GDG_DISPATCH(dim, maxdt_impl, D, S, U, bdata, s);
+}
+
+cudaError_t launch_edge(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
+  GDG_DISPATCH(dim, edge_impl, D, S, U, s);
 }
 
 cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final")  # GDG_K_* order
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge")  # GDG_K_* order
 BC_SLIP, BC_DIRICHLET = 0, 1
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 
