@@ -140,7 +140,7 @@ def main():
     ap.add_argument("--workload", default="q2_1024_four_quadrant", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-baseline-steps", type=int, default=2)
+    ap.add_argument("--cpu-baseline-steps", type=int, default=8)
     ap.add_argument("--fp64-rates", action="store_true", help="print the measured arithmetic rates and exit")
     args = ap.parse_args()
     if args.fp64_rates:
@@ -234,13 +234,18 @@ def main():
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # DRAM bytes per launch of the top kernel from the committed ncu table, scaled to this mesh by its node
+    # count; None when the table was taken from other library sources than the ones built here
+    traffic = costmodel.measured_traffic(os.path.join(ROOT, "profiles", "dram_traffic_q2_512_four_quadrant.txt"),
+                                         top, n)
     roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": fl / avg_s / 1e12,
                 "peak": costmodel.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "alg_flops_per_launch": fl}
     roofline_hbm = {"bound": "hbm", "kernel": f"k_{top}", "achieved": by / avg_s / 1e9, "peak": hbm_peak,
                     "unit": "GB/s", "frac": by / avg_s / 1e9 / hbm_peak, "alg_bytes_per_launch": by,
+                    "traffic": traffic,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                for k, v in prof.items() if v[1]}

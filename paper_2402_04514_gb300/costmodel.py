@@ -78,3 +78,39 @@ def flops_per_launch(c: Counts) -> dict:
 
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def library_source_digest() -> str:
+    """sha256 (first 16 hex digits) of the library's CUDA sources and public header.  A DRAM-traffic figure
+    taken with ncu is only valid for the sources it was taken from; bench.py reports it only while this
+    digest matches the one recorded beside the figure."""
+    import glob
+    import hashlib
+    import os
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    files = sorted(glob.glob(os.path.join(here, "csrc", "*.cu")) + glob.glob(os.path.join(here, "csrc", "*.cuh")))
+    files.append(os.path.join(os.path.dirname(here), "include", "gdg.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(path: str, kernel: str, n_nodes: int):
+    """DRAM bytes (read + write) per launch of `kernel` from an ncu summary table (lines
+    `kernel nodes dram_read_bytes dram_write_bytes source_digest`), scaled from the captured mesh to
+    `n_nodes` (every array a sweep kernel touches grows in proportion to the node count).  None when the
+    table is missing, has no row for the kernel, or was taken from other sources."""
+    try:
+        with open(path) as fh:
+            lines = [ln.split() for ln in fh if ln.strip() and not ln.lstrip().startswith("#")]
+    except OSError:
+        return None
+    digest = library_source_digest()
+    for f in lines:
+        if len(f) == 5 and f[0] == kernel and f[4] == digest:
+            return (float(f[2]) + float(f[3])) * n_nodes / float(f[1])
+    return None
