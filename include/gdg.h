@@ -137,7 +137,9 @@ int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream);
 /* Copies an intermediate of the last stage to host memory (for tests and diagnostics): name is one of
  * "dL" [nnz], "dB" [nb], "N" [n], "UL" [m][n], "rho_min" [n], "rho_max" [n], "s_min" [n], "l1" [nnz],
  * "l2" [nnz], "U1" [m][n], "A" [m][nnz]; entries follow gdg_problem's order (boundary data its own).
- * count must equal the array size.  Synchronises the stream. */
+ * "ls_deferred" [2] gives the number of line searches of each limiter pass that needed the bracketed
+ * iteration (run by a separate kernel over a queue).  count must equal the array size.  Synchronises
+ * the stream. */
 int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t count, void* stream);
 
 /* Kernel timing for measurement.  With gdg_profile(h, 1) every kernel launch of gdg_stage and
@@ -146,14 +148,16 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t 
  * (indices GDG_K_*) into total_ms[GDG_NKERNELS] and launches[GDG_NKERNELS], and clears the records.
  * gdg_profile(h, 0) stops recording and drops pending records. */
 enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIMIT2 = 4, GDG_K_FINAL = 5,
-       GDG_K_EDGE = 6, GDG_NKERNELS = 7 };
+       GDG_K_EDGE = 6, GDG_K_LSFIX = 7, GDG_NKERNELS = 8 };
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 
 /* Self-test of the FP64 helpers that replace CUDA's division and power on the sweep's hot loops:
  * fn 0 = reciprocal by Newton-Raphson from an FP32 seed, 1 = x^{-1/q} by Newton-Raphson from an FP32
- * seed, 2 = CUDA's 1.0 / x, 3 = CUDA's pow(x, -1.0 / q); x, y: device [n]; 1 <= q <= 16.  Asynchronous
- * on stream.  The tests compare 0 with 2 and 1 with 3 in ulps. */
+ * seed, 2 = CUDA's 1.0 / x, 3 = CUDA's pow(x, -1.0 / q), 4 = the integer-only FP64 -> FP32 -> FP64
+ * conversion pair of the FP32 certificates (truncation to 23 significand bits in the FP32 normal range,
+ * zeros kept, NaN otherwise); x, y: device [n]; 1 <= q <= 16.  Asynchronous on stream.  The tests
+ * compare 0 with 2 and 1 with 3 in ulps, and 4 with the truncation done on the host. */
 int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream);
 
 /* Measured throughput (operations per second over the GPU, timed with CUDA events) of the arithmetic

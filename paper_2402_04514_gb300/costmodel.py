@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge")
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix")
 
 
 @dataclass
@@ -53,6 +53,7 @@ def bytes_per_launch(c: Counts) -> dict:
         + 8 * 3 * n * 2 + 8 * m * n + 8 * n * 3 + 8 * (m + 1) * nnz + 8 * (m + 1) * nb,
         limit2=rowptr + nnz * (4 + 8 + 8 * m) + 8 * m * n * 2 + 8 * 3 * n + 8 * 2 * n + 8 * nnz,
         final=rowptr + nnz * (4 + 8 * 2 + 8 * m) + 8 * m * n * 3 + 8 * n,
+        lsfix=0,  # the deferred line searches: a data-dependent handful of entries, not counted
     )
 
 
@@ -73,6 +74,7 @@ def flops_per_launch(c: Counts) -> dict:
         high=s * (4 + 3 * m) + n * (2 * nl * m + m + 3) + nnz * (4 * m + m + ls) + nb * (3 * m + ls),
         limit2=nnz * (2 * m + 2 + m + ls) + n * 2 * m + nb * (2 * m + m + 2 + ls),
         final=nnz * (2 + 2 * m) + n * 3 * m + nb * (2 + 2 * m),
+        lsfix=0,
     )
 
 

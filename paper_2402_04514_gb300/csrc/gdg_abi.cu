@@ -443,6 +443,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   size_t o_bounds = ar.take<double>(3 * n), o_l1 = ar.take<double>(nnz), o_l1B = ar.take<double>(nb);
   size_t o_l2 = ar.take<double>(nnz), o_l2B = ar.take<double>(nb), o_U1 = ar.take<double>((size_t)m * n);
   size_t o_flags = ar.take<unsigned>(4), o_tau = ar.take<unsigned long long>(1);
+  size_t o_lsq = ar.take<int2>(nnz + nb);
   h->arena_bytes = ar.off;
   cudaError_t ce = cudaMalloc(&h->arena, h->arena_bytes);
   if (ce != cudaSuccess) {
@@ -548,6 +549,8 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   S.l2B = (double*)ptr(o_l2B);
   S.U1 = (double*)ptr(o_U1);
   S.flags = (unsigned*)ptr(o_flags);
+  S.lsq_n = S.flags + 2;
+  S.lsq = (int2*)ptr(o_lsq);
   S.tau_bits = (unsigned long long*)ptr(o_tau);
 
   if (int rc = upload_param_arrays(h, pa); rc != GDG_OK) return fail(rc);
@@ -604,15 +607,22 @@ int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double al
        })) != cudaSuccess)
     return cuda_fail(e);
   if (D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0)) return GDG_OK;
+  // empty the deferred line-search queues of both limiter passes
+  if (D.order == GDG_ORDER_LIMITED && (e = cudaMemsetAsync(S.lsq_n, 0, 2 * sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_fail(e);
   if ((e = timed(h, GDG_K_HIGH, s, [&] {
          return gdg::launch_high(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);
        })) != cudaSuccess)
     return cuda_fail(e);
   if (D.order == GDG_ORDER_HIGH) return GDG_OK;
+  if ((e = timed(h, GDG_K_LSFIX, s, [&] { return gdg::launch_lsfix(dim, D, S, 0, s); })) != cudaSuccess)
+    return cuda_fail(e);
   if ((e = timed(h, GDG_K_LIMIT2, s, [&] { return gdg::launch_limit2(dim, D, S, U_base, alpha, U_out, s); })) !=
       cudaSuccess)
     return cuda_fail(e);
   if (D.passes == 1) return GDG_OK;
+  if ((e = timed(h, GDG_K_LSFIX, s, [&] { return gdg::launch_lsfix(dim, D, S, 1, s); })) != cudaSuccess)
+    return cuda_fail(e);
   if ((e = timed(h, GDG_K_FINAL, s, [&] { return gdg::launch_final(dim, D, S, U_base, alpha, U_out, s); })) !=
       cudaSuccess)
     return cuda_fail(e);
@@ -649,10 +659,18 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count
   else if (nm == "s_min") { src = h->S.bounds + 2 * n; want = n; }
   else if (nm == "l1") { src = h->S.l1; want = nnz; kind = 1; }
   else if (nm == "l2") { src = h->S.l2; want = nnz; kind = 1; }
+  else if (nm == "ls_deferred") { want = 2; kind = 3; }
   else return GDG_EINVAL;
   if (count != want) return GDG_EINVAL;
   cudaError_t e;
   if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
+  if (kind == 3) {  // lengths of the deferred line-search queues of the last stage's two limiter passes
+    unsigned q[2];
+    if ((e = cudaMemcpy(q, h->S.lsq_n, sizeof(q), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+    dst[0] = q[0];
+    dst[1] = q[1];
+    return GDG_OK;
+  }
   std::vector<double> tmp(want);
   if (want > 0 && (e = cudaMemcpy(tmp.data(), src, sizeof(double) * want, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e);

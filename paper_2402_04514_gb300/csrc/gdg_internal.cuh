@@ -82,6 +82,8 @@ struct Scratch {
   double* l2B;     // [nb]
   double* U1;      // [m][n]
   unsigned int* flags;
+  unsigned int* lsq_n;  // [2] lengths of the deferred line-search queues of passes 1 and 2
+  int2* lsq;            // [nnz + nb] deferred line searches of the current pass (ls_defer)
   unsigned long long* tau_bits;  // min of positive doubles via their bit patterns
 };
 
@@ -106,6 +108,7 @@ cudaError_t launch_limit2(int dim, const Dev& D, const Scratch& S, const double*
                           double* Uout, cudaStream_t s);
 cudaError_t launch_final(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha,
                          double* Uout, cudaStream_t s);
+cudaError_t launch_lsfix(int dim, const Dev& D, const Scratch& S, int pass, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------------
 // Device helpers (Euler equations of Sec. 2.2 and the pieces of Sec. 3-5 used by several kernels).
@@ -120,25 +123,39 @@ __device__ __forceinline__ double ipow(double x, int k) {
   return r;
 }
 
-// FP64 -> FP32 by integer operations on the bit pattern (exponent rebias, significand truncated to 23
-// bits: relative error < 2^-23), which keeps the conversion off the FP64 pipe where the hardware
-// conversion costs about 1.6 FMA issue slots.  Values outside the FP32 normal range take the hardware
-// conversion.
+// FP64 -> FP32 by integer operations only (no instruction on the FP64 pipe, where the hardware conversion
+// costs about 1.6 FMA issue slots): exponent rebias and the significand truncated to 23 bits (relative
+// error < 2^-23) for values in the FP32 normal range, +-0 -> +-0.  Every other value (below the FP32
+// normal range, above it, inf, NaN) gives NaN, so that a certificate or a seed computed from it fails its
+// own check and the caller takes its FP64 path.
 __device__ __forceinline__ float d2f_fast(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e <= 0 || e >= 255) return (float)x;
-  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  unsigned r = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e <= 0 || e >= 255) r = (((hi & 0x7fffffffu) | lo) == 0u) ? (hi & 0x80000000u) : 0x7fc00000u;
+  return __uint_as_float(r);
 }
 
-// FP32 -> FP64 by integer operations on the bit pattern (exact for normal numbers).
+// FP32 -> FP64 by integer operations only: exact for normal numbers, zeros, infinities and NaN; an FP32
+// subnormal gives NaN (no caller produces one where a result is needed: the seeds below are normal, and
+// a NaN certificate fails).
 __device__ __forceinline__ double f2d_fast(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 255u) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+  const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, mt = u & 0x7fffffu;
+  unsigned hi = sg | ((e + 896u) << 20) | (mt >> 3);
+  if (e == 255u) hi = sg | 0x7ff00000u | (mt >> 3);
+  if (e == 0u) hi = mt ? 0x7ff80000u : sg;
+  return __hiloint2double((int)hi, (int)(mt << 29));
 }
+
+// |x| and min / max of non-negative doubles through their bit patterns (IEEE order of non-negative
+// numbers is the integer order), and x == +-0; all on the integer pipe.
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_one_bits(double x) { return __double_as_longlong(x) == 0x3ff0000000000000LL; }
 
 // FP64 reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (Muller et al., Handbook of
 // Floating-Point Arithmetic, ch. 5) started from the FP32 reciprocal: the relative error squares at
@@ -264,14 +281,14 @@ __device__ __forceinline__ void boundary_state(const Dev& D, int b, const double
 }
 
 // Per-row context of the line searches from one state U0 (the row's U^L or U^(1)) against the row's
-// bounds: psi(0) in FP64 once per row, and FP32 copies of U0's parts for the increment certificate.
-// The searches run along P = w A (w = the row's 1 / (kappa_i m_i), times 1 - l1 in pass 2), so a point
-// t of the search is U0 + (t w) A.
+// bounds: psi(0) in FP64 once per row, and FP32 copies of U0's parts, of psi(0) and of the distances of
+// rho(U0) to its bounds for the FP32 certificates.  The searches run along P = w A (w = the row's
+// 1 / (kappa_i m_i), times 1 - l1 in pass 2), so a point t of the search is U0 + (t w) A.
 template <int DIM>
 struct LsRow {
   double U0[DIM + 2];
   double rmin, rmax, smin, psi0;
-  float r0, m0[DIM], m0sq, sg0;
+  float r0, m0[DIM], m0sq, sg0, psi0f, dlo, dhi;
 };
 
 template <int DIM>
@@ -293,6 +310,13 @@ __device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double
   for (int k = 0; k < DIM; ++k) c.m0[k] = d2f_fast(U0[1 + k]);
   c.m0sq = d2f_fast(m2);
   c.sg0 = d2f_fast(smin * rg);
+  c.psi0f = d2f_fast(c.psi0);
+  // distances to the density bounds for the FP32 density certificate, kept only when they exceed 1e-6
+  // rho(U0): the FP64 comparisons of the closed form round relative to rho, so a certificate on a smaller
+  // gap could disagree with them (a zero distance sends every search of the row to the FP64 form)
+  const float dlo = d2f_fast(U0[0] - rmin), dhi = d2f_fast(rmax - U0[0]), gap = 1e-6f * c.r0;
+  c.dlo = dlo > gap ? dlo : 0.f;
+  c.dhi = dhi > gap ? dhi : 0.f;
 }
 
 // psi(s) = eps(U0 + s A) - s_min rho(s)^gamma (the entropy constraint of the set B_i, Sec. 5.4,
@@ -329,17 +353,19 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
   return deps - smin * D.gamma * rg * irho * A[0];
 }
 
-// Certifies psi(s) >= 0 from psi(0) (FP64) and the increment dpsi = psi(s) - psi(0) evaluated in FP32 in
+// Certifies psi(s) >= 0 from psi(0) and the increment dpsi = psi(s) - psi(0) evaluated in FP32 in
 // differenced form, so that its error scales with |s A| rather than with |U0|:
 //   dpsi = s A_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
 //   dG = s_min rho0^gamma expm1(gamma log1p(a / rho0)),   a = s A_rho, b = s A_m.
-// Every FP32 operation and conversion has relative error <= 2^-23 and log1pf / expm1f a few ulp, so the
-// FP32 dpsi is within 1e-6 (|s A_E| + S_K + |dG|) of the exact increment, S_K the magnitude of dK's
-// terms; certifying only when psi(0) + dpsi > 1e-4 times that scale leaves a factor 100.  Requires
-// a > -rho0 / 2 (otherwise the caller evaluates psi in FP64).
+// sf is s in FP32 with relative error at most 3 2^-23.  Every other FP32 operation and conversion has
+// relative error <= 2^-23 and log1pf / expm1f a few ulp, so the FP32 dpsi is within 2e-6 S of the exact
+// increment, S = |s A_E| + S_K + |dG| and S_K the magnitude of dK's terms.  With t = psi0f + dpsi in FP32
+// (psi0f = psi(0) truncated to FP32, relative error < 2^-23), certifying only when
+// t > 1e-4 S + 1e-6 |psi0f| leaves a factor of 50 on every error term, so psi(s) > 0 exactly.  Requires
+// a > -rho0 / 2 (otherwise the caller evaluates psi in FP64); any NaN (an input outside the FP32 normal
+// range) fails the final comparison.
 template <int DIM>
-__device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* A, double s) {
-  float sf = d2f_fast(s);
+__device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* A, float sf) {
   float a = sf * d2f_fast(A[0]);
   if (!(a > -0.5f * c.r0)) return false;
   float mb = 0.f, bb = 0.f, nb2 = 0.f;
@@ -358,31 +384,56 @@ __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, 
   float dG = c.sg0 * expm1f((float)D.gamma * log1pf(a / c.r0));
   float dpsi = eE - dK - dG;
   float scale = fabsf(eE) + SK + fabsf(dG);
-  double tot = c.psi0 + f2d_fast(dpsi);
-  return tot > 1e-4 * f2d_fast(scale) && tot > 0.0;
+  float t = c.psi0f + dpsi;
+  return t > 1e-4f * scale + 1e-6f * fabsf(c.psi0f);
 }
 
 // Largest l in [0, 1] with U0 + l P in B_i, P = w A (Sec. 5.4, eq. (ConvexScheme), Lemma
-// ConsInvariants): closed form for the density bounds, then, if the entropy constraint fails at
-// l_rho, a bracketed iteration on the concave psi: the chord root stays feasible, the tangent root
-// from the infeasible end stays infeasible (bisection when rounding keeps both from moving); stops
-// when the bracket is at most ls_tol wide and returns the feasible end.  The FP32 certificate only
-// skips FP64 evaluations whose outcome it proves; the result is that of the FP64 search.
+// ConsInvariants), in two parts.  The head takes the closed form for the density bounds and decides the
+// common cases: the entropy constraint holds at l_rho (proved by the FP32 certificate, else by psi in FP64),
+// or psi(0) < 0 (roundoff) and l = 0.  It returns false when psi(l_rho) < 0 <= psi(0); then the tail runs
+// a bracketed iteration on the concave psi from [0, l_rho]: the chord root stays feasible, the tangent root
+// from the infeasible end stays infeasible (bisection when rounding keeps both from moving); it stops when
+// the bracket is at most ls_tol wide and returns the feasible end.  The FP32 certificate only skips FP64
+// evaluations whose outcome it proves; the result is that of the FP64 search.
 template <int DIM>
-__device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c, const double* A, double w) {
+__device__ __forceinline__ bool line_search_head(const Dev& D, const LsRow<DIM>& c, const double* A, double w,
+                                                 float wf, double* l_out, double* fb_out) {
+  // Density bounds.  The common case, rho(U0) + w A_rho inside [rho_min, rho_max] so that l_rho = 1, is
+  // proved in FP32 (wf = w in FP32): the products and conversions have relative error below 4e-7, so a
+  // relative margin of 1e-6 on both sides leaves the exact distance to the bound above 8e-7 times a gap
+  // of at least 1e-6 rho (ls_row), far beyond the FP64 rounding of the closed form's comparisons, which
+  // therefore agree with it.
+  const float pr = wf * d2f_fast(A[0]);
+  const bool inside = pr >= 0.f ? pr * 1.000001f < c.dhi * 0.999999f : -pr * 1.000001f < c.dlo * 0.999999f;
+  double l = 1.0;
+  float sf = wf;
+  if (!inside) {
+    const double Pr = w * A[0];
+    if (c.U0[0] + Pr < c.rmin) l = (c.rmin - c.U0[0]) / Pr;
+    if (c.U0[0] + Pr > c.rmax) l = (c.rmax - c.U0[0]) / Pr;
+    if (!(l > 0.0)) l = 0.0;
+    if (l > 1.0) l = 1.0;
+    sf = d2f_fast(l * w);
+  }
+  *l_out = l;
+  if (ls_certified<DIM>(D, c, A, sf)) return true;
+  const double fb = ls_psi<DIM>(D, c.U0, A, l * w, c.smin);
+  *fb_out = fb;
+  if (fb >= 0.0) return true;
+  if (c.psi0 < 0.0) {
+    *l_out = 0.0;
+    return true;
+  }
+  return false;
+}
+
+template <int DIM>
+__device__ double line_search_tail(const Dev& D, const LsRow<DIM>& c, const double* A, double w,
+                                                double l, double fb) {
   const double* U0 = c.U0;
   const double smin = c.smin;
-  const double Pr = w * A[0];
-  double l = 1.0;
-  if (U0[0] + Pr < c.rmin) l = (c.rmin - U0[0]) / Pr;
-  if (U0[0] + Pr > c.rmax) l = (c.rmax - U0[0]) / Pr;
-  if (!(l > 0.0)) l = 0.0;
-  if (l > 1.0) l = 1.0;
-  if (ls_certified<DIM>(D, c, A, l * w)) return l;
-  double fb = ls_psi<DIM>(D, U0, A, l * w, smin);
-  if (fb >= 0.0) return l;
   double fa = c.psi0;
-  if (fa < 0.0) return 0.0;
   double a = 0.0, b = l;
   for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {
     bool moved = false;
@@ -407,6 +458,15 @@ __device__ __forceinline__ double line_search(const Dev& D, const LsRow<DIM>& c,
     }
   }
   return a;
+}
+
+// The searches that need the tail are rare (well under 1% of the entries) but take ~10 iterations, and a
+// lane that iterates holds up its whole warp; the sweep kernels therefore queue them (entry, row) and
+// k_lsfix runs the tails with every lane busy.  Queue item: x = CSR entry e, or -(b + 1) for boundary
+// entry b; y = row i.
+__device__ __forceinline__ void ls_defer(const Scratch& S, int pass, int code, int i) {
+  const unsigned k = atomicAdd(S.lsq_n + pass, 1u);
+  S.lsq[k] = make_int2(code, i);
 }
 
 template <int DIM>

@@ -19,7 +19,8 @@ constexpr int kMaxBlock = 160;
 //     its stencil neighbours and node i's own boundary bar states;
 //  4. A_ij = tau (d^H_ij - d^L_ij)(U_j - U_i) - m_ij (dU^H_j - dU^H_i) and
 //     A_i^{d,k} = tau (d^{d,H} - d^{d,L})(U^{d,k} - U_i) (Sec. 5.3, eq. (HighLowOrderIdentity)), and the
-//     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i).
+//     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i); the rare
+//     searches that need the bracketed iteration are queued for k_lsfix.
 // With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
 template <int DIM>
 __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const double* __restrict__ U,
@@ -37,23 +38,23 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
   double Ni = 0.0;
   if (valid) {
     load_state<DIM>(U, D.n, i, Ui);
-    Ni = fabs(S.N[i]);
+    Ni = abs_bits(S.N[i]);
     double rhs[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) rhs[q] = S.RHSL[(size_t)q * n + i];
+    // min / max of non-negative values and the m_ij-only test on the integer pipe
     for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-      double dl = S.dL[e];
-      if (D.cnorm[e] == 0.0) continue;
-      int j = D.col[e];
-      double Nj = fabs(S.N[j]);
-      double dev = dl * fmin(D.c_ev * fmax(Ni, Nj), 1.0);
-      double dh = fmax(D.mu[e] * dl, dev);
-      double dd = dh - dl;
+      if (is_zero_bits(D.cnorm[e])) continue;  // m_ij-only entry: not in I(i)
+      const double dl = S.dL[e];
+      const int j = D.col[e];
+      const double dev = dl * pmin(D.c_ev * pmax(Ni, abs_bits(S.N[j])), 1.0);
+      const double dd = pmax(D.mu[e] * dl, dev) - dl;
+      const double td = tau * dd;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
-        double v = dd * (U[(size_t)q * n + j] - Ui[q]);
-        rhs[q] -= v;
-        S.A[(size_t)q * D.nnz + e] = tau * v;  // viscous part of A_ij, completed below
+        const double du = U[(size_t)q * n + j] - Ui[q];
+        rhs[q] = fma(-dd, du, rhs[q]);
+        S.A[(size_t)q * D.nnz + e] = td * du;  // viscous part of A_ij, completed below
       }
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
       for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
       boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
       double dl = S.dB[b];
-      double dd = (fmax(D.muB[i], fmin(D.c_ev * Ni, 1.0)) - 1.0) * dl;
+      double dd = (pmax(D.muB[i], pmin(D.c_ev * Ni, 1.0)) - 1.0) * dl;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         rhs[q] -= dd * (UB[q] - Ui[q]);
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
     sl = pmin(sl, S.bbar[(size_t)D.nb + b]);
   }
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-    if (D.cnorm[e] == 0.0) continue;
+    if (is_zero_bits(D.cnorm[e])) continue;
     int j = D.col[e];
     lo = pmin(lo, S.agg[j]);
     hi = pmax(hi, S.agg[n + j]);
@@ -136,13 +137,14 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
   LsRow<DIM> ls;
   ls_row<DIM>(D, ls, UL, rmin, rmax, smin);
   const double ikm = D.inv_km[i];
+  const float ikmf = d2f_fast(ikm);
   const int nl = D.n_loc;
   const int elem = i / nl;
   const int t0 = t - (i % nl);
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int j = D.col[e];
     double A[M];
-    const bool stencil = D.cnorm[e] != 0.0;
+    const bool stencil = !is_zero_bits(D.cnorm[e]);
     const bool same = (j / nl) == elem;
     const double mij = same ? D.mij[e] : 0.0;
     const int tj = t0 + (j % nl);
@@ -153,13 +155,21 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
       A[q] = a;
       S.A[(size_t)q * D.nnz + e] = a;
     }
-    S.l1[e] = line_search<DIM>(D, ls, A, ikm);
+    double l, fb;
+    if (line_search_head<DIM>(D, ls, A, ikm, ikmf, &l, &fb))
+      S.l1[e] = l;
+    else
+      ls_defer(S, 0, e, i);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double A[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) A[q] = S.AB[(size_t)q * D.nb + b];
-    S.l1B[b] = line_search<DIM>(D, ls, A, ikm);
+    double l, fb;
+    if (line_search_head<DIM>(D, ls, A, ikm, ikmf, &l, &fb))
+      S.l1B[b] = l;
+    else
+      ls_defer(S, 0, -(b + 1), i);
   }
 }
 

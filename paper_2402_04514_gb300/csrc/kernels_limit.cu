@@ -1,5 +1,7 @@
 // Sweeps C and D: symmetrisation of the limiter coefficients, the limited updates of Sec. 5.3,
 // eq. (LimitedScheme), and the second limiter pass of Sec. 6.1.  One thread per row.
+#include <algorithm>
+
 #include "gdg_internal.cuh"
 
 namespace gdg {
@@ -23,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
   const int r0 = D.row_ptr[i], r1 = D.row_ptr[i + 1];
   for (int e = r0; e < r1; ++e) {
-    double l = fmin(S.l1[e], S.l1[D.tr[e]]);
+    double l = pmin(S.l1[e], S.l1[D.tr[e]]);  // limiter coefficients are in [0, 1]: integer min
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += l * S.A[q * nnz + e];
   }
@@ -49,26 +51,67 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
   const double ikm = D.inv_km[i];
   // an entry with l1 = 1 has no remainder: its l2 multiplies zero and is set to 1 without a search
   for (int e = r0; e < r1; ++e) {
-    double rem = 1.0 - fmin(S.l1[e], S.l1[D.tr[e]]);
-    if (rem == 0.0) {
+    const double l1s = pmin(S.l1[e], S.l1[D.tr[e]]);
+    if (is_one_bits(l1s)) {
       S.l2[e] = 1.0;
       continue;
     }
+    const double w = (1.0 - l1s) * ikm;
     double A[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) A[q] = S.A[q * nnz + e];
-    S.l2[e] = line_search<DIM>(D, ls, A, rem * ikm);
+    double l, fb;
+    if (line_search_head<DIM>(D, ls, A, w, d2f_fast(w), &l, &fb))
+      S.l2[e] = l;
+    else
+      ls_defer(S, 1, e, i);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    double rem = 1.0 - S.l1B[b];
-    if (rem == 0.0) {
+    if (is_one_bits(S.l1B[b])) {
       S.l2B[b] = 1.0;
       continue;
     }
+    const double w = (1.0 - S.l1B[b]) * ikm;
     double A[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) A[q] = S.AB[q * nb + b];
-    S.l2B[b] = line_search<DIM>(D, ls, A, rem * ikm);
+    double l, fb;
+    if (line_search_head<DIM>(D, ls, A, w, d2f_fast(w), &l, &fb))
+      S.l2B[b] = l;
+    else
+      ls_defer(S, 1, -(b + 1), i);
+  }
+}
+
+// The deferred line searches of one limiter pass (pass 0: from U^L with P = A / (kappa_i m_i), written to
+// l1; pass 1: from U^(1) with P = (1 - l1_ij) A / (kappa_i m_i), written to l2).  One thread per queued
+// entry, grid-stride over the queue: every lane runs a bracketed iteration.  The row context, l_rho and
+// psi(l_rho) are recomputed from the same stored values by the same code as in the queuing kernel.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_lsfix(Dev D, Scratch S, int pass) {
+  constexpr int M = DIM + 2;
+  const unsigned count = S.lsq_n[pass];
+  const size_t n = D.n, nnz = D.nnz, nb = D.nb;
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const int2 it = S.lsq[k];
+    const int i = it.y;
+    const bool bnd = it.x < 0;
+    const int e = bnd ? -(it.x + 1) : it.x;
+    double U0[M], A[M];
+    const double* Usrc = pass == 0 ? S.UL : S.U1;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      U0[q] = Usrc[q * n + i];
+      A[q] = bnd ? S.AB[q * nb + e] : S.A[q * nnz + e];
+    }
+    double w = D.inv_km[i];
+    if (pass == 1) w = (1.0 - (bnd ? S.l1B[e] : pmin(S.l1[e], S.l1[D.tr[e]]))) * w;
+    LsRow<DIM> ls;
+    ls_row<DIM>(D, ls, U0, S.bounds[i], S.bounds[n + i], S.bounds[2 * n + i]);
+    double l, fb;
+    if (!line_search_head<DIM>(D, ls, A, w, d2f_fast(w), &l, &fb)) l = line_search_tail<DIM>(D, ls, A, w, l, fb);
+    double* dst = pass == 0 ? (bnd ? S.l1B : S.l1) : (bnd ? S.l2B : S.l2);
+    dst[e] = l;
   }
 }
 
@@ -86,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_final(Dev D, Scratch S, const doub
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int t = D.tr[e];
-    double w = fmin(S.l2[e], S.l2[t]) * (1.0 - fmin(S.l1[e], S.l1[t]));
+    double w = pmin(S.l2[e], S.l2[t]) * (1.0 - pmin(S.l1[e], S.l1[t]));
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += w * S.A[q * nnz + e];
   }
@@ -120,7 +163,24 @@ cudaError_t final_impl(const Dev& D, const Scratch& S, const double* Ubase, doub
   return cudaGetLastError();
 }
 
+template <int DIM>
+cudaError_t lsfix_impl(const Dev& D, const Scratch& S, int pass, cudaStream_t s) {
+  if (D.n == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the queue length is only known on the device: a grid of 4 blocks per SM strides over it
+  const long long cap = ((long long)D.nnz + D.nb + 127) / 128;
+  const int blocks = (int)std::max(1LL, std::min<long long>(4LL * std::max(1, sms), cap));
+  k_lsfix<DIM><<<blocks, 128, 0, s>>>(D, S, pass);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_lsfix(int dim, const Dev& D, const Scratch& S, int pass, cudaStream_t s) {
+  GDG_DISPATCH(dim, lsfix_impl, D, S, pass, s);
+}
 
 cudaError_t launch_limit2(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha, double* Uout,
                           cudaStream_t s) {

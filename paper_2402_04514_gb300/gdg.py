@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge")  # GDG_K_* order
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix")  # GDG_K_* order
 BC_SLIP, BC_DIRICHLET = 0, 1
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 
@@ -236,7 +236,7 @@ class Solver:
     def export(self, name: str, stream=None) -> np.ndarray:
         m, n, nnz, nb = self.m, self.n, self.nnz, self.nb
         shapes = dict(dL=(nnz,), dB=(nb,), N=(n,), UL=(m, n), U1=(m, n), A=(m, nnz), rho_min=(n,), rho_max=(n,),
-                      s_min=(n,), l1=(nnz,), l2=(nnz,))
+                      s_min=(n,), l1=(nnz,), l2=(nnz,), ls_deferred=(2,))
         out = np.empty(shapes[name])
         _check(load().gdg_debug_export(self._h, name.encode(), out.ctypes.data if out.size else None, out.size,
                                        _stream(stream)), f"gdg_debug_export({name})")
