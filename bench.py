@@ -3,8 +3,8 @@
 
 Workload (default): 2D Euler, gamma = 1.4, dG Q2 on 1024 x 1024 uniform quads of [0,1]^2 (9,437,184
 nodes), four-quadrant Riemann data drawn from default_rng(0), slip walls, full limited scheme (two limiter
-passes), CFL 0.5.  One step = one SSP-RK3 step = gdg_max_dt + 3 gdg_stage calls, i.e. 3 DoF-stage
-updates per node.  Inputs are synthetic and resident in HBM; the working set (several GB) is larger than
+passes), CFL 0.5.  One step = one SSP-RK3 step = one gdg_ssprk3_step call (the time step is reduced
+on the device from the first stage's sweep, no host round trip), i.e. 3 DoF-stage updates per node.  Inputs are synthetic and resident in HBM; the working set (several GB) is larger than
 L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -127,7 +127,7 @@ def config_block(args, n):
     spec = WORKLOADS[args.workload]
     return {"workload": args.workload, "mesh": f"{spec['N']}x{spec['N']} quads", "degree": spec["k"],
             "dofs_per_gpu": n, "gamma": 1.4, "cfl": 0.5, "scheme": "convex-limited, 2 limiter passes",
-            "step": "SSP-RK3 step (max_dt + 3 stages)", "parallelism": f"replicas x{args.gpus}",
+            "step": "SSP-RK3 step (gdg_ssprk3_step: tau chosen on the device + 3 stages)", "parallelism": f"replicas x{args.gpus}",
             "l2": "no flush: working set larger than L2 (129 MB)"}
 
 
@@ -178,20 +178,17 @@ def main():
     P, U0 = make_problem(spec)
     counts = costmodel.Counts.of(P)
     solver = Solver(P)
+    solver.set_clock(0.0, float("inf"), 0.5)
     stream = torch.cuda.current_stream()
     U = torch.from_numpy(U0).cuda()
-    bufs = (torch.empty_like(U), torch.empty_like(U))
-    nxt = torch.empty_like(U)
+    work = (torch.empty_like(U), torch.empty_like(U))
     n = P.n
 
-    def step(Uc, out):
-        tau = solver.max_dt(Uc, 0.5)
-        solver.ssprk3_step(Uc, tau, bufs, out)
-        return out
+    def step():
+        solver.step(U, work)  # gdg_ssprk3_step: tau chosen on the device, U updated in place
 
     for _ in range(args.warmup):
-        step(U, nxt)
-        U, nxt = nxt, U
+        step()
     torch.cuda.synchronize()
     assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
 
@@ -205,8 +202,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(U, nxt)
-        U, nxt = nxt, U
+        step()
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -263,8 +259,8 @@ def main():
         e0.record(stream)
         for _ in range(args.steps):
             U.copy_(hin, non_blocking=True)
-            step(U, nxt)
-            hout.copy_(nxt, non_blocking=True)
+            step()
+            hout.copy_(U, non_blocking=True)
             stream.synchronize()
             hin, hout = hout, hin
         e1.record(stream)

@@ -125,11 +125,31 @@ int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, 
 
 /* One forward-Euler stage with step tau followed by the SSP Runge-Kutta combination:
  *   U_out = alpha * U_base + (1 - alpha) * FE(U_in)        (U_base may be NULL when alpha == 0).
- * U_in, U_base, U_out: device [m][n]; U_out must not alias U_in or U_base.  bdata as in gdg_max_dt,
- * evaluated at the stage time.  Asynchronous on stream; allocates nothing; inadmissible input and a
- * CFL violation set sticky flags (gdg_status), never trap. */
+ * U_in, U_base, U_out: device [m][n]; U_out must not alias U_in (GDG_EINVAL); it may equal U_base (each
+ * node reads its base value before its output is written).  bdata as in gdg_max_dt, evaluated at the
+ * stage time.  Asynchronous on stream; allocates nothing; inadmissible input and a CFL violation set
+ * sticky flags (gdg_status), never trap. */
 int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double alpha, double tau,
               const double* bdata, double* U_out, void* stream);
+
+/* One whole SSP-RK3 step (Sec. 6.2, Shu-Osher form) with the time step chosen and kept on the device:
+ *   tau = min(cfl * min_i (-m_i / (2 d_ii(U))), t_end - t)     (Sec. 3.3, eq. (MaxCFLdt); 0 once t >= t_end)
+ *   U1 = FE_tau(U) -> T1;  U2 = 3/4 U + 1/4 FE_tau(U1) -> T2;  U <- 1/3 U + 2/3 FE_tau(U2)  (in place)
+ * then t += tau.  cfl, t and t_end are the handle's clock (gdg_clock_set; t = 0, t_end = +inf, cfl = 0.5
+ * after gdg_setup).  The bound is reduced from the first stage's edge sweep, so the step does no work
+ * twice and never waits for the host: it is asynchronous on stream and allocates nothing.  U, T1, T2:
+ * device [m][n], distinct (GDG_EINVAL otherwise); T1 and T2 are workspace.  bdata: Dirichlet data as in
+ * gdg_stage, used unchanged at the three stage times (for time-dependent data call gdg_stage).
+ * Flags as gdg_stage. */
+int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream);
+
+/* Sets the clock of gdg_ssprk3_step: current time t, final time t_end >= t (+inf: no end), CFL number
+ * cfl > 0; resets the step count.  Synchronises the stream. */
+int gdg_clock_set(gdg_handle* h, double t, double t_end, double cfl, void* stream);
+
+/* Reads the clock: current time, tau of the last step, completed steps (any pointer may be NULL).
+ * Synchronises the stream. */
+int gdg_clock_get(gdg_handle* h, double* t, double* tau, int64_t* steps, void* stream);
 
 /* Reads (and with clear != 0 resets) the sticky device flags GDG_FLAG_*; synchronises the stream. */
 int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream);
@@ -142,13 +162,13 @@ int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream);
  * the stream. */
 int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t count, void* stream);
 
-/* Kernel timing for measurement.  With gdg_profile(h, 1) every kernel launch of gdg_stage and
- * gdg_max_dt is bracketed by CUDA events recorded on the launching stream (no synchronisation is
+/* Kernel timing for measurement.  With gdg_profile(h, 1) every kernel launch of gdg_stage,
+ * gdg_ssprk3_step and gdg_max_dt is bracketed by CUDA events recorded on the launching stream (no synchronisation is
  * added).  gdg_profile_read synchronises, accumulates the elapsed time of each kernel of the sweep
  * (indices GDG_K_*) into total_ms[GDG_NKERNELS] and launches[GDG_NKERNELS], and clears the records.
  * gdg_profile(h, 0) stops recording and drops pending records. */
 enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIMIT2 = 4, GDG_K_FINAL = 5,
-       GDG_K_EDGE = 6, GDG_K_LSFIX = 7, GDG_NKERNELS = 8 };
+       GDG_K_EDGE = 6, GDG_K_LSFIX = 7, GDG_K_TAU = 8, GDG_K_CLOCK = 9, GDG_NKERNELS = 10 };
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 

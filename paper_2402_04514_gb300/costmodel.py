@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix")
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock")
 
 
 @dataclass
@@ -54,6 +54,8 @@ def bytes_per_launch(c: Counts) -> dict:
         limit2=rowptr + nnz * (4 + 8 + 8 * m) + 8 * m * n * 2 + 8 * 3 * n + 8 * 2 * n + 8 * nnz,
         final=rowptr + nnz * (4 + 8 * 2 + 8 * m) + 8 * m * n * 3 + 8 * n,
         lsfix=0,  # the deferred line searches: a data-dependent handful of entries, not counted
+        tau=rowptr + 8 * nnz + 8 * n + 8 * (m + 6) * nb,
+        clock=0,
     )
 
 
@@ -75,6 +77,8 @@ def flops_per_launch(c: Counts) -> dict:
         limit2=nnz * (2 * m + 2 + m + ls) + n * 2 * m + nb * (2 * m + m + 2 + ls),
         final=nnz * (2 + 2 * m) + n * 3 * m + nb * (2 + 2 * m),
         lsfix=0,
+        tau=nnz + 2 * n + nb * (lam + vel + 10),
+        clock=0,
     )
 
 

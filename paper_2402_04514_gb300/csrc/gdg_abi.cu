@@ -40,6 +40,8 @@ struct gdg_handle {
   bool profiling = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  int sms = 1;                   // multiprocessors of the device (grid of the deferred line searches)
+  gdg::Clock* clk = nullptr;     // device clock of the fused step (in the arena)
 };
 
 namespace {
@@ -444,6 +446,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   size_t o_l2 = ar.take<double>(nnz), o_l2B = ar.take<double>(nb), o_U1 = ar.take<double>((size_t)m * n);
   size_t o_flags = ar.take<unsigned>(4), o_tau = ar.take<unsigned long long>(1);
   size_t o_lsq = ar.take<int2>(nnz + nb);
+  size_t o_clk = ar.take<gdg::Clock>(1);
   h->arena_bytes = ar.off;
   cudaError_t ce = cudaMalloc(&h->arena, h->arena_bytes);
   if (ce != cudaSuccess) {
@@ -551,6 +554,17 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   S.flags = (unsigned*)ptr(o_flags);
   S.lsq_n = S.flags + 2;
   S.lsq = (int2*)ptr(o_lsq);
+  h->clk = (gdg::Clock*)ptr(o_clk);
+  {
+    gdg::Clock c0{};
+    c0.tau_bits = gdg::kTauNone;
+    c0.t = 0.0;
+    c0.t_end = INFINITY;
+    c0.cfl = 0.5;
+    if ((ce = cudaMemcpy(h->clk, &c0, sizeof(c0), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(cuda_fail(ce));
+  }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->sms < 1) h->sms = 1;
   S.tau_bits = (unsigned long long*)ptr(o_tau);
 
   if (int rc = upload_param_arrays(h, pa); rc != GDG_OK) return fail(rc);
@@ -566,15 +580,32 @@ int gdg_set_params(gdg_handle* h, const gdg_params* params) {
   return upload_param_arrays(h, pa);
 }
 
+static gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Ubase, double* Uout,
+                         const double* bdata, double alpha, double tau, gdg::Clock* clk) {
+  gdg::Ctx c{};
+  c.D = h->D;
+  c.S = h->S;
+  c.U = U;
+  c.Ubase = Ubase;
+  c.Uout = Uout;
+  c.bdata = bdata;
+  c.alpha = alpha;
+  c.tau = tau;
+  c.clk = clk;
+  return c;
+}
+
 int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out, void* stream) {
   if (!h || (!U && h->n > 0) || !tau_out || !(cfl > 0)) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->S.tau_bits, 0x7f, sizeof(unsigned long long), s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_prim(h->dim, h->D, h->S, U, s); })) != cudaSuccess)
+  const gdg::Ctx c = make_ctx(h, U, nullptr, nullptr, bdata, 0.0, 0.0, nullptr);
+  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_one(gdg::KN_PRIM, h->dim, c, 0, h->sms, s); })) !=
+      cudaSuccess)
     return cuda_fail(e);
-  if ((e = timed(h, GDG_K_MAXDT, s, [&] { return gdg::launch_maxdt(h->dim, h->D, h->S, U, bdata, s); })) !=
+  if ((e = timed(h, GDG_K_MAXDT, s, [&] { return gdg::launch_one(gdg::KN_MAXDT, h->dim, c, 0, h->sms, s); })) !=
       cudaSuccess)
     return cuda_fail(e);
   unsigned long long bits = 0;
@@ -587,46 +618,86 @@ int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, 
   return GDG_OK;
 }
 
+// The kernels of one stage (Sec. 6.1): primitives, edge sweep, [the fused step's tau bound], sweep A,
+// then, as the order and the number of limiter passes ask, the element sweep, the deferred line searches
+// of pass 1, sweep C, those of pass 2 and sweep D.
+static int run_stage(gdg_handle* h, const gdg::Ctx& c, bool with_tau, cudaStream_t s) {
+  const int dim = h->dim;
+  const gdg::Dev& D = h->D;
+  cudaError_t e;
+  auto go = [&](int id, int kern, int arg) {
+    return timed(h, id, s, [&] { return gdg::launch_one(kern, dim, c, arg, h->sms, s); });
+  };
+  const bool low_only = D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0);
+  if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = go(GDG_K_EDGE, gdg::KN_EDGE, 0)) != cudaSuccess) return cuda_fail(e);
+  if (with_tau && (e = go(GDG_K_TAU, gdg::KN_TAU, 0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = go(GDG_K_LOW, gdg::KN_LOW, low_only ? 1 : 0)) != cudaSuccess) return cuda_fail(e);
+  if (low_only) return GDG_OK;
+  if ((e = go(GDG_K_HIGH, gdg::KN_HIGH, 0)) != cudaSuccess) return cuda_fail(e);
+  if (D.order == GDG_ORDER_HIGH) return GDG_OK;
+  if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = go(GDG_K_LIMIT2, gdg::KN_LIMIT2, D.passes == 1 ? 1 : 0)) != cudaSuccess) return cuda_fail(e);
+  if (D.passes == 1) return GDG_OK;
+  if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 1)) != cudaSuccess) return cuda_fail(e);
+  if ((e = go(GDG_K_FINAL, gdg::KN_FINAL, 0)) != cudaSuccess) return cuda_fail(e);
+  return GDG_OK;
+}
+
 int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double alpha, double tau,
               const double* bdata, double* U_out, void* stream) {
   if (!h || ((!U_in || !U_out) && h->n > 0) || !(tau >= 0) || !std::isfinite(tau)) return GDG_EINVAL;
-  if (h->n > 0 && (U_out == U_in || (U_base && U_out == U_base))) return GDG_EINVAL;
+  if (h->n > 0 && U_out == U_in) return GDG_EINVAL;
   if (alpha != 0.0 && !U_base && h->n > 0) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  const gdg::Ctx c = make_ctx(h, U_in, U_base, U_out, bdata, alpha, tau, nullptr);
+  return run_stage(h, c, false, (cudaStream_t)stream);
+}
+
+int gdg_clock_set(gdg_handle* h, double t, double t_end, double cfl, void* stream) {
+  if (!h || !std::isfinite(t) || !(t_end >= t) || !(cfl > 0) || !std::isfinite(cfl)) return GDG_EINVAL;
+  gdg::Clock c0{};
+  c0.tau_bits = gdg::kTauNone;
+  c0.t = t;
+  c0.t_end = t_end;
+  c0.cfl = cfl;
+  c0.tau = 0.0;
+  c0.steps = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  const int dim = h->dim;
-  const Dev& D = h->D;
   cudaError_t e;
-  const Scratch& S = h->S;
-  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_prim(dim, D, S, U_in, s); })) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = timed(h, GDG_K_EDGE, s, [&] { return gdg::launch_edge(dim, D, S, U_in, s); })) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = timed(h, GDG_K_LOW, s, [&] {
-         return gdg::launch_low(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);
-       })) != cudaSuccess)
-    return cuda_fail(e);
-  if (D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0)) return GDG_OK;
-  // empty the deferred line-search queues of both limiter passes
-  if (D.order == GDG_ORDER_LIMITED && (e = cudaMemsetAsync(S.lsq_n, 0, 2 * sizeof(unsigned), s)) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = timed(h, GDG_K_HIGH, s, [&] {
-         return gdg::launch_high(dim, D, S, U_in, bdata, tau, U_base, alpha, U_out, s);
-       })) != cudaSuccess)
-    return cuda_fail(e);
-  if (D.order == GDG_ORDER_HIGH) return GDG_OK;
-  if ((e = timed(h, GDG_K_LSFIX, s, [&] { return gdg::launch_lsfix(dim, D, S, 0, s); })) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = timed(h, GDG_K_LIMIT2, s, [&] { return gdg::launch_limit2(dim, D, S, U_base, alpha, U_out, s); })) !=
-      cudaSuccess)
-    return cuda_fail(e);
-  if (D.passes == 1) return GDG_OK;
-  if ((e = timed(h, GDG_K_LSFIX, s, [&] { return gdg::launch_lsfix(dim, D, S, 1, s); })) != cudaSuccess)
-    return cuda_fail(e);
-  if ((e = timed(h, GDG_K_FINAL, s, [&] { return gdg::launch_final(dim, D, S, U_base, alpha, U_out, s); })) !=
-      cudaSuccess)
-    return cuda_fail(e);
+  if ((e = cudaMemcpyAsync(h->clk, &c0, sizeof(c0), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
   return GDG_OK;
+}
+
+int gdg_clock_get(gdg_handle* h, double* t, double* tau, int64_t* steps, void* stream) {
+  if (!h) return GDG_EINVAL;
+  gdg::Clock c0{};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&c0, h->clk, sizeof(c0), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+  if (t) *t = c0.t;
+  if (tau) *tau = c0.tau;
+  if (steps) *steps = c0.steps;
+  return GDG_OK;
+}
+
+int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream) {
+  if (!h || ((!U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
+  if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Shu-Osher form of SSP-RK3 (Sec. 6.2): U1 = FE(U); U2 = 3/4 U + 1/4 FE(U1); U <- 1/3 U + 2/3 FE(U2),
+  // the last in place (each node reads its base value before writing it)
+  const gdg::Ctx c1 = make_ctx(h, U, nullptr, T1, bdata, 0.0, 0.0, h->clk);
+  const gdg::Ctx c2 = make_ctx(h, T1, U, T2, bdata, 0.75, 0.0, h->clk);
+  const gdg::Ctx c3 = make_ctx(h, T2, U, U, bdata, 1.0 / 3.0, 0.0, h->clk);
+  if (int rc = run_stage(h, c1, true, s); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, c2, false, s); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, c3, false, s); rc != GDG_OK) return rc;
+  cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, s); });
+  return e == cudaSuccess ? GDG_OK : cuda_fail(e);
 }
 
 int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream) {

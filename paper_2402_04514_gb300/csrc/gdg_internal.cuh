@@ -95,20 +95,129 @@ struct Scratch {
     default: return cudaErrorInvalidValue; \
   }
 
-// Kernel launchers (kernels_low.cu, kernels_high.cu, kernels_limit.cu); dim in 1..3.
-cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s);
-cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
-                         cudaStream_t s);
-cudaError_t launch_edge(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s);
-cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
-                       double tau, const double* Ubase, double alpha, double* Uout, cudaStream_t s);
-cudaError_t launch_high(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
-                        double tau, const double* Ubase, double alpha, double* Uout, cudaStream_t s);
-cudaError_t launch_limit2(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha,
-                          double* Uout, cudaStream_t s);
-cudaError_t launch_final(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha,
-                         double* Uout, cudaStream_t s);
-cudaError_t launch_lsfix(int dim, const Dev& D, const Scratch& S, int pass, cudaStream_t s);
+// Time state of one instance for the fused SSP-RK3 step (gdg_ssprk3_step and batches): the step's bound
+// min_i m_i / (2 |d_ii|) (Sec. 3.3, eq. (MaxCFLdt)) is reduced into tau_bits, and every kernel of the step
+// takes tau = min(cfl * bound, t_end - t) (0 once t >= t_end) from it, so the step needs no host round
+// trip.  k_clock advances t by tau at the end of the step.
+struct Clock {
+  unsigned long long tau_bits;  // bit pattern of the bound (positive doubles order like uint64); kTauNone: none
+  double t, t_end, cfl;
+  double tau;                   // tau of the last completed step
+  long long steps;              // completed steps
+};
+constexpr unsigned long long kTauNone = 0x7f7f7f7f7f7f7f7fULL;
+
+// Everything one kernel of a stage needs for one instance.
+struct Ctx {
+  Dev D;
+  Scratch S;
+  const double* U;      // stage input U_in [m][n]
+  const double* Ubase;  // SSP-RK base (read only where alpha != 0)
+  double* Uout;         // stage output; may equal Ubase (each node reads its base before writing itself)
+  const double* bdata;  // Dirichlet data [m][nb] or null
+  double alpha;         // U_out = alpha U_base + (1 - alpha) FE(U_in)
+  double tau;           // the stage's tau when clk is null
+  Clock* clk;           // device clock of the fused step, or null
+};
+
+// An instance whose clock has reached t_end: every kernel of the fused step returns at once, so the
+// step leaves its state untouched (bit for bit) and costs only the launches.
+__device__ __forceinline__ bool finished(const Ctx& c) { return c.clk && !(c.clk->t < c.clk->t_end); }
+
+__device__ __forceinline__ double stage_tau(const Ctx& c) {
+  if (!c.clk) return c.tau;
+  const unsigned long long b = c.clk->tau_bits;
+  if (b == kTauNone) return 0.0;
+  const double v = c.clk->cfl * __longlong_as_double((long long)b);
+  const double rem = c.clk->t_end - c.clk->t;
+  return v < rem ? v : (rem > 0.0 ? rem : 0.0);
+}
+
+// Where a kernel finds its context.  One: a single instance, the context is the kernel parameter and
+// the local block is blockIdx.x.  Many: a batch; the block's instance is the last k with
+// start[k] <= blockIdx.x (binary search over the batch's per-kernel block offsets), its context is
+// copied from the device table into shared memory, and the local block is blockIdx.x - start[k].  Every
+// thread of the block must call get() before any thread leaves.
+struct One {
+  Ctx c;
+  __device__ __forceinline__ const Ctx& get(Ctx*, int* lb) const {
+    *lb = blockIdx.x;
+    return c;
+  }
+};
+
+struct Many {
+  const Ctx* ctx;   // device [ninst]
+  const int* start; // device [ninst] first block of each instance
+  int ninst;
+  __device__ __forceinline__ const Ctx& get(Ctx* smem, int* lb) const {
+    int lo = 0, hi = ninst - 1;
+    const int bx = (int)blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= bx) lo = mid; else hi = mid - 1;
+    }
+    *lb = bx - start[lo];
+    const int* src = reinterpret_cast<const int*>(ctx + lo);
+    int* dst = reinterpret_cast<int*>(smem);
+    for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    return *smem;
+  }
+};
+
+// Kernels of the sweep and their block counts per instance (host and device agree on these).
+enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL, KN_LSFIX, KN_TAU, KN_COUNT };
+constexpr int kNodeThreads = 256;  // one thread per node or edge
+constexpr int kHighMaxBlock = 160; // element sweep: whole elements per block
+constexpr int kLsfixThreads = 128;
+
+__host__ __device__ inline int high_nodes_per_block(int n_loc) { return (kHighMaxBlock / n_loc) * n_loc; }
+__host__ __device__ inline int high_threads(int n_loc) {
+  int t = (high_nodes_per_block(n_loc) + 31) / 32 * 32;
+  return t > kHighMaxBlock ? kHighMaxBlock : t;
+}
+inline long long kernel_blocks(int k, const Dev& D, int sms) {
+  switch (k) {
+    case KN_EDGE: return ((long long)D.ne + kNodeThreads - 1) / kNodeThreads;
+    case KN_HIGH: {
+      const int npb = high_nodes_per_block(D.n_loc);
+      return npb > 0 ? ((long long)D.n + npb - 1) / npb : 0;
+    }
+    case KN_LSFIX: {  // the queue length is only known on the device: a grid-stride over it
+      const long long want = ((long long)D.nnz + D.nb) / 32768 + 1;
+      const long long cap = 4LL * (sms > 0 ? sms : 1);
+      return D.n == 0 ? 0 : (want < cap ? want : cap);
+    }
+    default: return ((long long)D.n + kNodeThreads - 1) / kNodeThreads;
+  }
+}
+
+// Kernel launchers of each file, dim in 1..3: one instance (context by value) or a batch (Many; blocks =
+// the batch's total for that kernel).  arg: write_out for KN_LOW (the stage ends after U^L), last for
+// KN_LIMIT2 (one limiter pass only), the pass (0 or 1) for KN_LSFIX.
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s);
+cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s);
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, cudaStream_t s);
+cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int n_loc, cudaStream_t s);
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s);
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int blocks_per_inst, int arg,
+                                   cudaStream_t s);
+// End of a fused SSP-RK3 step: advances the clock(s) (kernels_limit.cu).
+cudaError_t launch_clock_one(Clock* clk, cudaStream_t s);
+cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);
+
+// One kernel of the sweep for one instance, with the block count of kernel_blocks.
+inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, int sms, cudaStream_t s) {
+  const long long blocks = kernel_blocks(kern, c.D, sms);
+  switch (kern) {
+    case KN_HIGH: return launch_high_file(dim, c, blocks, s);
+    case KN_LIMIT2:
+    case KN_FINAL:
+    case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, arg, s);
+    default: return launch_low_file(kern, dim, c, blocks, arg, s);
+  }
+}
 
 // ------------------------------------------------------------------------------------------------
 // Device helpers (Euler equations of Sec. 2.2 and the pieces of Sec. 3-5 used by several kernels).

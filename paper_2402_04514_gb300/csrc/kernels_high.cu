@@ -7,7 +7,7 @@ namespace gdg {
 
 namespace {
 
-constexpr int kMaxBlock = 160;
+constexpr int kMaxBlock = kHighMaxBlock;
 
 // Per node i of the block:
 //  1. d_ij^H = max(d^min, d^ev) (Sec. 5, eq. (HighOrderViscosity); Sec. 5.1, eq. (ViscMin); Sec. 5.2),
@@ -22,18 +22,25 @@ constexpr int kMaxBlock = 160;
 //     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i); the rare
 //     searches that need the bracketed iteration are queued for k_lsfix.
 // With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
-template <int DIM>
-__global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const double* __restrict__ U,
-                                                    const double* __restrict__ bdata, double tau,
-                                                    const double* __restrict__ Ubase, double alpha,
-                                                    double* __restrict__ Uout, int nodes_per_block) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src) {
   constexpr int M = DIM + 2;
   __shared__ double sR[M][kMaxBlock];
   __shared__ double sdU[M][kMaxBlock];
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const double* U = c.U;
+  const double* bdata = c.bdata;
+  const int nodes_per_block = high_nodes_per_block(D.n_loc);
   const int t = threadIdx.x;
-  const int i = blockIdx.x * nodes_per_block + t;
+  const int i = lb * nodes_per_block + t;
   const bool valid = t < nodes_per_block && i < D.n;
   const size_t n = D.n;
+  const double tau = stage_tau(c);
   double Ui[M], dUi[M];
   double Ni = 0.0;
   if (valid) {
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         double uh = Ui[q] + dUi[q];
-        Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * Ubase[(size_t)q * n + i] + (1.0 - alpha) * uh : uh;
+        c.Uout[(size_t)q * n + i] = c.alpha != 0.0 ? c.alpha * c.Ubase[(size_t)q * n + i] + (1.0 - c.alpha) * uh : uh;
       }
     }
   }
@@ -173,25 +180,34 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Dev D, Scratch S, const d
   }
 }
 
-template <int DIM>
-cudaError_t high_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
-                      const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  int epb = kMaxBlock / D.n_loc;  // whole elements per block
-  if (epb < 1) return cudaErrorInvalidValue;
-  int npb = epb * D.n_loc;
-  int threads = (npb + 31) / 32 * 32;
-  if (threads > kMaxBlock) threads = kMaxBlock;
-  int blocks = (D.n + npb - 1) / npb;
-  k_high<DIM><<<blocks, threads, 0, s>>>(D, S, U, bdata, tau, Ubase, alpha, Uout, npb);
+template <int DIM, class Src>
+cudaError_t high_launch(const Src& src, long long blocks, int n_loc, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  if (high_nodes_per_block(n_loc) < 1) return cudaErrorInvalidValue;
+  k_high<DIM, Src><<<(unsigned)blocks, high_threads(n_loc), 0, s>>>(src);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_high(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
-                        const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
-  GDG_DISPATCH(dim, high_impl, D, S, U, bdata, tau, Ubase, alpha, Uout, s);
+// All instances of a batch share n_loc (it sets the block shape).
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, cudaStream_t s) {
+  const One src{c};
+  switch (dim) {
+    case 1: return high_launch<1, One>(src, blocks, c.D.n_loc, s);
+    case 2: return high_launch<2, One>(src, blocks, c.D.n_loc, s);
+    case 3: return high_launch<3, One>(src, blocks, c.D.n_loc, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int n_loc, cudaStream_t s) {
+  switch (dim) {
+    case 1: return high_launch<1, Many>(m, blocks, n_loc, s);
+    case 2: return high_launch<2, Many>(m, blocks, n_loc, s);
+    case 3: return high_launch<3, Many>(m, blocks, n_loc, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace gdg

@@ -1,7 +1,5 @@
 // Sweeps C and D: symmetrisation of the limiter coefficients, the limited updates of Sec. 5.3,
 // eq. (LimitedScheme), and the second limiter pass of Sec. 6.1.  One thread per row.
-#include <algorithm>
-
 #include "gdg_internal.cuh"
 
 namespace gdg {
@@ -13,11 +11,16 @@ constexpr int kThreads = 256;
 // Sweep C: l_ij = min(l_ij^(i), l_ji^(j)) (Lemma ConsInvariants needs l_ij = l_ji);
 // U^(1)_i = U^L_i + (sum_j l_ij A_ij + sum_k l_i^k A_i^k) / m_i; then the second pass limits the
 // remainder (1 - l) A from U^(1) against the same bounds.  With one pass it writes U_out from U^(1).
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const double* __restrict__ Ubase,
-                                                     double alpha, double* __restrict__ Uout, int last) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
   constexpr int M = DIM + 2;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const int i = lb * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   double acc[M];
@@ -39,9 +42,10 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
 #pragma unroll
   for (int q = 0; q < M; ++q) U1[q] = S.UL[q * n + i] + acc[q] * inv_mi;
   if (last) {
+    const double alpha = c.alpha;
 #pragma unroll
     for (int q = 0; q < M; ++q)
-      Uout[q * n + i] = alpha != 0.0 ? alpha * Ubase[q * n + i] + (1.0 - alpha) * U1[q] : U1[q];
+      c.Uout[q * n + i] = alpha != 0.0 ? alpha * c.Ubase[q * n + i] + (1.0 - alpha) * U1[q] : U1[q];
     return;
   }
 #pragma unroll
@@ -87,12 +91,19 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Dev D, Scratch S, const dou
 // l1; pass 1: from U^(1) with P = (1 - l1_ij) A / (kappa_i m_i), written to l2).  One thread per queued
 // entry, grid-stride over the queue: every lane runs a bracketed iteration.  The row context, l_rho and
 // psi(l_rho) are recomputed from the same stored values by the same code as in the queuing kernel.
-template <int DIM>
-__global__ void __launch_bounds__(128) k_lsfix(Dev D, Scratch S, int pass) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass, int blocks_per_inst) {
   constexpr int M = DIM + 2;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
   const unsigned count = S.lsq_n[pass];
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+  const unsigned stride = (unsigned)blocks_per_inst * blockDim.x;
+  for (unsigned k = lb * blockDim.x + threadIdx.x; k < count; k += stride) {
     const int2 it = S.lsq[k];
     const int i = it.y;
     const bool bnd = it.x < 0;
@@ -117,11 +128,16 @@ __global__ void __launch_bounds__(128) k_lsfix(Dev D, Scratch S, int pass) {
 
 // Sweep D: U^(2)_i = U^(1)_i + (sum_j l2_ij (1 - l1_ij) A_ij + sum_k l2_i^k (1 - l1_i^k) A_i^k) / m_i,
 // symmetrised as in sweep C, and U_out = alpha U_base + (1 - alpha) U^(2).
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_final(Dev D, Scratch S, const double* __restrict__ Ubase,
-                                                    double alpha, double* __restrict__ Uout) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_final(Src src) {
   constexpr int M = DIM + 2;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const int i = lb * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   double acc[M];
@@ -139,57 +155,111 @@ __global__ void __launch_bounds__(kThreads) k_final(Dev D, Scratch S, const doub
     for (int q = 0; q < M; ++q) acc[q] += w * S.AB[q * nb + b];
   }
   const double inv_mi = D.inv_mi[i];
+  const double alpha = c.alpha;
 #pragma unroll
   for (int q = 0; q < M; ++q) {
     double u2 = S.U1[q * n + i] + acc[q] * inv_mi;
-    Uout[q * n + i] = alpha != 0.0 ? alpha * Ubase[q * n + i] + (1.0 - alpha) * u2 : u2;
+    c.Uout[q * n + i] = alpha != 0.0 ? alpha * c.Ubase[q * n + i] + (1.0 - alpha) * u2 : u2;
   }
 }
 
-template <int DIM>
-cudaError_t limit2_impl(const Dev& D, const Scratch& S, const double* Ubase, double alpha, double* Uout,
-                        cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  k_limit2<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, Ubase, alpha, Uout,
-                                                                     D.passes == 1 ? 1 : 0);
+// End of a fused SSP-RK3 step for one instance's clock: t += tau of the step (the tau every kernel of the
+// step used), the step is counted, and the bound is reset for the next step.
+__device__ __forceinline__ void clock_advance(Clock* k) {
+  const unsigned long long b = k->tau_bits;
+  double tau = 0.0;
+  bool clipped = false;
+  if (b != kTauNone) {
+    const double v = k->cfl * __longlong_as_double((long long)b);
+    const double rem = k->t_end - k->t;
+    clipped = !(v < rem);
+    tau = clipped ? (rem > 0.0 ? rem : 0.0) : v;
+  } else {
+    clipped = k->t_end < INFINITY;  // no viscosity anywhere: nothing evolves, the instance is done
+  }
+  k->tau = tau;
+  k->t = clipped ? k->t_end : k->t + tau;  // a step clipped to t_end lands on it exactly
+  k->steps += 1;
+  k->tau_bits = kTauNone;
+}
+
+__global__ void k_clock_one(Clock* k) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) clock_advance(k);
+}
+
+__global__ void k_clock_many(const Ctx* ctx, int ninst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < ninst) clock_advance(ctx[k].clk);
+}
+
+template <int DIM, class Src>
+cudaError_t limit_launch(int kern, const Src& src, long long blocks, int arg, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)blocks;
+  switch (kern) {
+    case KN_LIMIT2: k_limit2<DIM, Src><<<g, kThreads, 0, s>>>(src, arg); break;
+    case KN_FINAL: k_final<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-template <int DIM>
-cudaError_t final_impl(const Dev& D, const Scratch& S, const double* Ubase, double alpha, double* Uout,
-                       cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  k_final<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, Ubase, alpha, Uout);
-  return cudaGetLastError();
-}
-
-template <int DIM>
-cudaError_t lsfix_impl(const Dev& D, const Scratch& S, int pass, cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // the queue length is only known on the device: a grid of 4 blocks per SM strides over it
-  const long long cap = ((long long)D.nnz + D.nb + 127) / 128;
-  const int blocks = (int)std::max(1LL, std::min<long long>(4LL * std::max(1, sms), cap));
-  k_lsfix<DIM><<<blocks, 128, 0, s>>>(D, S, pass);
+template <int DIM, class Src>
+cudaError_t lsfix_launch(const Src& src, long long blocks, int blocks_per_inst, int pass, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  k_lsfix<DIM, Src><<<(unsigned)blocks, kLsfixThreads, 0, s>>>(src, pass, blocks_per_inst);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_lsfix(int dim, const Dev& D, const Scratch& S, int pass, cudaStream_t s) {
-  GDG_DISPATCH(dim, lsfix_impl, D, S, pass, s);
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s) {
+  const One src{c};
+  if (kern == KN_LSFIX) {
+    switch (dim) {
+      case 1: return lsfix_launch<1, One>(src, blocks, (int)blocks, arg, s);
+      case 2: return lsfix_launch<2, One>(src, blocks, (int)blocks, arg, s);
+      case 3: return lsfix_launch<3, One>(src, blocks, (int)blocks, arg, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (dim) {
+    case 1: return limit_launch<1, One>(kern, src, blocks, arg, s);
+    case 2: return limit_launch<2, One>(kern, src, blocks, arg, s);
+    case 3: return limit_launch<3, One>(kern, src, blocks, arg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_limit2(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha, double* Uout,
-                          cudaStream_t s) {
-  GDG_DISPATCH(dim, limit2_impl, D, S, Ubase, alpha, Uout, s);
+// In a batch every instance gets blocks_per_inst blocks of k_lsfix (the batch's start offsets for that
+// kernel are k * blocks_per_inst).
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int blocks_per_inst, int arg,
+                                   cudaStream_t s) {
+  if (kern == KN_LSFIX) {
+    switch (dim) {
+      case 1: return lsfix_launch<1, Many>(m, blocks, blocks_per_inst, arg, s);
+      case 2: return lsfix_launch<2, Many>(m, blocks, blocks_per_inst, arg, s);
+      case 3: return lsfix_launch<3, Many>(m, blocks, blocks_per_inst, arg, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (dim) {
+    case 1: return limit_launch<1, Many>(kern, m, blocks, arg, s);
+    case 2: return limit_launch<2, Many>(kern, m, blocks, arg, s);
+    case 3: return limit_launch<3, Many>(kern, m, blocks, arg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_final(int dim, const Dev& D, const Scratch& S, const double* Ubase, double alpha, double* Uout,
-                         cudaStream_t s) {
-  GDG_DISPATCH(dim, final_impl, D, S, Ubase, alpha, Uout, s);
+cudaError_t launch_clock_one(Clock* clk, cudaStream_t s) {
+  k_clock_one<<<1, 32, 0, s>>>(clk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s) {
+  if (ninst <= 0) return cudaSuccess;
+  k_clock_many<<<(ninst + 127) / 128, 128, 0, s>>>(ctx, ninst);
+  return cudaGetLastError();
 }
 
 }  // namespace gdg

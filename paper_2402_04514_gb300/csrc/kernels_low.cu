@@ -1,22 +1,34 @@
 // Low-order sweep: per-node primitives, the time-step reduction (Sec. 3.3, eq. (MaxCFLdt)) and the
 // first stage sweep (low-order update, entropy-viscosity indicator, one-hop bound aggregates).
+// Every kernel takes its context from a source (One: a single instance, Many: a batch; gdg_internal.cuh).
 #include "gdg_internal.cuh"
 
 namespace gdg {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kNodeThreads;
 
 // Per-node primitives (Sec. 2.2): 1/rho, p, 1/p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
 // f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
-// Flags a state outside the admissible set of eq. (AddSet).
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_prim(Dev D, Scratch S, const double* __restrict__ U) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Flags a state outside the admissible set of eq. (AddSet).  Being the first kernel of every stage, it
+// also empties the stage's deferred line-search queues.
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_prim(Src src) {
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const int i = lb * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    S.lsq_n[0] = 0u;
+    S.lsq_n[1] = 0u;
+  }
   if (i >= D.n) return;
   double Ui[DIM + 2];
-  load_state<DIM>(U, D.n, i, Ui);
+  load_state<DIM>(c.U, D.n, i, Ui);
   double irho = 1.0 / Ui[0];
   double m2 = 0.0;
 #pragma unroll
@@ -39,13 +51,57 @@ __global__ void __launch_bounds__(kThreads) k_prim(Dev D, Scratch S, const doubl
   P[PR_ST * n + i] = st;
 }
 
-// Sum over the row of d_ij^L plus the boundary viscosities, i.e. -d_ii of
-// eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|).
+// d_i^{d,k} = |c_i^{d,k}| lambda_max^+(U_i, U^{d,k}, n_i^k) of boundary entry b (Sec. 4.2,
+// eq. (eq:dij_low_order_modified); interior state on the left), from node i's primitives.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const double* __restrict__ U,
-                                                    const double* __restrict__ bdata) {
+__device__ __forceinline__ double boundary_viscosity(const Dev& D, int b, const double* Ui, const double* bdata,
+                                                     double irho_i, double p_i, double ip_i, double a_i,
+                                                     double pme_i) {
   constexpr int M = DIM + 2;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double nv[DIM], UB[M];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
+  boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
+  double irB = 1.0 / UB[0];
+  double pB = D.gm1 * internal_energy<DIM>(UB);
+  double uL = 0.0, uR = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    uL += Ui[1 + k] * nv[k];
+    uR += UB[1 + k] * nv[k];
+  }
+  return D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, ip_i, a_i, pme_i, uR * irB, pB, 1.0 / pB,
+                                 sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
+}
+
+// Block minimum of val, then one 64-bit atomicMin per block on the bit pattern (positive doubles order
+// like uint64).  Every thread of the block calls it.
+__device__ __forceinline__ void block_min_to(double val, unsigned long long* dst) {
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    val = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : INFINITY;
+    for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
+    if (threadIdx.x == 0 && val < INFINITY) atomicMin(dst, (unsigned long long)__double_as_longlong(val));
+  }
+}
+
+// Sum over the row of d_ij^L plus the boundary viscosities, i.e. -d_ii of
+// eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|), with d_ij^L evaluated here
+// (gdg_max_dt, before any stage).
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
+  constexpr int M = DIM + 2;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const double* U = c.U;
+  const int i = lb * blockDim.x + threadIdx.x;
   double val = INFINITY;
   if (i < D.n) {
     size_t n = D.n;
@@ -57,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
     double dsum = 0.0;
     for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
       double cnm = D.cnorm[e];
-      if (cnm == 0.0) continue;
+      if (is_zero_bits(cnm)) continue;
       int j = D.col[e];
       double nv[DIM], uL = 0.0, uR = 0.0;
 #pragma unroll
@@ -71,35 +127,42 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
       dsum += cnm * lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], P[PR_IP * n + j], P[PR_A * n + j],
                                P[PR_PME * n + j]);
     }
-    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-      double nv[DIM], UB[M];
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
-      boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
-      double irB = 1.0 / UB[0];
-      double pB = D.gm1 * internal_energy<DIM>(UB);
-      double uL = 0.0, uR = 0.0;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        uL += Ui[1 + k] * nv[k];
-        uR += UB[1 + k] * nv[k];
-      }
-      dsum += D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, ip_i, a_i, pme_i, uR * irB, pB, 1.0 / pB,
-                                      sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
+    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b)
+      dsum += boundary_viscosity<DIM>(D, b, Ui, c.bdata, irho_i, p_i, ip_i, a_i, pme_i);
+    if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
+  }
+  block_min_to(val, S.tau_bits);
+}
+
+// The same bound inside the fused SSP-RK3 step, after the edge sweep of the step's first stage: the row
+// sums of the stored d_ij^L plus the boundary viscosities, reduced into the instance's clock.
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_tau(Src src) {
+  constexpr int M = DIM + 2;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const int i = lb * blockDim.x + threadIdx.x;
+  double val = INFINITY;
+  if (i < D.n) {
+    double dsum = 0.0;
+    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) dsum += S.dL[e];  // m_ij-only entries hold 0
+    const int b0 = D.b_ptr[i], b1 = D.b_ptr[i + 1];
+    if (b0 < b1) {
+      const size_t n = D.n;
+      const double* P = S.prim;
+      double Ui[M];
+      load_state<DIM>(c.U, D.n, i, Ui);
+      for (int b = b0; b < b1; ++b)
+        dsum += boundary_viscosity<DIM>(D, b, Ui, c.bdata, P[PR_IRHO * n + i], P[PR_P * n + i], P[PR_IP * n + i],
+                                        P[PR_A * n + i], P[PR_PME * n + i]);
     }
     if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
   }
-  // block minimum, then one atomic per block on the bit pattern (positive doubles order like uint64)
-  __shared__ double red[kThreads / 32];
-  for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    val = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : INFINITY;
-    for (int off = 16; off > 0; off >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, off));
-    if (threadIdx.x == 0 && val < INFINITY)
-      atomicMin(S.tau_bits, (unsigned long long)__double_as_longlong(val));
-  }
+  block_min_to(val, &c.clk->tau_bits);
 }
 
 // Edge sweep, one thread per undirected stencil edge {i, j} (i < j): the quantities of a pair that are
@@ -109,18 +172,24 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Dev D, Scratch S, const doub
 //  - the bar state Ubar_ij = Ubar_ji (eq. (UsualBarState)), of which only rho and s~ are kept (for the
 //    local bounds of eq. (eq:local_bounds));
 //  - G_ij = f(U_j) c_ij and G_ji = f(U_i) c_ji = -|c_ij| f(U_i) n_ij for the row sums of sweep A.
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_edge(Dev D, Scratch S, const double* __restrict__ U) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_edge(Src src) {
   constexpr int M = DIM + 2;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const int k = lb * blockDim.x + threadIdx.x;
   if (k >= D.ne) return;
   const size_t n = D.n, nnz = D.nnz;
   const int e = D.edge_e[k], i = D.edge_i[k];
   const int j = D.col[e], t = D.tr[e];
   const double* P = S.prim;
   double Ui[M], Uj[M], nv[DIM];
-  load_state<DIM>(U, D.n, i, Ui);
-  load_state<DIM>(U, D.n, j, Uj);
+  load_state<DIM>(c.U, D.n, i, Ui);
+  load_state<DIM>(c.U, D.n, j, Uj);
   const double cnm = D.cnorm[e];
   double mnL = 0.0, mnR = 0.0;
 #pragma unroll
@@ -167,14 +236,19 @@ __global__ void __launch_bounds__(kThreads) k_edge(Dev D, Scratch S, const doubl
 //    rho(Ubar_jk), rho_k and min of s~ over node j's stencil, with the bar states of
 //    eq. (UsualBarState); and rho, s~ of node i's boundary bar states (eq. (BoundaryBarState)).
 // With order LOW (or no limiter pass) it also writes U_out = alpha U_base + (1 - alpha) U^L.
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double* __restrict__ U,
-                                                  const double* __restrict__ bdata, double tau,
-                                                  const double* __restrict__ Ubase, double alpha,
-                                                  double* __restrict__ Uout, int write_out) {
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   constexpr int M = DIM + 2;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const Dev& D = c.D;
+  const Scratch& S = c.S;
+  const double* U = c.U;
+  const int i = lb * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
+  const double tau = stage_tau(c);
   size_t n = D.n;
   const double* P = S.prim;
   double Ui[M];
@@ -188,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
   double lo = Ui[0], hi = Ui[0], sl = st_i;
   const size_t nnz = D.nnz;
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-    if (D.cnorm[e] == 0.0) continue;  // m_ij-only entry: not in I(i)
+    if (is_zero_bits(D.cnorm[e])) continue;  // m_ij-only entry: not in I(i)
     const int j = D.col[e], t = D.tr[e];
     const double d = S.dL[e];
     dsum += d;
@@ -209,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
     double nv[DIM], UB[M];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
-    boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
+    boundary_state<DIM>(D, b, Ui, c.bdata, nv, UB);
     double irB = 1.0 / UB[0];
     double pB = D.gm1 * internal_energy<DIM>(UB);
     double uL = 0.0, uR = 0.0;
@@ -246,9 +320,10 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
 #pragma unroll
   for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
   if (write_out) {
+    const double alpha = c.alpha;
 #pragma unroll
     for (int q = 0; q < M; ++q)
-      Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * Ubase[(size_t)q * n + i] + (1.0 - alpha) * UL[q] : UL[q];
+      c.Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * c.Ubase[(size_t)q * n + i] + (1.0 - alpha) * UL[q] : UL[q];
     return;
   }
 #pragma unroll
@@ -282,56 +357,41 @@ __global__ void __launch_bounds__(kThreads) k_low(Dev D, Scratch S, const double
   S.N[i] = Dn > 0.0 ? R / Dn : 0.0;
 }
 
-template <int DIM>
-cudaError_t prim_impl(const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  k_prim<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U);
-  return cudaGetLastError();
-}
-
-template <int DIM>
-cudaError_t maxdt_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  k_maxdt<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U, bdata);
-  return cudaGetLastError();
-}
-
-template <int DIM>
-cudaError_t edge_impl(const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
-  if (D.ne == 0) return cudaSuccess;
-  k_edge<DIM><<<(D.ne + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U);
-  return cudaGetLastError();
-}
-
-template <int DIM>
-cudaError_t low_impl(const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
-                     const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
-  if (D.n == 0) return cudaSuccess;
-  int write_out = (D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0)) ? 1 : 0;
-  k_low<DIM><<<(D.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(D, S, U, bdata, tau, Ubase, alpha, Uout,
-                                                                  write_out);
+template <int DIM, class Src>
+cudaError_t low_launch(int kern, const Src& src, long long blocks, int arg, cudaStream_t s) {
+  if (blocks <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)blocks;
+  switch (kern) {
+    case KN_PRIM: k_prim<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    case KN_MAXDT: k_maxdt<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    case KN_TAU: k_tau<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    case KN_EDGE: k_edge<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    case KN_LOW: k_low<DIM, Src><<<g, kThreads, 0, s>>>(src, arg); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-
-cudaError_t launch_prim(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
-  GDG_DISPATCH(dim, prim_impl, D, S, U, s);
+// Launchers of this file's kernels, dispatched on the dimension (called by launch_kernel*).
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s) {
+  const One src{c};
+  switch (dim) {
+    case 1: return low_launch<1, One>(kern, src, blocks, arg, s);
+    case 2: return low_launch<2, One>(kern, src, blocks, arg, s);
+    case 3: return low_launch<3, One>(kern, src, blocks, arg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_maxdt(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata,
-                         cudaStream_t s) {
-  GDG_DISPATCH(dim, maxdt_impl, D, S, U, bdata, s);
-}
-
-cudaError_t launch_edge(int dim, const Dev& D, const Scratch& S, const double* U, cudaStream_t s) {
-  GDG_DISPATCH(dim, edge_impl, D, S, U, s);
-}
-
-cudaError_t launch_low(int dim, const Dev& D, const Scratch& S, const double* U, const double* bdata, double tau,
-                       const double* Ubase, double alpha, double* Uout, cudaStream_t s) {
-  GDG_DISPATCH(dim, low_impl, D, S, U, bdata, tau, Ubase, alpha, Uout, s);
+cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s) {
+  switch (dim) {
+    case 1: return low_launch<1, Many>(kern, m, blocks, arg, s);
+    case 2: return low_launch<2, Many>(kern, m, blocks, arg, s);
+    case 3: return low_launch<3, Many>(kern, m, blocks, arg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace gdg

@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix")  # GDG_K_* order
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock")  # GDG_K_* order
 BC_SLIP, BC_DIRICHLET = 0, 1
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 
@@ -80,6 +80,9 @@ def load(build_if_missing: bool = False):
     L.gdg_set_params.argtypes = [vp, C.POINTER(Params)]
     L.gdg_max_dt.argtypes = [vp, vp, vp, d, C.POINTER(d), vp]
     L.gdg_stage.argtypes = [vp, vp, vp, d, d, vp, vp, vp]
+    L.gdg_ssprk3_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.gdg_clock_set.argtypes = [vp, d, d, d, vp]
+    L.gdg_clock_get.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i64), vp]
     L.gdg_status.argtypes = [vp, C.POINTER(i32), i32, vp]
     L.gdg_debug_export.argtypes = [vp, C.c_char_p, vp, i64, vp]
     L.gdg_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -91,7 +94,8 @@ def load(build_if_missing: bool = False):
     L.gdg_destroy.argtypes = [vp]
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
-    for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_status", "gdg_debug_export",
+    for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_clock_set",
+              "gdg_clock_get", "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
               "gdg_max_dt_noalloc"):
         getattr(L, f).restype = C.c_int
@@ -267,6 +271,27 @@ class Solver:
         self.stage(U1, tau, U_base=U, alpha=0.75, bdata=bd(t + tau), out=U2, stream=stream)
         self.stage(U2, tau, U_base=U, alpha=1.0 / 3.0, bdata=bd(t + 0.5 * tau), out=out, stream=stream)
         return out
+
+    def step(self, U, work, bdata=None, stream=None):
+        """gdg_ssprk3_step: one SSP-RK3 step of U in place, the time step chosen on the device from the
+        handle's clock (set_clock); work = (T1, T2) are two scratch states."""
+        self._check_state(U)
+        T1, T2 = work
+        self._check_state(T1)
+        self._check_state(T2)
+        bd = self._bdata(bdata)
+        _check(load().gdg_ssprk3_step(self._h, _ptr(U), _ptr(T1), _ptr(T2), _ptr(bd), _stream(stream)),
+               "gdg_ssprk3_step")
+        return U
+
+    def set_clock(self, t: float = 0.0, t_end: float = float("inf"), cfl: float = 0.5, stream=None):
+        _check(load().gdg_clock_set(self._h, t, t_end, cfl, _stream(stream)), "gdg_clock_set")
+
+    def clock(self, stream=None):
+        """(t, tau of the last step, completed steps) of the fused step's clock; synchronises."""
+        t, tau, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(load().gdg_clock_get(self._h, C.byref(t), C.byref(tau), C.byref(n), _stream(stream)), "gdg_clock_get")
+        return t.value, tau.value, n.value
 
     def close(self):
         if getattr(self, "_h", None):
