@@ -34,6 +34,7 @@ WORKLOADS = {
     "q1_512_vortex_periodic": dict(N=512, k=1, vortex=True),
 }
 SAMPLE_N = 128  # oracle sample: same data on a 128 x 128 mesh
+SOLVE_STEPS = 50  # a batched solve: 50 SSP-RK3 steps of one instance
 
 
 def make_problem(spec):
@@ -123,6 +124,89 @@ def run_reference(args):
     return 0
 
 
+def c4_instances(count, seed=1):
+    """The batched workload: `count` instances of 2D Q1 on [0,1]^2 with N = round(32 * 16^u) quads per side
+    (u ~ U[0,1], so N is log-uniform in [32, 512]), slip walls, two-state Riemann data split by a line
+    through the centre at a random angle (rho, p log-uniform in [0.1, 10], |u| <= 2), all from
+    default_rng(seed).  Yields (N, problem, U0)."""
+    import numpy as np
+
+    from paper_2402_04514_gb300 import assembly, workloads
+
+    rng = np.random.default_rng(seed)
+    Ns = [int(round(32 * 16 ** u)) for u in rng.uniform(0.0, 1.0, count)]
+    for N in Ns:
+        P = assembly.assemble_2d(N, N, 1)
+        yield N, P, workloads.two_state_riemann(P.x[0], P.x[1], rng)
+
+
+def run_batched(args):
+    """Batched solves: one gdg_batch_step advances every instance by one SSP-RK3 step in shared launches;
+    against the same instances stepped one at a time (gdg_ssprk3_step per instance, in turn, on one
+    stream).  A solve is SOLVE_STEPS steps of one instance; solves/s = instances x timed steps /
+    SOLVE_STEPS / time."""
+    import torch
+
+    from paper_2402_04514_gb300.gdg import Batch, Solver
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    solvers, states, works, sizes = [], [], [], []
+    t0 = time.perf_counter()
+    for N, P, U in c4_instances(args.instances):
+        S = Solver(P)
+        S.set_clock(0.0, float("inf"), 0.5)
+        Ud = torch.from_numpy(U).cuda()
+        solvers.append(S)
+        states.append(Ud)
+        works.append((torch.empty_like(Ud), torch.empty_like(Ud)))
+        sizes.append(P.n)
+    setup_s = time.perf_counter() - t0
+    B = Batch(solvers, states, works)
+    stream = torch.cuda.current_stream()
+    dofs = sum(sizes)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def one_at_a_time():
+        for S, U, w in zip(solvers, states, works):
+            S.step(U, w)
+
+    for _ in range(args.warmup):
+        B.step()
+        one_at_a_time()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t_batch = timed(B.step, args.steps)
+    t_single = timed(one_at_a_time, args.steps)
+    clocks = sampler.stop()
+    flags = max(S.status() for S in solvers)
+    inst = len(solvers)
+    rate = inst * args.steps / SOLVE_STEPS / t_batch
+    line = {"metric": "batched solves/s", "value": rate, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched_q1_riemann", "instances": inst, "mesh": "N x N Q1 quads, N log-uniform "
+                       "in [32, 512]", "dofs_total": dofs, "solve": f"{SOLVE_STEPS} SSP-RK3 steps",
+                       "scheme": "convex-limited, 2 limiter passes", "cfl": 0.5, "seed": 1,
+                       "setup_s": round(setup_s, 1)},
+            "dof_stage_per_s": dofs * 3 * args.steps / t_batch,
+            "one_at_a_time": {"value": inst * args.steps / SOLVE_STEPS / t_single, "unit": "solves/s",
+                              "ms_per_step": 1e3 * t_single / args.steps,
+                              "dof_stage_per_s": dofs * 3 * args.steps / t_single},
+            "speedup_vs_one_at_a_time": t_single / t_batch, "gpu_launches": 26 * args.steps,
+            "clocks": clocks, "status_flags": flags}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(args, n):
     spec = WORKLOADS[args.workload]
     return {"workload": args.workload, "mesh": f"{spec['N']}x{spec['N']} quads", "degree": spec["k"],
@@ -137,7 +221,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="q2_1024_four_quadrant", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="q2_1024_four_quadrant", choices=sorted(WORKLOADS) + ["batched_q1_riemann"])
+    ap.add_argument("--instances", type=int, default=512, help="batched workload: number of instances")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-steps", type=int, default=8)
@@ -153,6 +238,8 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_q1_riemann":
+        return run_batched(args)
 
     import numpy as np
     import torch

@@ -229,6 +229,33 @@ typedef struct {
 int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, const double* bdata, double cfl,
                        double* tau_out, void* stream);
 
+/* Batches: many independent instances advanced together.  The paper solves one problem at a time; a
+ * batch runs the per-stage sweep of Sec. 6.1 for all its members in the same kernel launches (one
+ * launch per kernel and stage over all instances; each block finds its instance from per-kernel block
+ * offsets), so small meshes share the GPU instead of each paying its own launches and host round trips.
+ *
+ * gdg_batch_create: handles[count] (distinct, same device, dim, n_loc, order and limiter passes; each
+ * keeps its own mesh, scratch and clock), with the state U[k] and the workspace T1[k], T2[k] of member
+ * k (device [m][n_k], distinct, caller-owned, not copied: the batch keeps the pointers) and Dirichlet
+ * data bdata[k] (device [m][nb_k]; the array or an entry may be NULL where a member has no Dirichlet
+ * entry).  Copies two small tables to the device (contexts and block offsets; freed by
+ * gdg_batch_destroy).  The handles must outlive the batch.  Errors: GDG_EINVAL, GDG_ENOMEM, GDG_ENOTSUP
+ * (more than 2^31 - 1 blocks in one kernel), GDG_ECUDA.
+ *
+ * gdg_batch_step: one gdg_ssprk3_step of every member, each with the time step of its own clock
+ * (gdg_clock_set on its handle; a member whose clock reached t_end is left untouched).  Asynchronous on
+ * stream; allocates nothing; results are those of gdg_ssprk3_step on each handle alone.
+ *
+ * gdg_batch_profile / gdg_batch_profile_read: as gdg_profile / gdg_profile_read, for the batch's
+ * launches. */
+typedef struct gdg_batch gdg_batch;
+int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U, double* const* T1,
+                     double* const* T2, const double* const* bdata, gdg_batch** out);
+int gdg_batch_step(gdg_batch* b, void* stream);
+int gdg_batch_profile(gdg_batch* b, int32_t enable);
+int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches);
+void gdg_batch_destroy(gdg_batch* b);
+
 int gdg_get_info(gdg_handle* h, gdg_info* out);
 void gdg_destroy(gdg_handle* h);
 const char* gdg_error_string(int code);

@@ -1,0 +1,220 @@
+// Batches (gdg_batch_*): many independent instances (gdg handles, each with its own mesh, scratch, state
+// buffers and clock) advanced by fused SSP-RK3 steps in which every kernel of the sweep is one launch over
+// all instances.  A block of such a launch finds its instance from the batch's per-kernel block offsets
+// (gdg::Many); each instance keeps its own time step (its clock), so instances of different sizes, speeds
+// and end times share the launches.  The paper treats one problem at a time; batching is this library's.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "gdg_internal.cuh"
+#include "handle.cuh"
+
+struct gdg_batch {
+  int device = 0, dim = 0, n_loc = 0, order = 0, passes = 0, count = 0, sms = 1;
+  std::vector<gdg_handle*> hs;
+  void* mem = nullptr;                 // device: context tables and block offsets
+  gdg::Ctx* ctx[3] = {nullptr, nullptr, nullptr};  // [count] contexts of the three stages
+  int* start[gdg::KN_COUNT] = {};      // [count + 1] block offsets of each kernel
+  long long blocks[gdg::KN_COUNT] = {};
+  // kernel timing, as gdg_profile
+  struct Rec {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+int cuda_fail_b(cudaError_t) {
+  cudaGetLastError();
+  return GDG_ECUDA;
+}
+
+cudaError_t launch_many(const gdg_batch* b, int kern, int stage, int arg, cudaStream_t s) {
+  const gdg::Many m{b->ctx[stage], b->start[kern], b->count};
+  const long long blocks = b->blocks[kern];
+  switch (kern) {
+    case gdg::KN_HIGH: return gdg::launch_high_file_many(b->dim, m, blocks, b->n_loc, s);
+    case gdg::KN_LIMIT2:
+    case gdg::KN_FINAL:
+    case gdg::KN_LSFIX: return gdg::launch_limit_file_many(kern, b->dim, m, blocks, arg, s);
+    default: return gdg::launch_low_file_many(kern, b->dim, m, blocks, arg, s);
+  }
+}
+
+template <class F>
+cudaError_t btimed(gdg_batch* b, int kernel, cudaStream_t s, F&& launch) {
+  if (!b->profiling) return launch();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  for (cudaEvent_t* e : {&e0, &e1}) {
+    if (!b->pool.empty()) {
+      *e = b->pool.back();
+      b->pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  cudaEventRecord(e0, s);
+  cudaError_t e = launch();
+  cudaEventRecord(e1, s);
+  b->recs.push_back({kernel, e0, e1});
+  return e;
+}
+
+void release(gdg_batch* b) {
+  for (auto& r : b->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : b->pool) cudaEventDestroy(e);
+  if (b->mem) cudaFree(b->mem);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U, double* const* T1,
+                     double* const* T2, const double* const* bdata, gdg_batch** out) {
+  if (!out) return GDG_EINVAL;
+  *out = nullptr;
+  if (!handles || count < 1 || !U || !T1 || !T2) return GDG_EINVAL;
+  const gdg_handle* h0 = handles[0];
+  if (!h0) return GDG_EINVAL;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int k = 0; k < count; ++k) {
+    const gdg_handle* h = handles[k];
+    if (!h || h->device != dev || h->dim != h0->dim || h->n_loc != h0->n_loc || h->D.order != h0->D.order ||
+        h->D.passes != h0->D.passes)
+      return GDG_EINVAL;
+    if (h->n > 0 && (!U[k] || !T1[k] || !T2[k] || U[k] == T1[k] || U[k] == T2[k] || T1[k] == T2[k]))
+      return GDG_EINVAL;
+    if (h->has_dirichlet && !(bdata && bdata[k])) return GDG_EINVAL;
+    for (int q = 0; q < k; ++q)
+      if (handles[q] == h) return GDG_EINVAL;  // an instance's scratch and clock serve one member
+  }
+  gdg_batch* b = new (std::nothrow) gdg_batch;
+  if (!b) return GDG_ENOMEM;
+  b->device = dev;
+  b->dim = h0->dim;
+  b->n_loc = h0->n_loc;
+  b->order = h0->D.order;
+  b->passes = h0->D.passes;
+  b->count = count;
+  b->sms = h0->sms;
+  b->hs.assign(handles, handles + count);
+  // host tables: contexts of the three stages (Shu-Osher SSP-RK3, the last stage in place) and the
+  // block offsets of every kernel
+  std::vector<gdg::Ctx> ctx((size_t)3 * count);
+  std::vector<int> start((size_t)gdg::KN_COUNT * (count + 1));
+  for (int k = 0; k < count; ++k) {
+    gdg_handle* h = handles[k];
+    const double* bd = bdata ? bdata[k] : nullptr;
+    ctx[k] = make_ctx(h, U[k], nullptr, T1[k], bd, 0.0, 0.0, h->clk);
+    ctx[(size_t)count + k] = make_ctx(h, T1[k], U[k], T2[k], bd, 0.75, 0.0, h->clk);
+    ctx[(size_t)2 * count + k] = make_ctx(h, T2[k], U[k], U[k], bd, 1.0 / 3.0, 0.0, h->clk);
+  }
+  for (int kern = 0; kern < gdg::KN_COUNT; ++kern) {
+    long long acc = 0;
+    int* st = &start[(size_t)kern * (count + 1)];
+    for (int k = 0; k < count; ++k) {
+      st[k] = (int)acc;
+      acc += gdg::kernel_blocks(kern, handles[k]->D, b->sms);
+    }
+    st[count] = (int)acc;
+    if (acc > 0x7fffffffLL) {
+      release(b);
+      return GDG_ENOTSUP;  // more blocks than a grid holds
+    }
+    b->blocks[kern] = acc;
+  }
+  const size_t ctx_bytes = sizeof(gdg::Ctx) * ctx.size(), start_bytes = sizeof(int) * start.size();
+  cudaError_t e = cudaMalloc(&b->mem, ctx_bytes + start_bytes);
+  if (e != cudaSuccess) {
+    b->mem = nullptr;
+    cudaGetLastError();
+    release(b);
+    return GDG_ENOMEM;
+  }
+  char* base = (char*)b->mem;
+  if ((e = cudaMemcpy(base, ctx.data(), ctx_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(base + ctx_bytes, start.data(), start_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    release(b);
+    return cuda_fail_b(e);
+  }
+  for (int st = 0; st < 3; ++st) b->ctx[st] = (gdg::Ctx*)base + (size_t)st * count;
+  for (int kern = 0; kern < gdg::KN_COUNT; ++kern)
+    b->start[kern] = (int*)(base + ctx_bytes) + (size_t)kern * (count + 1);
+  *out = b;
+  return GDG_OK;
+}
+
+int gdg_batch_step(gdg_batch* b, void* stream) {
+  if (!b) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool low_only = b->order == GDG_ORDER_LOW || (b->order == GDG_ORDER_LIMITED && b->passes == 0);
+  cudaError_t e;
+  for (int stage = 0; stage < 3; ++stage) {
+    auto go = [&](int id, int kern, int arg) {
+      return btimed(b, id, s, [&] { return launch_many(b, kern, stage, arg, s); });
+    };
+    if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_EDGE, gdg::KN_EDGE, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (stage == 0 && (e = go(GDG_K_TAU, gdg::KN_TAU, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_LOW, gdg::KN_LOW, low_only ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (low_only) continue;
+    if ((e = go(GDG_K_HIGH, gdg::KN_HIGH, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (b->order == GDG_ORDER_HIGH) continue;
+    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_LIMIT2, gdg::KN_LIMIT2, b->passes == 1 ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (b->passes == 1) continue;
+    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 1)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_FINAL, gdg::KN_FINAL, 0)) != cudaSuccess) return cuda_fail_b(e);
+  }
+  e = btimed(b, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_many(b->ctx[0], b->count, s); });
+  return e == cudaSuccess ? GDG_OK : cuda_fail_b(e);
+}
+
+int gdg_batch_profile(gdg_batch* b, int32_t enable) {
+  if (!b) return GDG_EINVAL;
+  for (auto& r : b->recs) {
+    b->pool.push_back(r.a);
+    b->pool.push_back(r.b);
+  }
+  b->recs.clear();
+  b->profiling = enable != 0;
+  return GDG_OK;
+}
+
+int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches) {
+  if (!b || !total_ms || !launches) return GDG_EINVAL;
+  for (int k = 0; k < GDG_NKERNELS; ++k) {
+    total_ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  int rc = GDG_OK;
+  for (auto& r : b->recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) rc = cuda_fail_b(e);
+    total_ms[r.kernel] += ms;
+    launches[r.kernel] += 1;
+    b->pool.push_back(r.a);
+    b->pool.push_back(r.b);
+  }
+  b->recs.clear();
+  return rc;
+}
+
+void gdg_batch_destroy(gdg_batch* b) {
+  if (b) release(b);
+}
+
+}  // extern "C"

@@ -12,65 +12,10 @@
 
 #include "gdg_internal.cuh"
 
+#include "handle.cuh"
+
 using gdg::Dev;
 using gdg::Scratch;
-
-struct gdg_handle {
-  int device = 0;
-  int dim = 0, degree = 0, n_loc = 0;
-  int64_t n = 0, nnz = 0, nb = 0;
-  double gamma = 1.4, omega = 1.0;
-  gdg_params params{};
-  bool has_dirichlet = false;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  Dev D{};
-  Scratch S{};
-  // host copies needed after setup
-  std::vector<int> row_ptr, col, tr, borig, bnode_sorted;
-  std::vector<uint8_t> coloc;
-  std::vector<double> mi;
-  // device pointers of the parameter-dependent arrays
-  double *d_mu = nullptr, *d_rminus = nullptr, *d_rplus = nullptr, *d_muB = nullptr;
-  // kernel timing (gdg_profile)
-  struct Rec {
-    int kernel;
-    cudaEvent_t a, b;
-  };
-  bool profiling = false;
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  int sms = 1;                   // multiprocessors of the device (grid of the deferred line searches)
-  gdg::Clock* clk = nullptr;     // device clock of the fused step (in the arena)
-};
-
-namespace {
-
-cudaEvent_t take_event(gdg_handle* h) {
-  if (!h->pool.empty()) {
-    cudaEvent_t e = h->pool.back();
-    h->pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-
-// Runs one launcher, bracketed by events when profiling.
-template <class F>
-cudaError_t timed(gdg_handle* h, int kernel, cudaStream_t s, F&& launch) {
-  if (!h->profiling) return launch();
-  cudaEvent_t a = take_event(h), b = take_event(h);
-  if (!a || !b) return cudaErrorMemoryAllocation;
-  cudaEventRecord(a, s);
-  cudaError_t e = launch();
-  cudaEventRecord(b, s);
-  h->recs.push_back({kernel, a, b});
-  return e;
-}
-
-}  // namespace
 
 namespace {
 
@@ -578,21 +523,6 @@ int gdg_set_params(gdg_handle* h, const gdg_params* params) {
   if (int rc = param_arrays(h, *params, pa); rc != GDG_OK) return rc;
   h->params = *params;
   return upload_param_arrays(h, pa);
-}
-
-static gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Ubase, double* Uout,
-                         const double* bdata, double alpha, double tau, gdg::Clock* clk) {
-  gdg::Ctx c{};
-  c.D = h->D;
-  c.S = h->S;
-  c.U = U;
-  c.Ubase = Ubase;
-  c.Uout = Uout;
-  c.bdata = bdata;
-  c.alpha = alpha;
-  c.tau = tau;
-  c.clk = clk;
-  return c;
 }
 
 int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out, void* stream) {

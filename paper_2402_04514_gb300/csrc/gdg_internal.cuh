@@ -140,24 +140,26 @@ __device__ __forceinline__ double stage_tau(const Ctx& c) {
 // thread of the block must call get() before any thread leaves.
 struct One {
   Ctx c;
-  __device__ __forceinline__ const Ctx& get(Ctx*, int* lb) const {
+  __device__ __forceinline__ const Ctx& get(Ctx*, int* lb, int* nblk = nullptr) const {
     *lb = blockIdx.x;
+    if (nblk) *nblk = gridDim.x;
     return c;
   }
 };
 
 struct Many {
   const Ctx* ctx;   // device [ninst]
-  const int* start; // device [ninst] first block of each instance
+  const int* start; // device [ninst + 1] first block of each instance, then the total
   int ninst;
-  __device__ __forceinline__ const Ctx& get(Ctx* smem, int* lb) const {
+  __device__ __forceinline__ const Ctx& get(Ctx* smem, int* lb, int* nblk = nullptr) const {
     int lo = 0, hi = ninst - 1;
     const int bx = (int)blockIdx.x;
-    while (lo < hi) {
+    while (lo < hi) {  // the last instance starting at or before bx (instances without blocks are skipped)
       const int mid = (lo + hi + 1) >> 1;
       if (start[mid] <= bx) lo = mid; else hi = mid - 1;
     }
     *lb = bx - start[lo];
+    if (nblk) *nblk = start[lo + 1] - start[lo];
     const int* src = reinterpret_cast<const int*>(ctx + lo);
     int* dst = reinterpret_cast<int*>(smem);
     for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
@@ -201,8 +203,7 @@ cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blo
 cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, cudaStream_t s);
 cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int n_loc, cudaStream_t s);
 cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s);
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int blocks_per_inst, int arg,
-                                   cudaStream_t s);
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s);
 // End of a fused SSP-RK3 step: advances the clock(s) (kernels_limit.cu).
 cudaError_t launch_clock_one(Clock* clk, cudaStream_t s);
 cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);

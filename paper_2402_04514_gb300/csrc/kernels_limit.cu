@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
 // entry, grid-stride over the queue: every lane runs a bracketed iteration.  The row context, l_rho and
 // psi(l_rho) are recomputed from the same stored values by the same code as in the queuing kernel.
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass, int blocks_per_inst) {
+__global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
-  int lb;
-  const Ctx& c = src.get(&sctx, &lb);
+  int lb, blocks_per_inst;
+  const Ctx& c = src.get(&sctx, &lb, &blocks_per_inst);
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
@@ -205,9 +205,9 @@ cudaError_t limit_launch(int kern, const Src& src, long long blocks, int arg, cu
 }
 
 template <int DIM, class Src>
-cudaError_t lsfix_launch(const Src& src, long long blocks, int blocks_per_inst, int pass, cudaStream_t s) {
+cudaError_t lsfix_launch(const Src& src, long long blocks, int pass, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  k_lsfix<DIM, Src><<<(unsigned)blocks, kLsfixThreads, 0, s>>>(src, pass, blocks_per_inst);
+  k_lsfix<DIM, Src><<<(unsigned)blocks, kLsfixThreads, 0, s>>>(src, pass);
   return cudaGetLastError();
 }
 
@@ -217,9 +217,9 @@ cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks,
   const One src{c};
   if (kern == KN_LSFIX) {
     switch (dim) {
-      case 1: return lsfix_launch<1, One>(src, blocks, (int)blocks, arg, s);
-      case 2: return lsfix_launch<2, One>(src, blocks, (int)blocks, arg, s);
-      case 3: return lsfix_launch<3, One>(src, blocks, (int)blocks, arg, s);
+      case 1: return lsfix_launch<1, One>(src, blocks, arg, s);
+      case 2: return lsfix_launch<2, One>(src, blocks, arg, s);
+      case 3: return lsfix_launch<3, One>(src, blocks, arg, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -231,15 +231,12 @@ cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks,
   }
 }
 
-// In a batch every instance gets blocks_per_inst blocks of k_lsfix (the batch's start offsets for that
-// kernel are k * blocks_per_inst).
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int blocks_per_inst, int arg,
-                                   cudaStream_t s) {
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s) {
   if (kern == KN_LSFIX) {
     switch (dim) {
-      case 1: return lsfix_launch<1, Many>(m, blocks, blocks_per_inst, arg, s);
-      case 2: return lsfix_launch<2, Many>(m, blocks, blocks_per_inst, arg, s);
-      case 3: return lsfix_launch<3, Many>(m, blocks, blocks_per_inst, arg, s);
+      case 1: return lsfix_launch<1, Many>(m, blocks, arg, s);
+      case 2: return lsfix_launch<2, Many>(m, blocks, arg, s);
+      case 3: return lsfix_launch<3, Many>(m, blocks, arg, s);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -81,6 +81,12 @@ def load(build_if_missing: bool = False):
     L.gdg_max_dt.argtypes = [vp, vp, vp, d, C.POINTER(d), vp]
     L.gdg_stage.argtypes = [vp, vp, vp, d, d, vp, vp, vp]
     L.gdg_ssprk3_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.gdg_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                   C.POINTER(vp)]
+    L.gdg_batch_step.argtypes = [vp, vp]
+    L.gdg_batch_profile.argtypes = [vp, i32]
+    L.gdg_batch_profile_read.argtypes = [vp, vp, vp]
+    L.gdg_batch_destroy.argtypes = [vp]
     L.gdg_clock_set.argtypes = [vp, d, d, d, vp]
     L.gdg_clock_get.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i64), vp]
     L.gdg_status.argtypes = [vp, C.POINTER(i32), i32, vp]
@@ -95,7 +101,8 @@ def load(build_if_missing: bool = False):
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_clock_set",
-              "gdg_clock_get", "gdg_status", "gdg_debug_export",
+              "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_profile", "gdg_batch_profile_read",
+              "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
               "gdg_max_dt_noalloc"):
         getattr(L, f).restype = C.c_int
@@ -297,6 +304,57 @@ class Solver:
         if getattr(self, "_h", None):
             load().gdg_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """gdg_batch: instances (Solver objects) advanced by fused SSP-RK3 steps in shared kernel launches.
+    states[k] is member k's state (updated in place), works[k] = (T1, T2) its workspace, bdatas[k] its
+    Dirichlet data or None.  The solvers and tensors are kept alive by the batch."""
+
+    def __init__(self, solvers, states, works, bdatas=None):
+        n = len(solvers)
+        if n == 0:
+            raise ValueError("empty batch")
+        bdatas = bdatas or [None] * n
+        for S, U, (T1, T2), bd in zip(solvers, states, works, bdatas):
+            S._check_state(U)
+            S._check_state(T1)
+            S._check_state(T2)
+            S._bdata(bd)
+        self._keep = (list(solvers), list(states), list(works), list(bdatas))
+        arr = C.c_void_p * n
+        h = arr(*[S._h.value for S in solvers])
+        u = arr(*[U.data_ptr() for U in states])
+        t1 = arr(*[w[0].data_ptr() for w in works])
+        t2 = arr(*[w[1].data_ptr() for w in works])
+        bd = arr(*[None if b is None else b.data_ptr() for b in bdatas])
+        out = C.c_void_p()
+        _check(load().gdg_batch_create(h, n, u, t1, t2, bd, C.byref(out)), "gdg_batch_create")
+        self._b = out
+        self.count = n
+
+    def step(self, stream=None):
+        _check(load().gdg_batch_step(self._b, _stream(stream)), "gdg_batch_step")
+
+    def profile(self, enable: bool):
+        _check(load().gdg_batch_profile(self._b, 1 if enable else 0), "gdg_batch_profile")
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(len(KERNELS))
+        cnt = np.zeros(len(KERNELS), np.int64)
+        _check(load().gdg_batch_profile_read(self._b, ms.ctypes.data, cnt.ctypes.data), "gdg_batch_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().gdg_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

@@ -1,0 +1,154 @@
+"""Batches (gdg_batch_*): instances of different sizes, data and end times advanced in shared launches
+give, bit for bit, the states and clocks of the same instances stepped alone with gdg_ssprk3_step (which
+test_gpu_step checks against the oracle); a member's result does not depend on who else is in the batch."""
+import numpy as np
+import pytest
+
+from paper_2402_04514_gb300 import assembly, workloads
+from tests.helpers import dirichlet_vortex_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_04514_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _riemann_instance(N, k, seed):
+    P = assembly.assemble_2d(N, N, k)
+    rng = np.random.default_rng(seed)
+    U = workloads.two_state_riemann(P.x[0], P.x[1], rng)
+    return P, U
+
+
+def _members(torch, specs):
+    """specs: (N, degree, seed, f): the member's end time is f times its first time step (inf: none).
+    Returns solvers, initial states (numpy) and t_end per member."""
+    from paper_2402_04514_gb300.gdg import Solver
+
+    out = []
+    for N, k, seed, f in specs:
+        P, U = _riemann_instance(N, k, seed)
+        S = Solver(P)
+        U = np.ascontiguousarray(U)
+        t_end = np.inf if not np.isfinite(f) else f * S.max_dt(torch.from_numpy(U).cuda(), 0.5)
+        out.append((S, U, t_end))
+    return out
+
+
+def _run_alone(torch, members, steps):
+    res = []
+    for S, U, t_end in members:
+        S.set_clock(0.0, t_end, 0.5)
+        Ud = torch.from_numpy(U.copy()).cuda()
+        work = (torch.empty_like(Ud), torch.empty_like(Ud))
+        for _ in range(steps):
+            S.step(Ud, work)
+        res.append((Ud.cpu().numpy(), S.clock()))
+    return res
+
+
+def _run_batch(torch, members, steps, order=None):
+    from paper_2402_04514_gb300.gdg import Batch
+
+    order = order or list(range(len(members)))
+    sel = [members[i] for i in order]
+    states, works = [], []
+    for S, U, t_end in sel:
+        S.set_clock(0.0, t_end, 0.5)
+        Ud = torch.from_numpy(U.copy()).cuda()
+        states.append(Ud)
+        works.append((torch.empty_like(Ud), torch.empty_like(Ud)))
+    B = Batch([m[0] for m in sel], states, works)
+    for _ in range(steps):
+        B.step()
+    torch.cuda.synchronize()
+    res = {}
+    for i, (S, _, _), Ud in zip(order, sel, states):
+        res[i] = (Ud.cpu().numpy(), S.clock())
+    B.close()
+    return res
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_batch_equals_each_member_alone(torch_cuda, degree):
+    """Members of ragged sizes (several blocks with a partial last one, and one smaller than a block),
+    two of which reach their end time inside the run: same bits and clocks as alone, in two batch
+    orders."""
+    torch = torch_cuda
+    specs = [(13, degree, 1, np.inf), (3, degree, 2, np.inf), (21, degree, 3, 2.5), (8, degree, 4, np.inf),
+             (17, degree, 5, 1.5), (4, degree, 6, np.inf), (11, degree, 7, np.inf)]
+    members = _members(torch, specs)
+    steps = 6
+    alone = _run_alone(torch, members, steps)
+    for order in (None, [4, 0, 6, 2, 5, 1, 3]):
+        got = _run_batch(torch, members, steps, order)
+        for i, (U_a, clk_a) in enumerate(alone):
+            U_b, clk_b = got[i]
+            assert np.array_equal(U_a, U_b), i
+            assert clk_a == clk_b, (i, clk_a, clk_b)
+    # the members with an end time inside the run stopped on it
+    for i, (S, U, t_end) in enumerate(members):
+        t, tau, steps_done = alone[i][1]
+        assert steps_done == steps
+        if np.isfinite(t_end):
+            assert t == t_end and tau == 0.0
+    for S, _, _ in members:
+        assert S.status() == 0
+
+
+def test_batch_with_dirichlet_members(torch_cuda):
+    """Members with Dirichlet boundary data (time-independent here) next to slip-wall members."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import Batch, Solver
+
+    P1, U1, bd1 = dirichlet_vortex_problem(9, 1)
+    P2, U2 = _riemann_instance(10, 1, 11)
+    S1, S2 = Solver(P1, gamma=5.0 / 3.0), Solver(P2)
+    b1 = bd1(0.0)
+    b1d = torch.from_numpy(np.ascontiguousarray(b1)).cuda()
+    ref = []
+    for S, U, bd in ((S1, U1, b1d), (S2, U2, None)):
+        S.set_clock(0.0, np.inf, 0.4)
+        Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+        work = (torch.empty_like(Ud), torch.empty_like(Ud))
+        for _ in range(4):
+            S.step(Ud, work, bdata=bd)
+        ref.append(Ud.cpu().numpy())
+    states, works = [], []
+    for S, U in ((S1, U1), (S2, U2)):
+        S.set_clock(0.0, np.inf, 0.4)
+        Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+        states.append(Ud)
+        works.append((torch.empty_like(Ud), torch.empty_like(Ud)))
+    B = Batch([S1, S2], states, works, [b1d, None])
+    for _ in range(4):
+        B.step()
+    for r, Ud in zip(ref, states):
+        assert np.array_equal(r, Ud.cpu().numpy())
+
+
+def test_batch_rejects_inconsistent_members(torch_cuda):
+    """Members of different element types, a member listed twice, and aliased buffers are refused."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import Batch, GdgError, Solver
+
+    (S1, U1, _), (S2, U2, _) = _members(torch, [(5, 1, 1, np.inf), (5, 2, 2, np.inf)])
+    Ua = torch.from_numpy(U1).cuda()
+    Ub = torch.from_numpy(U2).cuda()
+    wa = (torch.empty_like(Ua), torch.empty_like(Ua))
+    wb = (torch.empty_like(Ub), torch.empty_like(Ub))
+    with pytest.raises(GdgError):
+        Batch([S1, S2], [Ua, Ub], [wa, wb])
+    with pytest.raises(GdgError):
+        Batch([S1, S1], [Ua, Ua.clone()], [wa, (torch.empty_like(Ua), torch.empty_like(Ua))])
+    with pytest.raises(GdgError):
+        Batch([S1], [Ua], [(Ua, wa[1])])
