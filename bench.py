@@ -207,6 +207,109 @@ def run_batched(args):
     return 0
 
 
+def served_requests(count, rate, seed=2, n_max=64):
+    """The served stream: `count` requests with Poisson arrivals at `rate` per second, all from
+    default_rng(seed): Q1 or Q2 (even odds), N x N quads of [0,1]^2 with N log-uniform in [16, n_max], slip
+    walls, two-state Riemann data (as the batched workload) or the isentropic vortex of Sec. 6.2 scaled to the
+    unit square (even odds), end time uniform in [0.1, 1].  Yields (arrival_s, problem, U0, t_end)."""
+    import numpy as np
+
+    from paper_2402_04514_gb300 import assembly, workloads
+
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate)
+        k = 1 + int(rng.integers(0, 2))
+        N = int(round(16 * (n_max / 16.0) ** rng.uniform(0.0, 1.0)))
+        P = assembly.assemble_2d(N, N, k)
+        if rng.uniform() < 0.5:
+            U = workloads.two_state_riemann(P.x[0], P.x[1], rng)
+        else:
+            U = workloads.vortex(10.0 * P.x[0] - 5.0, 10.0 * P.x[1] - 5.0, 0.0, gamma=1.4)
+        yield t, P, np.ascontiguousarray(U), float(rng.uniform(0.1, 1.0))
+
+
+def run_served(args):
+    """Served stream: requests submitted at their arrival times to the continuous-batching server
+    (gdg_server), against the same stream solved one request at a time (each with gdg_ssprk3_step to its
+    end time, in arrival order).  Reports solves/s over the makespan and p50/p99 time-to-solution."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2402_04514_gb300.gdg import Server, Solver
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = list(served_requests(args.requests, args.rate, n_max=args.n_max))
+    dofs = sum(P.n for _, P, _, _ in reqs)
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v), q))
+
+    # continuous batching
+    srv = Server()
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def client():
+        for i, (ta, P, U, te) in enumerate(reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids[i] = srv.submit(P, U, te)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    infos = [srv.wait(r)[1] for r in ids]
+    srv.close()
+    tts = [i["t_done"] - i["t_submit"] for i in infos]
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    steps = sum(i["steps"] for i in infos)
+    flags = max(i["flags"] for i in infos)
+    status = max(i["status"] for i in infos)
+
+    # one at a time, in arrival order, each request as soon as it has arrived and the previous one is done
+    t1 = time.perf_counter()
+    tts1 = []
+    for ta, P, U, te in reqs:
+        now = time.perf_counter() - t1
+        if now < ta:
+            time.sleep(ta - now)
+        S = Solver(P)
+        S.set_clock(0.0, te, 0.5)
+        Ud = torch.from_numpy(U).cuda()
+        work = (torch.empty_like(Ud), torch.empty_like(Ud))
+        while True:
+            for _ in range(8):  # finished steps are no-ops: check the clock every 8 steps
+                S.step(Ud, work)
+            if S.clock()[0] >= te:
+                break
+        Ud.cpu()
+        tts1.append(time.perf_counter() - t1 - ta)
+        S.close()
+    span1 = time.perf_counter() - t1 - reqs[0][0]
+    clocks = sampler.stop()
+    line = {"metric": "served solves/s", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served_stream", "requests": len(reqs), "rate_per_s": args.rate,
+                       "mesh": f"N x N Q1/Q2 quads, N log-uniform in [16, {args.n_max}]",
+                       "t_end": "uniform in [0.1, 1]", "data": "Riemann or scaled vortex", "seed": 2,
+                       "dofs_total": dofs, "budget": "80% of free HBM"},
+            "tts_p50_s": pct(tts, 50), "tts_p99_s": pct(tts, 99), "makespan_s": span,
+            "one_at_a_time": {"value": len(reqs) / span1, "unit": "solves/s", "tts_p50_s": pct(tts1, 50),
+                              "tts_p99_s": pct(tts1, 99), "makespan_s": span1},
+            "speedup_vs_one_at_a_time": span1 / span, "clocks": clocks, "status_flags": flags,
+            "status": status}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(args, n):
     spec = WORKLOADS[args.workload]
     return {"workload": args.workload, "mesh": f"{spec['N']}x{spec['N']} quads", "degree": spec["k"],
@@ -221,7 +324,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="q2_1024_four_quadrant", choices=sorted(WORKLOADS) + ["batched_q1_riemann"])
+    ap.add_argument("--workload", default="q2_1024_four_quadrant",
+                    choices=sorted(WORKLOADS) + ["batched_q1_riemann", "served_stream"])
+    ap.add_argument("--requests", type=int, default=64, help="served workload: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
+    ap.add_argument("--n-max", type=int, default=64, help="served workload: largest N")
     ap.add_argument("--instances", type=int, default=512, help="batched workload: number of instances")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,6 +347,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_q1_riemann":
         return run_batched(args)
+    if args.workload == "served_stream":
+        return run_served(args)
 
     import numpy as np
     import torch

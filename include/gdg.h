@@ -113,6 +113,11 @@ void gdg_default_params(int32_t degree, gdg_params* out);
  * Errors: GDG_EINVAL (NULL), GDG_ENOTSUP, GDG_ESETUP, GDG_ENOMEM, GDG_ECUDA; *out is NULL on error. */
 int gdg_setup(const gdg_problem* prob, gdg_handle** out);
 
+/* Device bytes gdg_setup would allocate for prob (its arena: setup copies and scratch; the caller's
+ * state buffers are not included), without touching the device.  Reads row_ptr, col_idx and cij only.
+ * Errors: GDG_EINVAL. */
+int gdg_footprint(const gdg_problem* prob, int64_t* bytes);
+
 /* Replaces the method parameters of a handle (same validation as gdg_setup). */
 int gdg_set_params(gdg_handle* h, const gdg_params* params);
 
@@ -255,6 +260,57 @@ int gdg_batch_step(gdg_batch* b, void* stream);
 int gdg_batch_profile(gdg_batch* b, int32_t enable);
 int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches);
 void gdg_batch_destroy(gdg_batch* b);
+
+/* Serving: a request loop with continuous batching, for streams of independent solves that arrive over
+ * time (the paper solves one problem at a time).  gdg_server_create starts two host threads on the
+ * current device.  A preparation thread takes submitted requests in arrival order, each as soon as its
+ * device footprint (gdg_footprint plus three state buffers and its Dirichlet data) fits the HBM budget,
+ * runs gdg_setup and uploads its state.  A loop thread adds prepared requests to the batch of their
+ * kind (dim, n_loc, order, limiter passes), advances every batch by one fused SSP-RK3 step per iteration
+ * (gdg_batch_step: each member with its own time step, up to its own end time) and retires the members
+ * that reached their end time: state to the host, device memory freed, budget released for the next
+ * arrivals.  A request's state stays on the device from admission to completion, and requests that
+ * arrive while others run join the running batches at the next iteration.  Results are those of the
+ * request run alone with gdg_ssprk3_step to t_end.
+ *
+ * gdg_server_create: hbm_budget_bytes > 0 caps the device memory of admitted requests (<= 0: 80% of the
+ *   free device memory).  Errors: GDG_ENOMEM, GDG_ECUDA.
+ * gdg_server_submit: copies prob (as gdg_setup reads it), U0 (host [m][n]) and bdata (host [m][nb],
+ *   Dirichlet data used at every stage; NULL when no entry is Dirichlet), to be solved from t = 0 to t_end
+ *   at CFL number cfl; returns at once with *id.  Errors: GDG_EINVAL, GDG_ENOMEM (the request alone
+ *   exceeds the budget).  Setup errors are reported by gdg_server_wait.
+ * gdg_server_wait: blocks until request id is done or timeout_s seconds passed (timeout_s < 0: no limit;
+ *   GDG_ETIMEOUT then, and the request stays pending), copies its final state to U_out (host [m][n], may
+ *   be NULL) and its timings to *info (may be NULL), forgets the request and returns its status.
+ * gdg_server_stats: a snapshot of the queue, the active members and the memory in use.
+ * gdg_server_destroy: finishes every submitted request, stops the threads, frees everything (results
+ *   not waited for are dropped).
+ * Times are seconds since gdg_server_create on a monotonic clock. */
+typedef struct gdg_server gdg_server;
+typedef struct {
+  double t_submit;      /* submitted */
+  double t_start;       /* set up and joined a batch */
+  double t_done;        /* final state on the host */
+  double t_final;       /* simulated time reached (t_end) */
+  int64_t steps;        /* SSP-RK3 steps taken */
+  int32_t status;       /* GDG_OK or the error of its setup or run */
+  int32_t flags;        /* sticky device flags GDG_FLAG_* */
+  int64_t device_bytes; /* footprint counted against the budget */
+} gdg_request_info;
+typedef struct {
+  int64_t queued;       /* submitted, not yet in a batch */
+  int64_t active;       /* in a batch on the device */
+  int64_t bytes_in_use; /* footprint of admitted requests */
+  int64_t budget;
+  int64_t iterations;   /* loop iterations (one step of every batch each) */
+  double now;
+} gdg_server_info;
+int gdg_server_create(int64_t hbm_budget_bytes, gdg_server** out);
+int gdg_server_submit(gdg_server* s, const gdg_problem* prob, const double* U0, const double* bdata, double t_end,
+                      double cfl, int64_t* id);
+int gdg_server_wait(gdg_server* s, int64_t id, double timeout_s, double* U_out, gdg_request_info* info);
+int gdg_server_stats(gdg_server* s, gdg_server_info* info);
+void gdg_server_destroy(gdg_server* s);
 
 int gdg_get_info(gdg_handle* h, gdg_info* out);
 void gdg_destroy(gdg_handle* h);

@@ -93,6 +93,38 @@ struct Arena {
   }
 };
 
+// The device arena of a handle: every array with its element type and count (m = dim + 2 components,
+// ne canonical stencil edges, nel elements of nl nodes).  gdg_setup allocates it; gdg_footprint sizes it.
+#define GDG_ARENA(X)                                                                                       \
+  X(rowptr, int, n + 1) X(col, int, nnz) X(tr, int, nnz) X(cnorm, double, nnz) X(cn, double, dim * nnz)   \
+  X(mij, double, nnz) X(mu, double, nnz) X(mi, double, n) X(imi, double, n) X(ikm, double, n)             \
+  X(rm, double, n) X(rp, double, n) X(muB, double, n) X(bptr, int, n + 1) X(bnorm, double, nb)           \
+  X(bn, double, dim * nb) X(btype, int, nb) X(borig, int, nb) X(minv, double, nel * nl * nl)             \
+  X(ee, int, ne) X(ei, int, ne) X(G, double, m * nnz) X(barR, double, nnz) X(barS, double, nnz)          \
+  X(prim, double, gdg::NPRIM * n) X(dL, double, nnz) X(dB, double, nb) X(bbar, double, 2 * nb)            \
+  X(UL, double, m * n) X(RHSL, double, m * n) X(N, double, n) X(agg, double, 3 * n) X(A, double, m * nnz) \
+  X(AB, double, m * nb) X(bounds, double, 3 * n) X(l1, double, nnz) X(l1B, double, nb) X(l2, double, nnz) \
+  X(l2B, double, nb) X(U1, double, m * n) X(flags, unsigned, 4) X(tau, unsigned long long, 1)             \
+  X(lsq, int2, nnz + nb) X(clk, gdg::Clock, 1)
+
+struct Layout {
+#define GDG_F(name, T, cnt) size_t o_##name;
+  GDG_ARENA(GDG_F)
+#undef GDG_F
+  size_t total;
+};
+
+Layout make_layout(int dim, int64_t n, int64_t nnz, int64_t nb, int nl, int64_t ne, int64_t nel) {
+  const int64_t m = dim + 2;
+  Layout Lo;
+  Arena ar;
+#define GDG_F(name, T, cnt) Lo.o_##name = ar.take<T>((size_t)(cnt));
+  GDG_ARENA(GDG_F)
+#undef GDG_F
+  Lo.total = ar.off;
+  return Lo;
+}
+
 int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? GDG_ENOMEM : GDG_ECUDA; }
 
 // Parameter-dependent per-entry / per-node data: c_k h^{p_k} (Sec. 5.1) and r_h^{+-} (Sec. 5.4).
@@ -372,27 +404,11 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   if (int rc = param_arrays(h, h->params, pa); rc != GDG_OK) return fail(rc);
 
   // ---- device arena ----
-  Arena ar;
-  size_t o_rowptr = ar.take<int>(n + 1), o_col = ar.take<int>(nnz), o_tr = ar.take<int>(nnz);
-  size_t o_cnorm = ar.take<double>(nnz), o_cn = ar.take<double>((size_t)dim * nnz), o_mij = ar.take<double>(nnz);
-  size_t o_mu = ar.take<double>(nnz);
-  size_t o_mi = ar.take<double>(n), o_imi = ar.take<double>(n), o_ikm = ar.take<double>(n);
-  size_t o_rm = ar.take<double>(n), o_rp = ar.take<double>(n), o_muB = ar.take<double>(n);
-  size_t o_bptr = ar.take<int>(n + 1), o_bnorm = ar.take<double>(nb), o_bn = ar.take<double>((size_t)dim * nb);
-  size_t o_btype = ar.take<int>(nb), o_borig = ar.take<int>(nb);
-  size_t o_minv = ar.take<double>((size_t)nel * nl * nl);
-  size_t o_ee = ar.take<int>(ne), o_ei = ar.take<int>(ne);
-  size_t o_G = ar.take<double>((size_t)m * nnz), o_barR = ar.take<double>(nnz), o_barS = ar.take<double>(nnz);
-  size_t o_prim = ar.take<double>((size_t)gdg::NPRIM * n), o_dL = ar.take<double>(nnz), o_dB = ar.take<double>(nb);
-  size_t o_bbar = ar.take<double>(2 * nb), o_UL = ar.take<double>((size_t)m * n), o_RHSL = ar.take<double>((size_t)m * n);
-  size_t o_N = ar.take<double>(n), o_agg = ar.take<double>(3 * n);
-  size_t o_A = ar.take<double>((size_t)m * nnz), o_AB = ar.take<double>((size_t)m * nb);
-  size_t o_bounds = ar.take<double>(3 * n), o_l1 = ar.take<double>(nnz), o_l1B = ar.take<double>(nb);
-  size_t o_l2 = ar.take<double>(nnz), o_l2B = ar.take<double>(nb), o_U1 = ar.take<double>((size_t)m * n);
-  size_t o_flags = ar.take<unsigned>(4), o_tau = ar.take<unsigned long long>(1);
-  size_t o_lsq = ar.take<int2>(nnz + nb);
-  size_t o_clk = ar.take<gdg::Clock>(1);
-  h->arena_bytes = ar.off;
+  const Layout Lo = make_layout(dim, n, nnz, nb, nl, ne, nel);
+#define GDG_F(name, T, cnt) const size_t o_##name = Lo.o_##name;
+  GDG_ARENA(GDG_F)
+#undef GDG_F
+  h->arena_bytes = Lo.total;
   cudaError_t ce = cudaMalloc(&h->arena, h->arena_bytes);
   if (ce != cudaSuccess) {
     h->arena = nullptr;
@@ -514,6 +530,22 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
 
   if (int rc = upload_param_arrays(h, pa); rc != GDG_OK) return fail(rc);
   *out = h;
+  return GDG_OK;
+}
+
+int gdg_footprint(const gdg_problem* P, int64_t* bytes) {
+  if (!P || !bytes || P->dim < 1 || P->dim > 3 || P->n < 0 || P->nnz < 0 || P->nb < 0 || P->n_loc < 1)
+    return GDG_EINVAL;
+  if ((P->n > 0 && (!P->row_ptr || !P->col_idx)) || (P->nnz > 0 && !P->cij)) return GDG_EINVAL;
+  int64_t ne = 0;
+  for (int64_t i = 0; i < P->n; ++i)
+    for (int64_t q = P->row_ptr[i]; q < P->row_ptr[i + 1]; ++q) {
+      if (q < 0 || q >= P->nnz) return GDG_EINVAL;
+      bool nz = false;
+      for (int k = 0; k < P->dim; ++k) nz = nz || P->cij[(size_t)k * P->nnz + q] != 0.0;
+      if (nz && P->col_idx[q] > i) ++ne;
+    }
+  *bytes = (int64_t)make_layout(P->dim, P->n, P->nnz, P->nb, P->n_loc, ne, P->n / P->n_loc).total;
   return GDG_OK;
 }
 

@@ -55,6 +55,16 @@ class _Info(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class RequestInfo(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double), ("t_final", C.c_double),
+                ("steps", C.c_int64), ("status", C.c_int32), ("flags", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("bytes_in_use", C.c_int64), ("budget", C.c_int64),
+                ("iterations", C.c_int64), ("now", C.c_double)]
+
+
 _lib = None
 
 
@@ -87,6 +97,12 @@ def load(build_if_missing: bool = False):
     L.gdg_batch_profile.argtypes = [vp, i32]
     L.gdg_batch_profile_read.argtypes = [vp, vp, vp]
     L.gdg_batch_destroy.argtypes = [vp]
+    L.gdg_footprint.argtypes = [C.POINTER(_Problem), C.POINTER(i64)]
+    L.gdg_server_create.argtypes = [i64, C.POINTER(vp)]
+    L.gdg_server_submit.argtypes = [vp, C.POINTER(_Problem), vp, vp, d, d, C.POINTER(i64)]
+    L.gdg_server_wait.argtypes = [vp, i64, d, vp, C.POINTER(RequestInfo)]
+    L.gdg_server_stats.argtypes = [vp, C.POINTER(ServerInfo)]
+    L.gdg_server_destroy.argtypes = [vp]
     L.gdg_clock_set.argtypes = [vp, d, d, d, vp]
     L.gdg_clock_get.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(i64), vp]
     L.gdg_status.argtypes = [vp, C.POINTER(i32), i32, vp]
@@ -102,6 +118,7 @@ def load(build_if_missing: bool = False):
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_clock_set",
               "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_profile", "gdg_batch_profile_read",
+              "gdg_footprint", "gdg_server_create", "gdg_server_submit", "gdg_server_wait", "gdg_server_stats",
               "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
               "gdg_max_dt_noalloc"):
@@ -160,6 +177,33 @@ def fp64_throughput(stream=None) -> dict:
     return out
 
 
+def _problem_struct(P, gamma, params):
+    """gdg_problem for an assembled problem; returns it with the arrays it points into (keep them alive)."""
+    prm = {**default_params(P.degree), **(params or {})}
+    keep = dict(row_ptr=np.ascontiguousarray(P.row_ptr, np.int64), col_idx=np.ascontiguousarray(P.col_idx, np.int32),
+                cij=np.ascontiguousarray(P.cij, np.float64), coloc=np.ascontiguousarray(P.coloc, np.uint8),
+                mi=np.ascontiguousarray(P.mi, np.float64), MK=np.ascontiguousarray(P.MK, np.float64),
+                b_node=np.ascontiguousarray(P.b_node, np.int32), b_c=np.ascontiguousarray(P.b_c, np.float64),
+                b_type=np.ascontiguousarray(P.b_type, np.int32))
+
+    def hp(a):
+        return a.ctypes.data if a.size else None
+
+    cp = _Problem(P.dim, P.degree, P.n_loc, int(P.n), int(P.col_idx.shape[0]), int(P.b_node.shape[0]),
+                  hp(keep["row_ptr"]), hp(keep["col_idx"]), hp(keep["cij"]), hp(keep["coloc"]), hp(keep["mi"]),
+                  hp(keep["MK"]), hp(keep["b_node"]), hp(keep["b_c"]), hp(keep["b_type"]), gamma, P.omega_measure,
+                  Params(**prm))
+    return cp, keep
+
+
+def footprint(problem, gamma: float = 1.4, params: dict | None = None) -> int:
+    """gdg_footprint: device bytes gdg_setup would allocate for the problem."""
+    cp, keep = _problem_struct(problem, gamma, params)
+    b = C.c_int64()
+    _check(load().gdg_footprint(C.byref(cp), C.byref(b)), "gdg_footprint")
+    return b.value
+
+
 class Solver:
     """One mesh instance on the current CUDA device (a gdg handle)."""
 
@@ -175,21 +219,8 @@ class Solver:
         self.nnz = int(P.col_idx.shape[0])
         self.gamma = gamma
         self.has_dirichlet = bool((np.asarray(P.b_type) == BC_DIRICHLET).any())
-        prm = {**default_params(P.degree), **(params or {})}
-        keep = dict(row_ptr=np.ascontiguousarray(P.row_ptr, np.int64),
-                    col_idx=np.ascontiguousarray(P.col_idx, np.int32),
-                    cij=np.ascontiguousarray(P.cij, np.float64), coloc=np.ascontiguousarray(P.coloc, np.uint8),
-                    mi=np.ascontiguousarray(P.mi, np.float64), MK=np.ascontiguousarray(P.MK, np.float64),
-                    b_node=np.ascontiguousarray(P.b_node, np.int32), b_c=np.ascontiguousarray(P.b_c, np.float64),
-                    b_type=np.ascontiguousarray(P.b_type, np.int32))
-
-        def hp(a):
-            return a.ctypes.data if a.size else None
-
-        self._params = Params(**prm)
-        cp = _Problem(P.dim, P.degree, P.n_loc, self.n, self.nnz, self.nb, hp(keep["row_ptr"]), hp(keep["col_idx"]),
-                      hp(keep["cij"]), hp(keep["coloc"]), hp(keep["mi"]), hp(keep["MK"]), hp(keep["b_node"]),
-                      hp(keep["b_c"]), hp(keep["b_type"]), gamma, P.omega_measure, self._params)
+        cp, keep = _problem_struct(P, gamma, params)
+        self._params = cp.params
         h = C.c_void_p()
         _check(L.gdg_setup(C.byref(cp), C.byref(h)), "gdg_setup")
         self._h = h
@@ -355,6 +386,60 @@ class Batch:
         if getattr(self, "_b", None):
             load().gdg_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """gdg_server: continuous-batching request loop on the current device.  submit() returns an id at
+    once; wait(id) returns (final state, info dict).  hbm_budget <= 0: 80% of the free device memory."""
+
+    def __init__(self, hbm_budget: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("gdg needs a CUDA device; there is no CPU fallback")
+        out = C.c_void_p()
+        _check(load().gdg_server_create(int(hbm_budget), C.byref(out)), "gdg_server_create")
+        self._s = out
+        self._shapes = {}
+
+    def submit(self, problem, U0, t_end: float, cfl: float = 0.5, gamma: float = 1.4, params: dict | None = None,
+               bdata=None) -> int:
+        cp, keep = _problem_struct(problem, gamma, params)
+        U0 = np.ascontiguousarray(U0, np.float64)
+        assert U0.shape == (problem.dim + 2, problem.n)
+        bd = None if bdata is None else np.ascontiguousarray(bdata, np.float64)
+        rid = C.c_int64()
+        _check(load().gdg_server_submit(self._s, C.byref(cp), U0.ctypes.data if U0.size else None,
+                                        None if bd is None else bd.ctypes.data, t_end, cfl, C.byref(rid)),
+               "gdg_server_submit")
+        self._shapes[rid.value] = U0.shape
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0):
+        out = np.empty(self._shapes[rid])
+        info = RequestInfo()
+        rc = load().gdg_server_wait(self._s, rid, timeout, out.ctypes.data if out.size else None, C.byref(info))
+        if rc == 7:
+            raise TimeoutError(f"request {rid} not done after {timeout} s")
+        del self._shapes[rid]
+        _check(rc, f"request {rid}")
+        return out, {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+
+    def stats(self) -> dict:
+        i = ServerInfo()
+        _check(load().gdg_server_stats(self._s, C.byref(i)), "gdg_server_stats")
+        return {f: getattr(i, f) for f, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().gdg_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:
