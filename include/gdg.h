@@ -152,8 +152,8 @@ int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const doub
  * cfl > 0; resets the step count.  Synchronises the stream. */
 int gdg_clock_set(gdg_handle* h, double t, double t_end, double cfl, void* stream);
 
-/* Reads the clock: current time, tau of the last step, completed steps (any pointer may be NULL).
- * Synchronises the stream. */
+/* Reads the clock: current time, tau of the last step, completed steps (any pointer may be NULL; steps
+ * taken after t reached t_end change nothing and are not counted).  Synchronises the stream. */
 int gdg_clock_get(gdg_handle* h, double* t, double* tau, int64_t* steps, void* stream);
 
 /* Reads (and with clear != 0 resets) the sticky device flags GDG_FLAG_*; synchronises the stream. */

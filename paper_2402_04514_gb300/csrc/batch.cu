@@ -25,6 +25,9 @@ struct gdg_batch {
   bool profiling = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  // the step as a CUDA graph (captured on the first step on a non-default stream, replayed after)
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
 };
 
 namespace {
@@ -71,8 +74,34 @@ void release(gdg_batch* b) {
     cudaEventDestroy(r.b);
   }
   for (auto e : b->pool) cudaEventDestroy(e);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->mem) cudaFree(b->mem);
   delete b;
+}
+
+// The launches of one fused SSP-RK3 step of every member.
+int step_launches(gdg_batch* b, cudaStream_t s) {
+  const bool low_only = b->order == GDG_ORDER_LOW || (b->order == GDG_ORDER_LIMITED && b->passes == 0);
+  cudaError_t e;
+  for (int stage = 0; stage < 3; ++stage) {
+    auto go = [&](int id, int kern, int arg) {
+      return btimed(b, id, s, [&] { return launch_many(b, kern, stage, arg, s); });
+    };
+    if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_EDGE, gdg::KN_EDGE, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (stage == 0 && (e = go(GDG_K_TAU, gdg::KN_TAU, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_LOW, gdg::KN_LOW, low_only ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (low_only) continue;
+    if ((e = go(GDG_K_HIGH, gdg::KN_HIGH, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (b->order == GDG_ORDER_HIGH) continue;
+    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 0)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_LIMIT2, gdg::KN_LIMIT2, b->passes == 1 ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
+    if (b->passes == 1) continue;
+    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 1)) != cudaSuccess) return cuda_fail_b(e);
+    if ((e = go(GDG_K_FINAL, gdg::KN_FINAL, 0)) != cudaSuccess) return cuda_fail_b(e);
+  }
+  e = btimed(b, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_many(b->ctx[0], b->count, s); });
+  return e == cudaSuccess ? GDG_OK : cuda_fail_b(e);
 }
 
 }  // namespace
@@ -158,26 +187,29 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
 int gdg_batch_step(gdg_batch* b, void* stream) {
   if (!b) return GDG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool low_only = b->order == GDG_ORDER_LOW || (b->order == GDG_ORDER_LIMITED && b->passes == 0);
-  cudaError_t e;
-  for (int stage = 0; stage < 3; ++stage) {
-    auto go = [&](int id, int kern, int arg) {
-      return btimed(b, id, s, [&] { return launch_many(b, kern, stage, arg, s); });
-    };
-    if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail_b(e);
-    if ((e = go(GDG_K_EDGE, gdg::KN_EDGE, 0)) != cudaSuccess) return cuda_fail_b(e);
-    if (stage == 0 && (e = go(GDG_K_TAU, gdg::KN_TAU, 0)) != cudaSuccess) return cuda_fail_b(e);
-    if ((e = go(GDG_K_LOW, gdg::KN_LOW, low_only ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
-    if (low_only) continue;
-    if ((e = go(GDG_K_HIGH, gdg::KN_HIGH, 0)) != cudaSuccess) return cuda_fail_b(e);
-    if (b->order == GDG_ORDER_HIGH) continue;
-    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 0)) != cudaSuccess) return cuda_fail_b(e);
-    if ((e = go(GDG_K_LIMIT2, gdg::KN_LIMIT2, b->passes == 1 ? 1 : 0)) != cudaSuccess) return cuda_fail_b(e);
-    if (b->passes == 1) continue;
-    if ((e = go(GDG_K_LSFIX, gdg::KN_LSFIX, 1)) != cudaSuccess) return cuda_fail_b(e);
-    if ((e = go(GDG_K_FINAL, gdg::KN_FINAL, 0)) != cudaSuccess) return cuda_fail_b(e);
+  // Every step launches the same kernels with the same arguments (the members' time steps live on the
+  // device), so the step is captured once as a CUDA graph and replayed: one launch instead of ~26.  Not
+  // on the legacy default stream (which cannot be captured) nor while profiling.
+  if (b->profiling || s == nullptr || b->graph_failed) return step_launches(b, s);
+  if (!b->exec) {
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      b->graph_failed = true;
+      return step_launches(b, s);
+    }
+    const int rc = step_launches(b, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess && rc == GDG_OK && g) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != GDG_OK || e != cudaSuccess || !b->exec) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      b->graph_failed = true;
+      return step_launches(b, s);
+    }
   }
-  e = btimed(b, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_many(b->ctx[0], b->count, s); });
+  const cudaError_t e = cudaGraphLaunch(b->exec, s);
   return e == cudaSuccess ? GDG_OK : cuda_fail_b(e);
 }
 

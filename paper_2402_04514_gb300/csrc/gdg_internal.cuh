@@ -145,19 +145,34 @@ struct One {
     if (nblk) *nblk = gridDim.x;
     return c;
   }
+  // the length of the deferred line-search queue of a pass, read before the context is loaded
+  __device__ __forceinline__ unsigned queue_length(int pass, int* lb) const {
+    *lb = blockIdx.x;
+    return c.S.lsq_n[pass];
+  }
 };
 
 struct Many {
   const Ctx* ctx;   // device [ninst]
   const int* start; // device [ninst + 1] first block of each instance, then the total
   int ninst;
-  __device__ __forceinline__ const Ctx& get(Ctx* smem, int* lb, int* nblk = nullptr) const {
+  __device__ __forceinline__ int instance() const {
     int lo = 0, hi = ninst - 1;
     const int bx = (int)blockIdx.x;
     while (lo < hi) {  // the last instance starting at or before bx (instances without blocks are skipped)
       const int mid = (lo + hi + 1) >> 1;
       if (start[mid] <= bx) lo = mid; else hi = mid - 1;
     }
+    return lo;
+  }
+  __device__ __forceinline__ unsigned queue_length(int pass, int* lb) const {
+    const int k = instance();
+    *lb = (int)blockIdx.x - start[k];
+    return ctx[k].S.lsq_n[pass];
+  }
+  __device__ __forceinline__ const Ctx& get(Ctx* smem, int* lb, int* nblk = nullptr) const {
+    const int lo = instance();
+    const int bx = (int)blockIdx.x;
     *lb = bx - start[lo];
     if (nblk) *nblk = start[lo + 1] - start[lo];
     const int* src = reinterpret_cast<const int*>(ctx + lo);
@@ -186,10 +201,12 @@ inline long long kernel_blocks(int k, const Dev& D, int sms) {
       const int npb = high_nodes_per_block(D.n_loc);
       return npb > 0 ? ((long long)D.n + npb - 1) / npb : 0;
     }
-    case KN_LSFIX: {  // the queue length is only known on the device: a grid-stride over it
-      const long long want = ((long long)D.nnz + D.nb) / 32768 + 1;
-      const long long cap = 4LL * (sms > 0 ? sms : 1);
-      return D.n == 0 ? 0 : (want < cap ? want : cap);
+    case KN_LSFIX: {
+      // The queue length is only known on the device.  The grid covers a quarter of the entries (a
+      // deferred search per thread unless more than a quarter of the entries defer, when the threads take
+      // a few each), and its blocks beyond the queue return before loading their context.
+      (void)sms;
+      return D.n == 0 ? 0 : ((long long)D.nnz + D.nb + 4LL * kLsfixThreads - 1) / (4LL * kLsfixThreads);
     }
     default: return ((long long)D.n + kNodeThreads - 1) / kNodeThreads;
   }

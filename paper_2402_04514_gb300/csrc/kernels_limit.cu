@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb, blocks_per_inst;
+  if ((unsigned)src.queue_length(pass, &lb) <= (unsigned)lb * blockDim.x) return;  // a block with no item
   const Ctx& c = src.get(&sctx, &lb, &blocks_per_inst);
   if (finished(c)) return;
   const Dev& D = c.D;
@@ -164,8 +165,14 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
 }
 
 // End of a fused SSP-RK3 step for one instance's clock: t += tau of the step (the tau every kernel of the
-// step used), the step is counted, and the bound is reset for the next step.
+// step used), the step is counted, and the bound is reset for the next step.  Steps taken after t reached
+// t_end are no-ops and are not counted.
 __device__ __forceinline__ void clock_advance(Clock* k) {
+  if (!(k->t < k->t_end)) {  // finished before this step: the step did nothing and is not counted
+    k->tau = 0.0;
+    k->tau_bits = kTauNone;
+    return;
+  }
   const unsigned long long b = k->tau_bits;
   double tau = 0.0;
   bool clipped = false;

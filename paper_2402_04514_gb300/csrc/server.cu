@@ -171,7 +171,12 @@ __global__ void k_finished(gdg::Clock* const* clks, int n, int* finished) {
 struct LaneDev {
   gdg::Clock** clks = nullptr;  // device [cap]
   int cap = 0;
+  cudaStream_t stream = nullptr;  // each batch runs on its own stream, so batches of different kinds overlap
 };
+
+// Steps per completion check: a member that finished in between only takes no-op steps (its kernels
+// return at once), and the loop synchronises with the device once per kSteps steps.
+constexpr int kSteps = 4;
 
 int rebuild(Lane& L, LaneDev& LD, cudaStream_t s) {
   if (L.batch) gdg_batch_destroy(L.batch);
@@ -257,15 +262,23 @@ void loop_main(gdg_server* s) {
       Lane& L = kv.second;
       LaneDev& LD = lanedev[kv.first];
       if (L.members.empty()) continue;
+      if (!LD.stream && cudaStreamCreateWithFlags(&LD.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        LD.stream = nullptr;
+        for (Request* r : L.members) fail_member(s, r, GDG_ECUDA);
+        L.members.clear();
+        continue;
+      }
       if (L.dirty) {
-        const int rc = rebuild(L, LD, s->loop_stream);
+        const int rc = rebuild(L, LD, LD.stream);
         if (rc != GDG_OK) {  // the batch could not be formed: its members fail
           for (Request* r : L.members) fail_member(s, r, rc);
           L.members.clear();
           continue;
         }
       }
-      const int rc = gdg_batch_step(L.batch, s->loop_stream);
+      int rc = GDG_OK;
+      for (int q = 0; q < kSteps && rc == GDG_OK; ++q) rc = gdg_batch_step(L.batch, LD.stream);
       if (rc != GDG_OK) {
         for (Request* r : L.members) fail_member(s, r, rc);
         L.members.clear();
@@ -292,13 +305,15 @@ void loop_main(gdg_server* s) {
     bool ok = s->done_dev != nullptr || total == 0;
     for (auto& p : live) {
       const int n = (int)p.first->members.size();
-      if (ok && n > 0) k_finished<<<(n + 127) / 128, 128, 0, s->loop_stream>>>(p.second->clks, n, s->done_dev + off);
+      cudaStream_t ls = p.second->stream;
+      if (ok && n > 0) {
+        k_finished<<<(n + 127) / 128, 128, 0, ls>>>(p.second->clks, n, s->done_dev + off);
+        ok = cudaMemcpyAsync(s->done_host + off, s->done_dev + off, sizeof(int) * n, cudaMemcpyDeviceToHost, ls) ==
+             cudaSuccess;
+      }
       off += n;
     }
-    if (ok && total > 0)
-      ok = cudaMemcpyAsync(s->done_host, s->done_dev, sizeof(int) * total, cudaMemcpyDeviceToHost, s->loop_stream) ==
-           cudaSuccess;
-    ok = ok && cudaStreamSynchronize(s->loop_stream) == cudaSuccess;
+    for (auto& p : live) ok = (cudaStreamSynchronize(p.second->stream) == cudaSuccess) && ok;
     off = 0;
     for (auto& p : live) {
       Lane& L = *p.first;
@@ -351,8 +366,10 @@ void loop_main(gdg_server* s) {
   }
   for (auto& kv : lanes)
     if (kv.second.batch) gdg_batch_destroy(kv.second.batch);
-  for (auto& kv : lanedev)
+  for (auto& kv : lanedev) {
     if (kv.second.clks) cudaFree(kv.second.clks);
+    if (kv.second.stream) cudaStreamDestroy(kv.second.stream);
+  }
 }
 
 }  // namespace

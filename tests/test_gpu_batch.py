@@ -56,7 +56,7 @@ def _run_alone(torch, members, steps):
     return res
 
 
-def _run_batch(torch, members, steps, order=None):
+def _run_batch(torch, members, steps, order=None, stream=None):
     from paper_2402_04514_gb300.gdg import Batch
 
     order = order or list(range(len(members)))
@@ -68,8 +68,9 @@ def _run_batch(torch, members, steps, order=None):
         states.append(Ud)
         works.append((torch.empty_like(Ud), torch.empty_like(Ud)))
     B = Batch([m[0] for m in sel], states, works)
+    torch.cuda.synchronize()
     for _ in range(steps):
-        B.step()
+        B.step(stream=stream)  # on a stream of its own the step is captured once and replayed as a graph
     torch.cuda.synchronize()
     res = {}
     for i, (S, _, _), Ud in zip(order, sel, states):
@@ -82,15 +83,15 @@ def _run_batch(torch, members, steps, order=None):
 def test_batch_equals_each_member_alone(torch_cuda, degree):
     """Members of ragged sizes (several blocks with a partial last one, and one smaller than a block),
     two of which reach their end time inside the run: same bits and clocks as alone, in two batch
-    orders."""
+    orders, and with the step replayed as a CUDA graph on a stream of its own."""
     torch = torch_cuda
     specs = [(13, degree, 1, np.inf), (3, degree, 2, np.inf), (21, degree, 3, 2.5), (8, degree, 4, np.inf),
              (17, degree, 5, 1.5), (4, degree, 6, np.inf), (11, degree, 7, np.inf)]
     members = _members(torch, specs)
     steps = 6
     alone = _run_alone(torch, members, steps)
-    for order in (None, [4, 0, 6, 2, 5, 1, 3]):
-        got = _run_batch(torch, members, steps, order)
+    for order, stream in ((None, None), ([4, 0, 6, 2, 5, 1, 3], None), (None, torch.cuda.Stream())):
+        got = _run_batch(torch, members, steps, order, stream)
         for i, (U_a, clk_a) in enumerate(alone):
             U_b, clk_b = got[i]
             assert np.array_equal(U_a, U_b), i
@@ -98,9 +99,10 @@ def test_batch_equals_each_member_alone(torch_cuda, degree):
     # the members with an end time inside the run stopped on it
     for i, (S, U, t_end) in enumerate(members):
         t, tau, steps_done = alone[i][1]
-        assert steps_done == steps
-        if np.isfinite(t_end):
-            assert t == t_end and tau == 0.0
+        if np.isfinite(t_end):  # the steps after t_end did nothing and were not counted
+            assert t == t_end and tau == 0.0 and steps_done < steps
+        else:
+            assert steps_done == steps
     for S, _, _ in members:
         assert S.status() == 0
 
