@@ -182,6 +182,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         B.step()
         one_at_a_time()
+    schedule = B.schedule() if args.no_autotune else B.autotune(trials=1)  # states restored
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     t_batch = timed(B.step, args.steps)
@@ -196,7 +197,7 @@ def run_batched(args):
             "config": {"workload": "batched_q1_riemann", "instances": inst, "mesh": "N x N Q1 quads, N log-uniform "
                        "in [32, 512]", "dofs_total": dofs, "solve": f"{SOLVE_STEPS} SSP-RK3 steps",
                        "scheme": "convex-limited, 2 limiter passes", "cfl": 0.5, "seed": 1,
-                       "setup_s": round(setup_s, 1)},
+                       "setup_s": round(setup_s, 1), "schedule": schedule},
             "dof_stage_per_s": dofs * 3 * args.steps / t_batch,
             "one_at_a_time": {"value": inst * args.steps / SOLVE_STEPS / t_single, "unit": "solves/s",
                               "ms_per_step": 1e3 * t_single / args.steps,
@@ -332,6 +333,7 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--n-max", type=int, default=48, help="served workload: largest N")
     ap.add_argument("--skip-one-at-a-time", action="store_true", help="served workload: no one-at-a-time run")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--instances", type=int, default=512, help="batched workload: number of instances")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -390,6 +392,7 @@ def main():
         step()
     torch.cuda.synchronize()
     assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
+    schedule = solver.schedule() if args.no_autotune else solver.autotune(U, work, trials=1)  # state restored
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier()
@@ -484,7 +487,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_block(args, n), "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "config": {**config_block(args, n), "schedule": schedule}, "roofline": roofline,
+            "roofline_hbm": roofline_hbm,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
             "kernels": kernels, "status_flags": flags}
     print(json.dumps(line), flush=True)

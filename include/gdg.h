@@ -234,6 +234,27 @@ typedef struct {
 int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, const double* bdata, double cfl,
                        double* tau_out, void* stream);
 
+/* Launch schedule: threads per block of the one-thread-per-row (per-edge) kernels (128, 256 or 512),
+ * the largest element block of the element sweep (whole elements, 1..160 nodes) and the queue slots per
+ * thread of the deferred line-search grid (1..1024).  Defaults: 256 threads, 160 nodes, 4 slots.
+ * gdg_autotune picks them for one handle by timing: it saves U and the clock, runs 3 + 4 + 3 candidate
+ * schedules of (trials + 1) gdg_ssprk3_step each from that saved state (coordinate descent: row-kernel
+ * block sizes, then the element block, then the queue grid; each kernel keeps its fastest candidate),
+ * and restores U, the clock and the status flags.  It allocates one temporary state copy and
+ * synchronises the stream.  Arguments as gdg_ssprk3_step.  The schedule changes speed only: results are
+ * bit-identical under every schedule.  gdg_get_schedule / gdg_set_schedule read or install one (e.g. a
+ * schedule tuned on one instance for others of the same kind).  Errors: GDG_EINVAL (bad values),
+ * GDG_ENOMEM, GDG_ECUDA. */
+typedef struct {
+  int32_t prim_threads, edge_threads, tau_threads, low_threads, limit2_threads, final_threads, maxdt_threads;
+  int32_t high_block_cap;
+  int32_t lsfix_slots;
+} gdg_schedule;
+int gdg_autotune(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, int32_t trials,
+                 void* stream);
+int gdg_get_schedule(gdg_handle* h, gdg_schedule* out);
+int gdg_set_schedule(gdg_handle* h, const gdg_schedule* in);
+
 /* Batches: many independent instances advanced together.  The paper solves one problem at a time; a
  * batch runs the per-stage sweep of Sec. 6.1 for all its members in the same kernel launches (one
  * launch per kernel and stage over all instances; each block finds its instance from per-kernel block
@@ -259,6 +280,12 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
 int gdg_batch_step(gdg_batch* b, void* stream);
 int gdg_batch_profile(gdg_batch* b, int32_t enable);
 int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches);
+/* gdg_batch_autotune: as gdg_autotune for the whole batch (every member's state and clock saved and
+ * restored; one temporary copy of all members' states).  gdg_batch_get_schedule / _set_schedule as for
+ * a handle. */
+int gdg_batch_autotune(gdg_batch* b, int32_t trials, void* stream);
+int gdg_batch_get_schedule(gdg_batch* b, gdg_schedule* out);
+int gdg_batch_set_schedule(gdg_batch* b, const gdg_schedule* in);
 void gdg_batch_destroy(gdg_batch* b);
 
 /* Serving: a request loop with continuous batching, for streams of independent solves that arrive over

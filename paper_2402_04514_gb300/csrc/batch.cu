@@ -11,7 +11,8 @@
 #include "handle.cuh"
 
 struct gdg_batch {
-  int device = 0, dim = 0, n_loc = 0, order = 0, passes = 0, count = 0, sms = 1;
+  int device = 0, dim = 0, n_loc = 0, order = 0, passes = 0, count = 0;
+  gdg::Sched sched = gdg::default_sched();  // launch shapes (gdg_batch_autotune)
   std::vector<gdg_handle*> hs;
   void* mem = nullptr;                 // device: context tables and block offsets
   gdg::Ctx* ctx[3] = {nullptr, nullptr, nullptr};  // [count] contexts of the three stages
@@ -41,12 +42,36 @@ cudaError_t launch_many(const gdg_batch* b, int kern, int stage, int arg, cudaSt
   const gdg::Many m{b->ctx[stage], b->start[kern], b->count};
   const long long blocks = b->blocks[kern];
   switch (kern) {
-    case gdg::KN_HIGH: return gdg::launch_high_file_many(b->dim, m, blocks, b->n_loc, s);
+    case gdg::KN_HIGH:
+      return gdg::launch_high_file_many(b->dim, m, blocks, gdg::high_nodes_per_block(b->n_loc, b->sched.high_cap), s);
     case gdg::KN_LIMIT2:
     case gdg::KN_FINAL:
-    case gdg::KN_LSFIX: return gdg::launch_limit_file_many(kern, b->dim, m, blocks, arg, s);
-    default: return gdg::launch_low_file_many(kern, b->dim, m, blocks, arg, s);
+    case gdg::KN_LSFIX: return gdg::launch_limit_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], arg, s);
+    default: return gdg::launch_low_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], arg, s);
   }
+}
+
+// Block offsets of every kernel under the batch's schedule, uploaded into the batch's table (synchronous).
+int upload_offsets(gdg_batch* b) {
+  std::vector<int> start((size_t)gdg::KN_COUNT * (b->count + 1));
+  for (int kern = 0; kern < gdg::KN_COUNT; ++kern) {
+    long long acc = 0;
+    int* st = &start[(size_t)kern * (b->count + 1)];
+    for (int k = 0; k < b->count; ++k) {
+      st[k] = (int)acc;
+      acc += gdg::kernel_blocks(kern, b->hs[k]->D, b->sched);
+    }
+    st[b->count] = (int)acc;
+    if (acc > 0x7fffffffLL) return GDG_ENOTSUP;  // more blocks than a grid holds
+    b->blocks[kern] = acc;
+  }
+  if (cudaMemcpy(b->start[0], start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail_b(cudaErrorUnknown);
+  if (b->exec) {  // the captured step has the old shapes
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return GDG_OK;
 }
 
 template <class F>
@@ -136,12 +161,10 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
   b->order = h0->D.order;
   b->passes = h0->D.passes;
   b->count = count;
-  b->sms = h0->sms;
   b->hs.assign(handles, handles + count);
   // host tables: contexts of the three stages (Shu-Osher SSP-RK3, the last stage in place) and the
   // block offsets of every kernel
   std::vector<gdg::Ctx> ctx((size_t)3 * count);
-  std::vector<int> start((size_t)gdg::KN_COUNT * (count + 1));
   for (int k = 0; k < count; ++k) {
     gdg_handle* h = handles[k];
     const double* bd = bdata ? bdata[k] : nullptr;
@@ -149,21 +172,8 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
     ctx[(size_t)count + k] = make_ctx(h, T1[k], U[k], T2[k], bd, 0.75, 0.0, h->clk);
     ctx[(size_t)2 * count + k] = make_ctx(h, T2[k], U[k], U[k], bd, 1.0 / 3.0, 0.0, h->clk);
   }
-  for (int kern = 0; kern < gdg::KN_COUNT; ++kern) {
-    long long acc = 0;
-    int* st = &start[(size_t)kern * (count + 1)];
-    for (int k = 0; k < count; ++k) {
-      st[k] = (int)acc;
-      acc += gdg::kernel_blocks(kern, handles[k]->D, b->sms);
-    }
-    st[count] = (int)acc;
-    if (acc > 0x7fffffffLL) {
-      release(b);
-      return GDG_ENOTSUP;  // more blocks than a grid holds
-    }
-    b->blocks[kern] = acc;
-  }
-  const size_t ctx_bytes = sizeof(gdg::Ctx) * ctx.size(), start_bytes = sizeof(int) * start.size();
+  const size_t ctx_bytes = sizeof(gdg::Ctx) * ctx.size();
+  const size_t start_bytes = sizeof(int) * (size_t)gdg::KN_COUNT * (count + 1);
   cudaError_t e = cudaMalloc(&b->mem, ctx_bytes + start_bytes);
   if (e != cudaSuccess) {
     b->mem = nullptr;
@@ -172,14 +182,17 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
     return GDG_ENOMEM;
   }
   char* base = (char*)b->mem;
-  if ((e = cudaMemcpy(base, ctx.data(), ctx_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(base + ctx_bytes, start.data(), start_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+  if ((e = cudaMemcpy(base, ctx.data(), ctx_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
     release(b);
     return cuda_fail_b(e);
   }
   for (int st = 0; st < 3; ++st) b->ctx[st] = (gdg::Ctx*)base + (size_t)st * count;
   for (int kern = 0; kern < gdg::KN_COUNT; ++kern)
     b->start[kern] = (int*)(base + ctx_bytes) + (size_t)kern * (count + 1);
+  if (int rc = upload_offsets(b); rc != GDG_OK) {
+    release(b);
+    return rc;
+  }
   *out = b;
   return GDG_OK;
 }
@@ -243,6 +256,97 @@ int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches) {
   }
   b->recs.clear();
   return rc;
+}
+
+int gdg_batch_autotune(gdg_batch* b, int32_t trials, void* stream) {
+  if (!b) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the members' states (the third stage's output U of each member) and clocks
+  std::vector<double*> U(b->count);
+  std::vector<size_t> bytes(b->count), off(b->count);
+  size_t total = 0;
+  for (int k = 0; k < b->count; ++k) {
+    const gdg_handle* h = b->hs[k];
+    bytes[k] = sizeof(double) * (size_t)(h->dim + 2) * h->n;
+    off[k] = total;
+    total += bytes[k];
+  }
+  // member k's U is the stage-3 output: read it back from the context table
+  std::vector<gdg::Ctx> c3(b->count);
+  cudaError_t e = cudaMemcpy(c3.data(), b->ctx[2], sizeof(gdg::Ctx) * b->count, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail_b(e);
+  for (int k = 0; k < b->count; ++k) U[k] = c3[k].Uout;
+  char* save = nullptr;
+  if ((e = cudaMalloc(&save, std::max<size_t>(total, 1))) != cudaSuccess) {
+    cudaGetLastError();
+    return GDG_ENOMEM;
+  }
+  std::vector<gdg::Clock> clk0(b->count), tune(b->count);
+  std::vector<unsigned> flags0(b->count);
+  for (int k = 0; k < b->count && e == cudaSuccess; ++k) {
+    if (bytes[k]) e = cudaMemcpyAsync(save + off[k], U[k], bytes[k], cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&clk0[k], b->hs[k]->clk, sizeof(gdg::Clock), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&flags0[k], b->hs[k]->S.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(save);
+    return cuda_fail_b(e);
+  }
+  for (int k = 0; k < b->count; ++k) {  // members that already reached t_end would time no-op steps
+    tune[k] = clk0[k];
+    tune[k].t_end = INFINITY;
+    tune[k].tau_bits = gdg::kTauNone;
+  }
+  auto put_back = [&](const std::vector<gdg::Clock>& ck) -> int {
+    cudaError_t r = cudaSuccess;
+    for (int k = 0; k < b->count && r == cudaSuccess; ++k) {
+      if (bytes[k]) r = cudaMemcpyAsync(U[k], save + off[k], bytes[k], cudaMemcpyDeviceToDevice, s);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(b->hs[k]->clk, &ck[k], sizeof(gdg::Clock), cudaMemcpyHostToDevice, s);
+      if (r == cudaSuccess)
+        r = cudaMemcpyAsync(b->hs[k]->S.flags, &flags0[k], sizeof(unsigned), cudaMemcpyHostToDevice, s);
+    }
+    if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+    return r == cudaSuccess ? GDG_OK : cuda_fail_b(r);
+  };
+  const bool prof0 = b->profiling;
+  gdg_batch_profile(b, 1);
+  int rc = autotune_schedule(
+      b->sched, b->n_loc, trials,
+      [&](const gdg::Sched& sc) {
+        b->sched = sc;
+        return upload_offsets(b);
+      },
+      [&] { return gdg_batch_step(b, stream); },
+      [&](double* ms) {
+        double tot[GDG_NKERNELS];
+        int64_t cnt[GDG_NKERNELS];
+        const int r = gdg_batch_profile_read(b, tot, cnt);
+        for (int k = 0; k < GDG_NKERNELS; ++k) ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;
+        return r;
+      },
+      [&] { return put_back(tune); });
+  gdg_batch_profile(b, prof0 ? 1 : 0);
+  const int rc2 = put_back(clk0);
+  cudaFree(save);
+  return rc != GDG_OK ? rc : rc2;
+}
+
+int gdg_batch_get_schedule(gdg_batch* b, gdg_schedule* out) {
+  if (!b || !out) return GDG_EINVAL;
+  sched_to_public(b->sched, out);
+  return GDG_OK;
+}
+
+int gdg_batch_set_schedule(gdg_batch* b, const gdg_schedule* in) {
+  if (!b || !in) return GDG_EINVAL;
+  gdg::Sched sc;
+  if (!sched_from_public(in, &sc)) return GDG_EINVAL;
+  b->sched = sc;
+  return upload_offsets(b);
 }
 
 void gdg_batch_destroy(gdg_batch* b) {

@@ -524,8 +524,6 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     c0.cfl = 0.5;
     if ((ce = cudaMemcpy(h->clk, &c0, sizeof(c0), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(cuda_fail(ce));
   }
-  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (h->sms < 1) h->sms = 1;
   S.tau_bits = (unsigned long long*)ptr(o_tau);
 
   if (int rc = upload_param_arrays(h, pa); rc != GDG_OK) return fail(rc);
@@ -564,10 +562,10 @@ int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, 
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->S.tau_bits, 0x7f, sizeof(unsigned long long), s)) != cudaSuccess) return cuda_fail(e);
   const gdg::Ctx c = make_ctx(h, U, nullptr, nullptr, bdata, 0.0, 0.0, nullptr);
-  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_one(gdg::KN_PRIM, h->dim, c, 0, h->sms, s); })) !=
+  if ((e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_one(gdg::KN_PRIM, h->dim, c, 0, h->sched, s); })) !=
       cudaSuccess)
     return cuda_fail(e);
-  if ((e = timed(h, GDG_K_MAXDT, s, [&] { return gdg::launch_one(gdg::KN_MAXDT, h->dim, c, 0, h->sms, s); })) !=
+  if ((e = timed(h, GDG_K_MAXDT, s, [&] { return gdg::launch_one(gdg::KN_MAXDT, h->dim, c, 0, h->sched, s); })) !=
       cudaSuccess)
     return cuda_fail(e);
   unsigned long long bits = 0;
@@ -588,7 +586,7 @@ static int run_stage(gdg_handle* h, const gdg::Ctx& c, bool with_tau, cudaStream
   const gdg::Dev& D = h->D;
   cudaError_t e;
   auto go = [&](int id, int kern, int arg) {
-    return timed(h, id, s, [&] { return gdg::launch_one(kern, dim, c, arg, h->sms, s); });
+    return timed(h, id, s, [&] { return gdg::launch_one(kern, dim, c, arg, h->sched, s); });
   };
   const bool low_only = D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0);
   if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail(e);
@@ -660,6 +658,78 @@ int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const doub
   if (int rc = run_stage(h, c3, false, s); rc != GDG_OK) return rc;
   cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, s); });
   return e == cudaSuccess ? GDG_OK : cuda_fail(e);
+}
+
+int gdg_autotune(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, int32_t trials,
+                 void* stream) {
+  if (!h || ((!U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
+  if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  if (h->n == 0) return GDG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)(h->dim + 2) * h->n;
+  double* save = nullptr;
+  cudaError_t e = cudaMalloc(&save, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GDG_ENOMEM;
+  }
+  gdg::Clock clk0{};
+  unsigned flags0 = 0;
+  if ((e = cudaMemcpyAsync(save, U, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&clk0, h->clk, sizeof(clk0), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&flags0, h->S.flags, sizeof(flags0), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cudaFree(save);
+    return cuda_fail(e);
+  }
+  gdg::Clock tune_clk = clk0;  // an instance that already reached t_end would time no-op steps
+  tune_clk.t_end = INFINITY;
+  tune_clk.tau_bits = gdg::kTauNone;
+  auto put_back = [&](const gdg::Clock& ck) -> int {
+    cudaError_t r;
+    if ((r = cudaMemcpyAsync(U, save, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+        (r = cudaMemcpyAsync(h->clk, &ck, sizeof(ck), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (r = cudaMemcpyAsync(h->S.flags, &flags0, sizeof(flags0), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (r = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(r);
+    return GDG_OK;
+  };
+  const bool prof0 = h->profiling;
+  gdg_profile(h, 1);
+  int rc = autotune_schedule(
+      h->sched, h->n_loc, trials,
+      [&](const gdg::Sched& sc) {
+        h->sched = sc;
+        return GDG_OK;
+      },
+      [&] { return gdg_ssprk3_step(h, U, T1, T2, bdata, stream); },
+      [&](double* ms) {
+        double tot[GDG_NKERNELS];
+        int64_t cnt[GDG_NKERNELS];
+        const int r = gdg_profile_read(h, tot, cnt);
+        for (int k = 0; k < GDG_NKERNELS; ++k) ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;
+        return r;
+      },
+      [&] { return put_back(tune_clk); });
+  gdg_profile(h, prof0 ? 1 : 0);
+  const int rc2 = put_back(clk0);
+  cudaFree(save);
+  return rc != GDG_OK ? rc : rc2;
+}
+
+int gdg_get_schedule(gdg_handle* h, gdg_schedule* out) {
+  if (!h || !out) return GDG_EINVAL;
+  sched_to_public(h->sched, out);
+  return GDG_OK;
+}
+
+int gdg_set_schedule(gdg_handle* h, const gdg_schedule* in) {
+  if (!h || !in) return GDG_EINVAL;
+  gdg::Sched sc;
+  if (!sched_from_public(in, &sc)) return GDG_EINVAL;
+  h->sched = sc;
+  return GDG_OK;
 }
 
 int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream) {

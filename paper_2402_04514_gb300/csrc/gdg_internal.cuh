@@ -183,57 +183,78 @@ struct Many {
   }
 };
 
-// Kernels of the sweep and their block counts per instance (host and device agree on these).
+// Kernels of the sweep and their launch shapes.
 enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL, KN_LSFIX, KN_TAU, KN_COUNT };
-constexpr int kNodeThreads = 256;  // one thread per node or edge
-constexpr int kHighMaxBlock = 160; // element sweep: whole elements per block
+constexpr int kRowMaxThreads = 512;  // one-thread-per-row / per-edge kernels: 128, 256 or 512 threads
+constexpr int kHighMaxBlock = 160;   // element sweep: whole elements, at most this many nodes per block
 constexpr int kLsfixThreads = 128;
 
-__host__ __device__ inline int high_nodes_per_block(int n_loc) { return (kHighMaxBlock / n_loc) * n_loc; }
-__host__ __device__ inline int high_threads(int n_loc) {
-  int t = (high_nodes_per_block(n_loc) + 31) / 32 * 32;
+// The launch schedule: threads per block of each one-thread-per-row kernel (KN_EDGE: per edge), the
+// largest element block of the element sweep (whole elements, <= kHighMaxBlock nodes), and how many
+// queue slots per thread the deferred line-search grid is sized for.  The defaults are what an untuned
+// handle or batch runs; gdg_autotune / gdg_batch_autotune pick others by timing.
+struct Sched {
+  int bt[KN_COUNT];
+  int high_cap;
+  int lsfix_slots;
+};
+inline Sched default_sched() {
+  Sched sc;
+  for (int k = 0; k < KN_COUNT; ++k) sc.bt[k] = 256;
+  sc.high_cap = kHighMaxBlock;
+  sc.lsfix_slots = 4;
+  return sc;
+}
+__host__ __device__ inline int high_nodes_per_block(int n_loc, int cap) { return n_loc > 0 ? (cap / n_loc) * n_loc : 0; }
+__host__ __device__ inline int high_threads(int npb) {
+  const int t = (npb + 31) / 32 * 32;
   return t > kHighMaxBlock ? kHighMaxBlock : t;
 }
-inline long long kernel_blocks(int k, const Dev& D, int sms) {
+inline long long kernel_blocks(int k, const Dev& D, const Sched& sc) {
   switch (k) {
-    case KN_EDGE: return ((long long)D.ne + kNodeThreads - 1) / kNodeThreads;
+    case KN_EDGE: return ((long long)D.ne + sc.bt[k] - 1) / sc.bt[k];
     case KN_HIGH: {
-      const int npb = high_nodes_per_block(D.n_loc);
+      const int npb = high_nodes_per_block(D.n_loc, sc.high_cap);
       return npb > 0 ? ((long long)D.n + npb - 1) / npb : 0;
     }
     case KN_LSFIX: {
-      // The queue length is only known on the device.  The grid covers a quarter of the entries (a
-      // deferred search per thread unless more than a quarter of the entries defer, when the threads take
-      // a few each), and its blocks beyond the queue return before loading their context.
-      (void)sms;
-      return D.n == 0 ? 0 : ((long long)D.nnz + D.nb + 4LL * kLsfixThreads - 1) / (4LL * kLsfixThreads);
+      // The queue length is only known on the device.  The grid covers the entries at lsfix_slots per
+      // thread (a deferred search per thread unless more than that share of the entries defer, when the
+      // threads take a few each), and its blocks beyond the queue return before loading their context.
+      const long long per_block = (long long)kLsfixThreads * sc.lsfix_slots;
+      return D.n == 0 ? 0 : ((long long)D.nnz + D.nb + per_block - 1) / per_block;
     }
-    default: return ((long long)D.n + kNodeThreads - 1) / kNodeThreads;
+    default: return ((long long)D.n + sc.bt[k] - 1) / sc.bt[k];
   }
 }
 
 // Kernel launchers of each file, dim in 1..3: one instance (context by value) or a batch (Many; blocks =
 // the batch's total for that kernel).  arg: write_out for KN_LOW (the stage ends after U^L), last for
-// KN_LIMIT2 (one limiter pass only), the pass (0 or 1) for KN_LSFIX.
-cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s);
-cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s);
-cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, cudaStream_t s);
-cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int n_loc, cudaStream_t s);
-cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s);
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s);
+// KN_LIMIT2 (one limiter pass only), the pass (0 or 1) for KN_LSFIX.  threads: the block size of a
+// one-thread-per-row kernel; npb: nodes per element block of KN_HIGH.
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+                            cudaStream_t s);
+cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+                                 cudaStream_t s);
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s);
+cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int npb, cudaStream_t s);
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+                              cudaStream_t s);
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+                                   cudaStream_t s);
 // End of a fused SSP-RK3 step: advances the clock(s) (kernels_limit.cu).
 cudaError_t launch_clock_one(Clock* clk, cudaStream_t s);
 cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);
 
-// One kernel of the sweep for one instance, with the block count of kernel_blocks.
-inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, int sms, cudaStream_t s) {
-  const long long blocks = kernel_blocks(kern, c.D, sms);
+// One kernel of the sweep for one instance, shaped by the schedule.
+inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sched& sc, cudaStream_t s) {
+  const long long blocks = kernel_blocks(kern, c.D, sc);
   switch (kern) {
-    case KN_HIGH: return launch_high_file(dim, c, blocks, s);
+    case KN_HIGH: return launch_high_file(dim, c, blocks, high_nodes_per_block(c.D.n_loc, sc.high_cap), s);
     case KN_LIMIT2:
     case KN_FINAL:
-    case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, arg, s);
-    default: return launch_low_file(kern, dim, c, blocks, arg, s);
+    case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
+    default: return launch_low_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
   }
 }
 

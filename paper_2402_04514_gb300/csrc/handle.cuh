@@ -31,7 +31,7 @@ struct gdg_handle {
   bool profiling = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  int sms = 1;                   // multiprocessors of the device (grid of the deferred line searches)
+  gdg::Sched sched = gdg::default_sched();  // launch shapes (gdg_autotune)
   gdg::Clock* clk = nullptr;     // device clock of the fused step (in the arena)
 };
 
@@ -82,3 +82,113 @@ inline gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Uba
   return c;
 }
 
+
+// Launch-shape autotuning shared by handles and batches (gdg_autotune, gdg_batch_autotune).  Coordinate
+// descent over three groups of knobs, each candidate timed over `trials` fused steps from the same saved
+// state (restore() puts state and clocks back before every candidate and at the end):
+//   1. threads per block of the one-thread-per-row/edge kernels, 128, 256 or 512, chosen per kernel
+//      (all row kernels take the candidate together; each keeps its own fastest);
+//   2. the element sweep's block cap (whole elements of n_loc nodes), among the caps that give
+//      different blocks;
+//   3. the queue slots per thread of the deferred line-search grid, 1, 4 or 16.
+// apply(sc) installs a schedule, step() runs one fused step with kernel timing on, kernel_ms(ms) returns
+// the mean ms per launch of each GDG_K_* kernel since the last call.
+template <class Apply, class Step, class Read, class Restore>
+int autotune_schedule(gdg::Sched& sched, int n_loc, int trials, Apply apply, Step step, Read kernel_ms,
+                      Restore restore) {
+  if (trials < 1) trials = 1;
+  static const int row_kern[][2] = {{gdg::KN_PRIM, GDG_K_PRIM},   {gdg::KN_EDGE, GDG_K_EDGE},
+                                    {gdg::KN_TAU, GDG_K_TAU},     {gdg::KN_LOW, GDG_K_LOW},
+                                    {gdg::KN_LIMIT2, GDG_K_LIMIT2}, {gdg::KN_FINAL, GDG_K_FINAL}};
+  gdg::Sched sc = sched;
+  double ms[GDG_NKERNELS];
+  auto trial = [&](const gdg::Sched& cand, double* out) -> int {
+    if (int rc = restore(); rc != GDG_OK) return rc;
+    if (int rc = apply(cand); rc != GDG_OK) return rc;
+    if (int rc = step(); rc != GDG_OK) return rc;  // warm-up: first launches of new shapes
+    if (int rc = kernel_ms(out); rc != GDG_OK) return rc;
+    for (int t = 0; t < trials; ++t)
+      if (int rc = step(); rc != GDG_OK) return rc;
+    return kernel_ms(out);
+  };
+  // 1. row kernels
+  const int bts[3] = {128, 256, 512};
+  double best_row[6];
+  for (int r = 0; r < 6; ++r) best_row[r] = 1e300;
+  for (int bt : bts) {
+    gdg::Sched cand = sc;
+    for (auto& rk : row_kern) cand.bt[rk[0]] = bt;
+    if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
+    for (int r = 0; r < 6; ++r)
+      if (ms[row_kern[r][1]] > 0.0 && ms[row_kern[r][1]] < best_row[r]) {
+        best_row[r] = ms[row_kern[r][1]];
+        sc.bt[row_kern[r][0]] = bt;
+      }
+  }
+  // 2. element sweep block cap
+  double best = 1e300;
+  int last_npb = -1, best_cap = sc.high_cap;
+  for (int cap : {64, 96, 128, gdg::kHighMaxBlock}) {
+    const int npb = gdg::high_nodes_per_block(n_loc, cap);
+    if (npb < 1 || npb == last_npb) continue;
+    last_npb = npb;
+    gdg::Sched cand = sc;
+    cand.high_cap = cap;
+    if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
+    if (ms[GDG_K_HIGH] > 0.0 && ms[GDG_K_HIGH] < best) {
+      best = ms[GDG_K_HIGH];
+      best_cap = cap;
+    }
+  }
+  sc.high_cap = best_cap;
+  // 3. deferred line-search grid
+  best = 1e300;
+  int best_slots = sc.lsfix_slots;
+  for (int slots : {1, 4, 16}) {
+    gdg::Sched cand = sc;
+    cand.lsfix_slots = slots;
+    if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
+    if (ms[GDG_K_LSFIX] < best) {
+      best = ms[GDG_K_LSFIX];
+      best_slots = slots;
+    }
+  }
+  sc.lsfix_slots = best_slots;
+  if (int rc = restore(); rc != GDG_OK) return rc;
+  if (int rc = apply(sc); rc != GDG_OK) return rc;
+  sched = sc;
+  return GDG_OK;
+}
+
+// Public <-> internal schedule.
+inline void sched_to_public(const gdg::Sched& sc, gdg_schedule* out) {
+  out->prim_threads = sc.bt[gdg::KN_PRIM];
+  out->edge_threads = sc.bt[gdg::KN_EDGE];
+  out->tau_threads = sc.bt[gdg::KN_TAU];
+  out->low_threads = sc.bt[gdg::KN_LOW];
+  out->limit2_threads = sc.bt[gdg::KN_LIMIT2];
+  out->final_threads = sc.bt[gdg::KN_FINAL];
+  out->maxdt_threads = sc.bt[gdg::KN_MAXDT];
+  out->high_block_cap = sc.high_cap;
+  out->lsfix_slots = sc.lsfix_slots;
+}
+
+inline bool sched_from_public(const gdg_schedule* in, gdg::Sched* sc) {
+  const int32_t t[7] = {in->prim_threads, in->edge_threads,  in->tau_threads,  in->low_threads,
+                        in->limit2_threads, in->final_threads, in->maxdt_threads};
+  for (int32_t v : t)
+    if (v != 128 && v != 256 && v != 512) return false;
+  if (in->high_block_cap < 1 || in->high_block_cap > gdg::kHighMaxBlock) return false;
+  if (in->lsfix_slots < 1 || in->lsfix_slots > 1024) return false;
+  *sc = gdg::default_sched();
+  sc->bt[gdg::KN_PRIM] = in->prim_threads;
+  sc->bt[gdg::KN_EDGE] = in->edge_threads;
+  sc->bt[gdg::KN_TAU] = in->tau_threads;
+  sc->bt[gdg::KN_LOW] = in->low_threads;
+  sc->bt[gdg::KN_LIMIT2] = in->limit2_threads;
+  sc->bt[gdg::KN_FINAL] = in->final_threads;
+  sc->bt[gdg::KN_MAXDT] = in->maxdt_threads;
+  sc->high_cap = in->high_block_cap;
+  sc->lsfix_slots = in->lsfix_slots;
+  return true;
+}

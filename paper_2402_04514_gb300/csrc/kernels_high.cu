@@ -23,7 +23,7 @@ constexpr int kMaxBlock = kHighMaxBlock;
 //     searches that need the bracketed iteration are queued for k_lsfix.
 // With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src) {
+__global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_block) {
   constexpr int M = DIM + 2;
   __shared__ double sR[M][kMaxBlock];
   __shared__ double sdU[M][kMaxBlock];
@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src) {
   const Scratch& S = c.S;
   const double* U = c.U;
   const double* bdata = c.bdata;
-  const int nodes_per_block = high_nodes_per_block(D.n_loc);
   const int t = threadIdx.x;
   const int i = lb * nodes_per_block + t;
   const bool valid = t < nodes_per_block && i < D.n;
@@ -181,31 +180,31 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src) {
 }
 
 template <int DIM, class Src>
-cudaError_t high_launch(const Src& src, long long blocks, int n_loc, cudaStream_t s) {
+cudaError_t high_launch(const Src& src, long long blocks, int npb, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  if (high_nodes_per_block(n_loc) < 1) return cudaErrorInvalidValue;
-  k_high<DIM, Src><<<(unsigned)blocks, high_threads(n_loc), 0, s>>>(src);
+  if (npb < 1 || npb > kMaxBlock) return cudaErrorInvalidValue;
+  k_high<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// All instances of a batch share n_loc (it sets the block shape).
-cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, cudaStream_t s) {
+// npb: nodes per block, whole elements (all instances of a batch share n_loc, hence the block shape).
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s) {
   const One src{c};
   switch (dim) {
-    case 1: return high_launch<1, One>(src, blocks, c.D.n_loc, s);
-    case 2: return high_launch<2, One>(src, blocks, c.D.n_loc, s);
-    case 3: return high_launch<3, One>(src, blocks, c.D.n_loc, s);
+    case 1: return high_launch<1, One>(src, blocks, npb, s);
+    case 2: return high_launch<2, One>(src, blocks, npb, s);
+    case 3: return high_launch<3, One>(src, blocks, npb, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int n_loc, cudaStream_t s) {
+cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int npb, cudaStream_t s) {
   switch (dim) {
-    case 1: return high_launch<1, Many>(m, blocks, n_loc, s);
-    case 2: return high_launch<2, Many>(m, blocks, n_loc, s);
-    case 3: return high_launch<3, Many>(m, blocks, n_loc, s);
+    case 1: return high_launch<1, Many>(m, blocks, npb, s);
+    case 2: return high_launch<2, Many>(m, blocks, npb, s);
+    case 3: return high_launch<3, Many>(m, blocks, npb, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,7 +6,7 @@ namespace gdg {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches 128, 256 or 512
 
 // Sweep C: l_ij = min(l_ij^(i), l_ji^(j)) (Lemma ConsInvariants needs l_ij = l_ji);
 // U^(1)_i = U^L_i + (sum_j l_ij A_ij + sum_k l_i^k A_i^k) / m_i; then the second pass limits the
@@ -200,57 +200,38 @@ __global__ void k_clock_many(const Ctx* ctx, int ninst) {
 }
 
 template <int DIM, class Src>
-cudaError_t limit_launch(int kern, const Src& src, long long blocks, int arg, cudaStream_t s) {
+cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads, int arg, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
+  if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
-    case KN_LIMIT2: k_limit2<DIM, Src><<<g, kThreads, 0, s>>>(src, arg); break;
-    case KN_FINAL: k_final<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
+    case KN_LIMIT2: k_limit2<DIM, Src><<<g, threads, 0, s>>>(src, arg); break;
+    case KN_FINAL: k_final<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_LSFIX: k_lsfix<DIM, Src><<<g, kLsfixThreads, 0, s>>>(src, arg); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-template <int DIM, class Src>
-cudaError_t lsfix_launch(const Src& src, long long blocks, int pass, cudaStream_t s) {
-  if (blocks <= 0) return cudaSuccess;
-  k_lsfix<DIM, Src><<<(unsigned)blocks, kLsfixThreads, 0, s>>>(src, pass);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s) {
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+                              cudaStream_t s) {
   const One src{c};
-  if (kern == KN_LSFIX) {
-    switch (dim) {
-      case 1: return lsfix_launch<1, One>(src, blocks, arg, s);
-      case 2: return lsfix_launch<2, One>(src, blocks, arg, s);
-      case 3: return lsfix_launch<3, One>(src, blocks, arg, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (dim) {
-    case 1: return limit_launch<1, One>(kern, src, blocks, arg, s);
-    case 2: return limit_launch<2, One>(kern, src, blocks, arg, s);
-    case 3: return limit_launch<3, One>(kern, src, blocks, arg, s);
+    case 1: return limit_launch<1, One>(kern, src, blocks, threads, arg, s);
+    case 2: return limit_launch<2, One>(kern, src, blocks, threads, arg, s);
+    case 3: return limit_launch<3, One>(kern, src, blocks, threads, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s) {
-  if (kern == KN_LSFIX) {
-    switch (dim) {
-      case 1: return lsfix_launch<1, Many>(m, blocks, arg, s);
-      case 2: return lsfix_launch<2, Many>(m, blocks, arg, s);
-      case 3: return lsfix_launch<3, Many>(m, blocks, arg, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+                                   cudaStream_t s) {
   switch (dim) {
-    case 1: return limit_launch<1, Many>(kern, m, blocks, arg, s);
-    case 2: return limit_launch<2, Many>(kern, m, blocks, arg, s);
-    case 3: return limit_launch<3, Many>(kern, m, blocks, arg, s);
+    case 1: return limit_launch<1, Many>(kern, m, blocks, threads, arg, s);
+    case 2: return limit_launch<2, Many>(kern, m, blocks, threads, arg, s);
+    case 3: return limit_launch<3, Many>(kern, m, blocks, threads, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,7 +7,7 @@ namespace gdg {
 
 namespace {
 
-constexpr int kThreads = kNodeThreads;
+constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches 128, 256 or 512
 
 // Per-node primitives (Sec. 2.2): 1/rho, p, 1/p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
 // f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
@@ -358,15 +358,16 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
 }
 
 template <int DIM, class Src>
-cudaError_t low_launch(int kern, const Src& src, long long blocks, int arg, cudaStream_t s) {
+cudaError_t low_launch(int kern, const Src& src, long long blocks, int threads, int arg, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
+  if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
-    case KN_PRIM: k_prim<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
-    case KN_MAXDT: k_maxdt<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
-    case KN_TAU: k_tau<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
-    case KN_EDGE: k_edge<DIM, Src><<<g, kThreads, 0, s>>>(src); break;
-    case KN_LOW: k_low<DIM, Src><<<g, kThreads, 0, s>>>(src, arg); break;
+    case KN_PRIM: k_prim<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_MAXDT: k_maxdt<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_TAU: k_tau<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_EDGE: k_edge<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_LOW: k_low<DIM, Src><<<g, threads, 0, s>>>(src, arg); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -375,21 +376,23 @@ cudaError_t low_launch(int kern, const Src& src, long long blocks, int arg, cuda
 }  // namespace
 
 // Launchers of this file's kernels, dispatched on the dimension (called by launch_kernel*).
-cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int arg, cudaStream_t s) {
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+                            cudaStream_t s) {
   const One src{c};
   switch (dim) {
-    case 1: return low_launch<1, One>(kern, src, blocks, arg, s);
-    case 2: return low_launch<2, One>(kern, src, blocks, arg, s);
-    case 3: return low_launch<3, One>(kern, src, blocks, arg, s);
+    case 1: return low_launch<1, One>(kern, src, blocks, threads, arg, s);
+    case 2: return low_launch<2, One>(kern, src, blocks, threads, arg, s);
+    case 3: return low_launch<3, One>(kern, src, blocks, threads, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int arg, cudaStream_t s) {
+cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+                                 cudaStream_t s) {
   switch (dim) {
-    case 1: return low_launch<1, Many>(kern, m, blocks, arg, s);
-    case 2: return low_launch<2, Many>(kern, m, blocks, arg, s);
-    case 3: return low_launch<3, Many>(kern, m, blocks, arg, s);
+    case 1: return low_launch<1, Many>(kern, m, blocks, threads, arg, s);
+    case 2: return low_launch<2, Many>(kern, m, blocks, threads, arg, s);
+    case 3: return low_launch<3, Many>(kern, m, blocks, threads, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }

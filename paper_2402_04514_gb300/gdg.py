@@ -55,6 +55,15 @@ class _Info(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class Schedule(C.Structure):
+    """gdg_schedule: launch shapes (threads per block of the row kernels, element block cap, deferred
+    line-search slots per thread)."""
+
+    _fields_ = [("prim_threads", C.c_int32), ("edge_threads", C.c_int32), ("tau_threads", C.c_int32),
+                ("low_threads", C.c_int32), ("limit2_threads", C.c_int32), ("final_threads", C.c_int32),
+                ("maxdt_threads", C.c_int32), ("high_block_cap", C.c_int32), ("lsfix_slots", C.c_int32)]
+
+
 class RequestInfo(C.Structure):
     _fields_ = [("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double), ("t_final", C.c_double),
                 ("steps", C.c_int64), ("status", C.c_int32), ("flags", C.c_int32), ("device_bytes", C.c_int64)]
@@ -98,6 +107,12 @@ def load(build_if_missing: bool = False):
     L.gdg_batch_profile_read.argtypes = [vp, vp, vp]
     L.gdg_batch_destroy.argtypes = [vp]
     L.gdg_footprint.argtypes = [C.POINTER(_Problem), C.POINTER(i64)]
+    L.gdg_autotune.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.gdg_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    L.gdg_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    L.gdg_batch_autotune.argtypes = [vp, i32, vp]
+    L.gdg_batch_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    L.gdg_batch_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
     L.gdg_server_create.argtypes = [i64, C.POINTER(vp)]
     L.gdg_server_submit.argtypes = [vp, C.POINTER(_Problem), vp, vp, d, d, C.POINTER(i64)]
     L.gdg_server_wait.argtypes = [vp, i64, d, vp, C.POINTER(RequestInfo)]
@@ -119,6 +134,8 @@ def load(build_if_missing: bool = False):
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_clock_set",
               "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_profile", "gdg_batch_profile_read",
               "gdg_footprint", "gdg_server_create", "gdg_server_submit", "gdg_server_wait", "gdg_server_stats",
+              "gdg_autotune", "gdg_get_schedule", "gdg_set_schedule", "gdg_batch_autotune", "gdg_batch_get_schedule",
+              "gdg_batch_set_schedule",
               "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
               "gdg_max_dt_noalloc"):
@@ -322,6 +339,24 @@ class Solver:
                "gdg_ssprk3_step")
         return U
 
+    def autotune(self, U, work, trials: int = 2, bdata=None, stream=None) -> dict:
+        """gdg_autotune: picks the launch schedule by timing fused steps from U (restored afterwards)."""
+        self._check_state(U)
+        T1, T2 = work
+        bd = self._bdata(bdata)
+        _check(load().gdg_autotune(self._h, _ptr(U), _ptr(T1), _ptr(T2), _ptr(bd), trials, _stream(stream)),
+               "gdg_autotune")
+        return self.schedule()
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(load().gdg_get_schedule(self._h, C.byref(sc)), "gdg_get_schedule")
+        return {f: getattr(sc, f) for f, _ in Schedule._fields_}
+
+    def set_schedule(self, **kw):
+        sc = Schedule(**{**self.schedule(), **kw})
+        _check(load().gdg_set_schedule(self._h, C.byref(sc)), "gdg_set_schedule")
+
     def set_clock(self, t: float = 0.0, t_end: float = float("inf"), cfl: float = 0.5, stream=None):
         _check(load().gdg_clock_set(self._h, t, t_end, cfl, _stream(stream)), "gdg_clock_set")
 
@@ -375,6 +410,20 @@ class Batch:
 
     def profile(self, enable: bool):
         _check(load().gdg_batch_profile(self._b, 1 if enable else 0), "gdg_batch_profile")
+
+    def autotune(self, trials: int = 2, stream=None) -> dict:
+        """gdg_batch_autotune: picks the batch's launch schedule by timing steps (states restored)."""
+        _check(load().gdg_batch_autotune(self._b, trials, _stream(stream)), "gdg_batch_autotune")
+        return self.schedule()
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(load().gdg_batch_get_schedule(self._b, C.byref(sc)), "gdg_batch_get_schedule")
+        return {f: getattr(sc, f) for f, _ in Schedule._fields_}
+
+    def set_schedule(self, **kw):
+        sc = Schedule(**{**self.schedule(), **kw})
+        _check(load().gdg_batch_set_schedule(self._b, C.byref(sc)), "gdg_batch_set_schedule")
 
     def profile_read(self) -> dict:
         ms = np.zeros(len(KERNELS))
