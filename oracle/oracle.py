@@ -156,6 +156,19 @@ class Oracle:
             return out, flags, arrays
         return out, flags
 
+    def ssprk54_step(self, U, dt, bdata_fn=None, t=0.0):
+        """One SSPRK(5,4) step (oracle/ssprk.py) of size dt built from this oracle's limited forward-Euler
+        stages; bdata_fn(t) gives Dirichlet data at a stage time."""
+        from . import ssprk
+
+        bd = (lambda s: None) if bdata_fn is None else bdata_fn
+        U1, flags = ssprk.shu_osher_step(U, dt, lambda u, tau, ts: self.stage(u, tau, bdata=bd(ts)),
+                                         ssprk.SSPRK54_ALPHA, ssprk.SSPRK54_BETA, t)
+        f = 0
+        for x in flags:
+            f |= x
+        return U1, f
+
     def ssprk3_step(self, U, tau, bdata_fn=None, t=0.0):
         """One Shu-Osher SSPRK3 step; bdata_fn(t) gives Dirichlet data [m][nb] at a stage time."""
         bd = (lambda s: None) if bdata_fn is None else bdata_fn
