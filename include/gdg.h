@@ -148,7 +148,17 @@ int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double al
  * Flags as gdg_stage. */
 int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream);
 
-/* Sets the clock of gdg_ssprk3_step: current time t, final time t_end >= t (+inf: no end), CFL number
+/* One SSPRK(5,4) step: the five-stage fourth-order SSP Runge-Kutta method the paper's experiments use
+ * (Sec. 6.2; the optimal coefficients of Spiteri and Ruuth, SSP coefficient C = 1.508), in Shu-Osher form
+ * from limited forward-Euler stages, with dt = min(cfl * C * min_i (-m_i / (2 d_ii(U))), t_end - t) chosen
+ * on the device as in gdg_ssprk3_step (each stage's forward-Euler step is at most cfl times the bound of
+ * eq. (MaxCFLdt)).  Five stage sweeps and two elementwise combinations; the result is written back to U.
+ * U, T1, T2, T3: device [m][n], distinct (GDG_EINVAL otherwise); T1..T3 are workspace.  Clock, bdata,
+ * flags, asynchrony and allocation as gdg_ssprk3_step. */
+int gdg_ssprk54_step(gdg_handle* h, double* U, double* T1, double* T2, double* T3, const double* bdata,
+                     void* stream);
+
+/* Sets the clock of gdg_ssprk3_step and gdg_ssprk54_step: current time t, final time t_end >= t (+inf: no end), CFL number
  * cfl > 0; resets the step count.  Synchronises the stream. */
 int gdg_clock_set(gdg_handle* h, double t, double t_end, double cfl, void* stream);
 
@@ -173,7 +183,7 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* host_dst, int64_t 
  * (indices GDG_K_*) into total_ms[GDG_NKERNELS] and launches[GDG_NKERNELS], and clears the records.
  * gdg_profile(h, 0) stops recording and drops pending records. */
 enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIMIT2 = 4, GDG_K_FINAL = 5,
-       GDG_K_EDGE = 6, GDG_K_LSFIX = 7, GDG_K_TAU = 8, GDG_K_CLOCK = 9, GDG_NKERNELS = 10 };
+       GDG_K_EDGE = 6, GDG_K_LSFIX = 7, GDG_K_TAU = 8, GDG_K_CLOCK = 9, GDG_K_AXPY = 10, GDG_NKERNELS = 11 };
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 

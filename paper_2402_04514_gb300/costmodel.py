@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock")
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock", "axpy")
 
 
 @dataclass
@@ -56,6 +56,7 @@ def bytes_per_launch(c: Counts) -> dict:
         lsfix=0,  # the deferred line searches: a data-dependent handful of entries, not counted
         tau=rowptr + 8 * nnz + 8 * n + 8 * (m + 6) * nb,
         clock=0,
+        axpy=8 * m * n * 3,
     )
 
 
@@ -79,6 +80,7 @@ def flops_per_launch(c: Counts) -> dict:
         lsfix=0,
         tau=nnz + 2 * n + nb * (lam + vel + 10),
         clock=0,
+        axpy=3 * m * n,
     )
 
 

@@ -656,7 +656,71 @@ int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const doub
   if (int rc = run_stage(h, c1, true, s); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c2, false, s); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c3, false, s); rc != GDG_OK) return rc;
-  cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, s); });
+  cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, 1.0, s); });
+  return e == cudaSuccess ? GDG_OK : cuda_fail(e);
+}
+
+// SSPRK(5,4): the optimal five-stage fourth-order SSP method (Spiteri-Ruuth coefficients; the method the
+// paper's experiments use, Sec. 6.2) in Shu-Osher form.  Stage j's forward-Euler step is
+// (beta / alpha) dt; u_3 enters u_4 and u_5 with the same step, so one evaluation F3 = FE(u_3) serves both.
+namespace {
+constexpr double kA[5][5] = {{1.0, 0, 0, 0, 0},
+                             {0.444370493651235, 0.555629506348765, 0, 0, 0},
+                             {0.620101851488403, 0.0, 0.379898148511597, 0, 0},
+                             {0.178079954393132, 0.0, 0.0, 0.821920045606868, 0},
+                             {0.0, 0.0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
+constexpr double kB[5][5] = {{0.391752226571890, 0, 0, 0, 0},
+                             {0.0, 0.368410593050371, 0, 0, 0},
+                             {0.0, 0.0, 0.251891774271694, 0, 0},
+                             {0.0, 0.0, 0.0, 0.544974750228521, 0},
+                             {0.0, 0.0, 0.0, 0.063692468666290, 0.226007483236906}};
+// the SSP coefficient min alpha / beta: dt = cfl * C * bound keeps every stage's step within cfl * bound
+double ssp54_coefficient() {
+  double c = 1e300;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j <= i; ++j)
+      if (kB[i][j] != 0.0) c = std::min(c, kA[i][j] / kB[i][j]);
+  return c;
+}
+}  // namespace
+
+int gdg_ssprk54_step(gdg_handle* h, double* U, double* T1, double* T2, double* T3, const double* bdata,
+                     void* stream) {
+  if (!h || ((!U || !T1 || !T2 || !T3) && h->n > 0)) return GDG_EINVAL;
+  if (h->n > 0 && (U == T1 || U == T2 || U == T3 || T1 == T2 || T1 == T3 || T2 == T3)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double C = ssp54_coefficient();
+  auto ctx = [&](const double* in, const double* base, double alpha, double* out, double scale) {
+    gdg::Ctx c = make_ctx(h, in, base, out, bdata, alpha, 0.0, h->clk);
+    c.tau_scale = scale;
+    c.dt_factor = C;
+    return c;
+  };
+  // u1 = FE(u) -> T1;  u2 = a u + b FE(u1) -> T2;  u3 = a u + b FE(u2) -> T1;  F3 = FE(u3) -> T3;
+  // u4 = a u + b F3 -> T1;  u5 = a u2 + b F3 + c FE(u4) -> T2 (in place on u2);  U <- u5
+  const gdg::Ctx s1 = ctx(U, nullptr, 0.0, T1, kB[0][0] / kA[0][0]);
+  const gdg::Ctx s2 = ctx(T1, U, kA[1][0], T2, kB[1][1] / kA[1][1]);
+  const gdg::Ctx s3 = ctx(T2, U, kA[2][0], T1, kB[2][2] / kA[2][2]);
+  const gdg::Ctx s4 = ctx(T1, nullptr, 0.0, T3, kB[3][3] / kA[3][3]);
+  const gdg::Ctx c4 = ctx(T3, U, kA[3][0], T1, 0.0);
+  gdg::Ctx s5 = ctx(T1, T2, kA[4][2], T2, kB[4][4] / kA[4][4]);
+  s5.Ubase2 = T3;
+  s5.alpha2 = kA[4][3];
+  s5.w_fe = kA[4][4];
+  const gdg::Ctx cp = ctx(T2, nullptr, 0.0, U, 0.0);
+  auto axpy = [&](const gdg::Ctx& c) {
+    return timed(h, GDG_K_AXPY, s, [&] { return gdg::launch_one(gdg::KN_AXPY, h->dim, c, 0, h->sched, s); });
+  };
+  if (int rc = run_stage(h, s1, true, s); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, s2, false, s); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, s3, false, s); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, s4, false, s); rc != GDG_OK) return rc;
+  cudaError_t e;
+  if ((e = axpy(c4)) != cudaSuccess) return cuda_fail(e);
+  if (int rc = run_stage(h, s5, false, s); rc != GDG_OK) return rc;
+  if ((e = axpy(cp)) != cudaSuccess) return cuda_fail(e);
+  e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, C, s); });
   return e == cudaSuccess ? GDG_OK : cuda_fail(e);
 }
 

@@ -115,22 +115,40 @@ struct Ctx {
   const double* Ubase;  // SSP-RK base (read only where alpha != 0)
   double* Uout;         // stage output; may equal Ubase (each node reads its base before writing itself)
   const double* bdata;  // Dirichlet data [m][nb] or null
-  double alpha;         // U_out = alpha U_base + (1 - alpha) FE(U_in)
+  double alpha;         // U_out = alpha U_base + (1 - alpha) FE(U_in)  (Ubase2 null), or
+  const double* Ubase2; //        alpha U_base + alpha2 U_base2 + w_fe FE(U_in)  (a second base term)
+  double alpha2, w_fe;
   double tau;           // the stage's tau when clk is null
   Clock* clk;           // device clock of the fused step, or null
+  double tau_scale;     // the stage's tau is tau_scale * dt of the step (fused steps)
+  double dt_factor;     // dt = min(cfl * dt_factor * bound, t_end - t): the method's SSP coefficient
 };
+
+// The stage's output at flat index idx from its forward-Euler value fe (Shu-Osher combination).
+__device__ __forceinline__ double rk_out(const Ctx& c, size_t idx, double fe) {
+  if (c.Ubase2) return c.alpha * c.Ubase[idx] + c.alpha2 * c.Ubase2[idx] + c.w_fe * fe;
+  return c.alpha != 0.0 ? c.alpha * c.Ubase[idx] + (1.0 - c.alpha) * fe : fe;
+}
 
 // An instance whose clock has reached t_end: every kernel of the fused step returns at once, so the
 // step leaves its state untouched (bit for bit) and costs only the launches.
 __device__ __forceinline__ bool finished(const Ctx& c) { return c.clk && !(c.clk->t < c.clk->t_end); }
 
+// dt of a fused step from its clock: min(cfl * dt_factor * bound, t_end - t), 0 without a bound.
+__device__ __forceinline__ double clock_dt(const Clock* k, double dt_factor, bool* clipped) {
+  const unsigned long long b = k->tau_bits;
+  *clipped = false;
+  if (b == kTauNone) return 0.0;
+  const double v = k->cfl * dt_factor * __longlong_as_double((long long)b);
+  const double rem = k->t_end - k->t;
+  *clipped = !(v < rem);
+  return *clipped ? (rem > 0.0 ? rem : 0.0) : v;
+}
+
 __device__ __forceinline__ double stage_tau(const Ctx& c) {
   if (!c.clk) return c.tau;
-  const unsigned long long b = c.clk->tau_bits;
-  if (b == kTauNone) return 0.0;
-  const double v = c.clk->cfl * __longlong_as_double((long long)b);
-  const double rem = c.clk->t_end - c.clk->t;
-  return v < rem ? v : (rem > 0.0 ? rem : 0.0);
+  bool clipped;
+  return c.tau_scale * clock_dt(c.clk, c.dt_factor, &clipped);
 }
 
 // Where a kernel finds its context.  One: a single instance, the context is the kernel parameter and
@@ -184,7 +202,8 @@ struct Many {
 };
 
 // Kernels of the sweep and their launch shapes.
-enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL, KN_LSFIX, KN_TAU, KN_COUNT };
+enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL, KN_LSFIX, KN_TAU, KN_AXPY,
+            KN_COUNT };
 constexpr int kRowMaxThreads = 512;  // one-thread-per-row / per-edge kernels: 128, 256 or 512 threads
 constexpr int kHighMaxBlock = 160;   // element sweep: whole elements, at most this many nodes per block
 constexpr int kLsfixThreads = 128;
@@ -242,8 +261,8 @@ cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks,
                               cudaStream_t s);
 cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
                                    cudaStream_t s);
-// End of a fused SSP-RK3 step: advances the clock(s) (kernels_limit.cu).
-cudaError_t launch_clock_one(Clock* clk, cudaStream_t s);
+// End of a fused step: advances the clock(s) by the step's dt (kernels_limit.cu).
+cudaError_t launch_clock_one(Clock* clk, double dt_factor, cudaStream_t s);
 cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);
 
 // One kernel of the sweep for one instance, shaped by the schedule.
@@ -253,6 +272,7 @@ inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sc
     case KN_HIGH: return launch_high_file(dim, c, blocks, high_nodes_per_block(c.D.n_loc, sc.high_cap), s);
     case KN_LIMIT2:
     case KN_FINAL:
+    case KN_AXPY:
     case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
     default: return launch_low_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
   }

@@ -77,8 +77,13 @@ inline gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Uba
   c.Uout = Uout;
   c.bdata = bdata;
   c.alpha = alpha;
+  c.Ubase2 = nullptr;
+  c.alpha2 = 0.0;
+  c.w_fe = 0.0;
   c.tau = tau;
   c.clk = clk;
+  c.tau_scale = 1.0;
+  c.dt_factor = 1.0;
   return c;
 }
 

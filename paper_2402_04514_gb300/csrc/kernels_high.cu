@@ -101,8 +101,7 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
     if (D.order == GDG_ORDER_HIGH) {
 #pragma unroll
       for (int q = 0; q < M; ++q) {
-        double uh = Ui[q] + dUi[q];
-        c.Uout[(size_t)q * n + i] = c.alpha != 0.0 ? c.alpha * c.Ubase[(size_t)q * n + i] + (1.0 - c.alpha) * uh : uh;
+        c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, Ui[q] + dUi[q]);
       }
     }
   }

@@ -42,10 +42,8 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
 #pragma unroll
   for (int q = 0; q < M; ++q) U1[q] = S.UL[q * n + i] + acc[q] * inv_mi;
   if (last) {
-    const double alpha = c.alpha;
 #pragma unroll
-    for (int q = 0; q < M; ++q)
-      c.Uout[q * n + i] = alpha != 0.0 ? alpha * c.Ubase[q * n + i] + (1.0 - alpha) * U1[q] : U1[q];
+    for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, U1[q]);
     return;
   }
 #pragma unroll
@@ -156,47 +154,55 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
     for (int q = 0; q < M; ++q) acc[q] += w * S.AB[q * nb + b];
   }
   const double inv_mi = D.inv_mi[i];
-  const double alpha = c.alpha;
 #pragma unroll
-  for (int q = 0; q < M; ++q) {
-    double u2 = S.U1[q * n + i] + acc[q] * inv_mi;
-    c.Uout[q * n + i] = alpha != 0.0 ? alpha * c.Ubase[q * n + i] + (1.0 - alpha) * u2 : u2;
-  }
+  for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, S.U1[q * n + i] + acc[q] * inv_mi);
 }
 
-// End of a fused SSP-RK3 step for one instance's clock: t += tau of the step (the tau every kernel of the
-// step used), the step is counted, and the bound is reset for the next step.  Steps taken after t reached
+// End of a fused step for one instance's clock: t += dt of the step (the dt every kernel of the step
+// used), the step is counted, and the bound is reset for the next step.  Steps taken after t reached
 // t_end are no-ops and are not counted.
-__device__ __forceinline__ void clock_advance(Clock* k) {
+__device__ __forceinline__ void clock_advance(Clock* k, double dt_factor) {
   if (!(k->t < k->t_end)) {  // finished before this step: the step did nothing and is not counted
     k->tau = 0.0;
     k->tau_bits = kTauNone;
     return;
   }
-  const unsigned long long b = k->tau_bits;
-  double tau = 0.0;
-  bool clipped = false;
-  if (b != kTauNone) {
-    const double v = k->cfl * __longlong_as_double((long long)b);
-    const double rem = k->t_end - k->t;
-    clipped = !(v < rem);
-    tau = clipped ? (rem > 0.0 ? rem : 0.0) : v;
-  } else {
-    clipped = k->t_end < INFINITY;  // no viscosity anywhere: nothing evolves, the instance is done
-  }
-  k->tau = tau;
-  k->t = clipped ? k->t_end : k->t + tau;  // a step clipped to t_end lands on it exactly
+  bool clipped;
+  const double dt = clock_dt(k, dt_factor, &clipped);
+  if (k->tau_bits == kTauNone) clipped = k->t_end < INFINITY;  // no viscosity anywhere: nothing evolves
+  k->tau = dt;
+  k->t = clipped ? k->t_end : k->t + dt;  // a step clipped to t_end lands on it exactly
   k->steps += 1;
   k->tau_bits = kTauNone;
 }
 
-__global__ void k_clock_one(Clock* k) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) clock_advance(k);
+__global__ void k_clock_one(Clock* k, double dt_factor) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) clock_advance(k, dt_factor);
 }
 
 __global__ void k_clock_many(const Ctx* ctx, int ninst) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < ninst) clock_advance(ctx[k].clk);
+  if (k < ninst) clock_advance(ctx[k].clk, ctx[k].dt_factor);
+}
+
+// U_out = alpha U_base + (1 - alpha) U_in at every node and component (alpha = 0: a copy): the linear
+// stage combinations of a Runge-Kutta step that involve no forward-Euler evaluation.
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kThreads) k_axpy(Src src) {
+  constexpr int M = DIM + 2;
+  __shared__ Ctx sctx;
+  int lb;
+  const Ctx& c = src.get(&sctx, &lb);
+  if (finished(c)) return;
+  const int i = lb * blockDim.x + threadIdx.x;
+  if (i >= c.D.n) return;
+  const size_t n = c.D.n;
+  const double alpha = c.alpha;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const size_t idx = (size_t)q * n + i;
+    c.Uout[idx] = alpha != 0.0 ? alpha * c.Ubase[idx] + (1.0 - alpha) * c.U[idx] : c.U[idx];
+  }
 }
 
 template <int DIM, class Src>
@@ -207,6 +213,7 @@ cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads
   switch (kern) {
     case KN_LIMIT2: k_limit2<DIM, Src><<<g, threads, 0, s>>>(src, arg); break;
     case KN_FINAL: k_final<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_AXPY: k_axpy<DIM, Src><<<g, threads, 0, s>>>(src); break;
     case KN_LSFIX: k_lsfix<DIM, Src><<<g, kLsfixThreads, 0, s>>>(src, arg); break;
     default: return cudaErrorInvalidValue;
   }
@@ -236,8 +243,8 @@ cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long b
   }
 }
 
-cudaError_t launch_clock_one(Clock* clk, cudaStream_t s) {
-  k_clock_one<<<1, 32, 0, s>>>(clk);
+cudaError_t launch_clock_one(Clock* clk, double dt_factor, cudaStream_t s) {
+  k_clock_one<<<1, 32, 0, s>>>(clk, dt_factor);
   return cudaGetLastError();
 }
 

@@ -320,10 +320,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
 #pragma unroll
   for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
   if (write_out) {
-    const double alpha = c.alpha;
 #pragma unroll
-    for (int q = 0; q < M; ++q)
-      c.Uout[(size_t)q * n + i] = alpha != 0.0 ? alpha * c.Ubase[(size_t)q * n + i] + (1.0 - alpha) * UL[q] : UL[q];
+    for (int q = 0; q < M; ++q) c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, UL[q]);
     return;
   }
 #pragma unroll

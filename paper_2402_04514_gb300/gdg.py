@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
-KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock")  # GDG_K_* order
+KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock", "axpy")  # GDG_K_*
 BC_SLIP, BC_DIRICHLET = 0, 1
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
     L.gdg_max_dt.argtypes = [vp, vp, vp, d, C.POINTER(d), vp]
     L.gdg_stage.argtypes = [vp, vp, vp, d, d, vp, vp, vp]
     L.gdg_ssprk3_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.gdg_ssprk54_step.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.gdg_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(vp)]
     L.gdg_batch_step.argtypes = [vp, vp]
@@ -131,7 +132,8 @@ def load(build_if_missing: bool = False):
     L.gdg_destroy.argtypes = [vp]
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
-    for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_clock_set",
+    for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_ssprk54_step",
+              "gdg_clock_set",
               "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_profile", "gdg_batch_profile_read",
               "gdg_footprint", "gdg_server_create", "gdg_server_submit", "gdg_server_wait", "gdg_server_stats",
               "gdg_autotune", "gdg_get_schedule", "gdg_set_schedule", "gdg_batch_autotune", "gdg_batch_get_schedule",
@@ -328,15 +330,20 @@ class Solver:
         return out
 
     def step(self, U, work, bdata=None, stream=None):
-        """gdg_ssprk3_step: one SSP-RK3 step of U in place, the time step chosen on the device from the
-        handle's clock (set_clock); work = (T1, T2) are two scratch states."""
+        """One fused step of U in place, the time step chosen on the device from the handle's clock
+        (set_clock): gdg_ssprk3_step with work = (T1, T2), gdg_ssprk54_step with work = (T1, T2, T3)."""
         self._check_state(U)
-        T1, T2 = work
-        self._check_state(T1)
-        self._check_state(T2)
+        for T in work:
+            self._check_state(T)
         bd = self._bdata(bdata)
-        _check(load().gdg_ssprk3_step(self._h, _ptr(U), _ptr(T1), _ptr(T2), _ptr(bd), _stream(stream)),
-               "gdg_ssprk3_step")
+        if len(work) == 2:
+            _check(load().gdg_ssprk3_step(self._h, _ptr(U), _ptr(work[0]), _ptr(work[1]), _ptr(bd), _stream(stream)),
+                   "gdg_ssprk3_step")
+        elif len(work) == 3:
+            _check(load().gdg_ssprk54_step(self._h, _ptr(U), _ptr(work[0]), _ptr(work[1]), _ptr(work[2]), _ptr(bd),
+                                           _stream(stream)), "gdg_ssprk54_step")
+        else:
+            raise ValueError("work holds two (SSPRK3) or three (SSPRK(5,4)) scratch states")
         return U
 
     def autotune(self, U, work, trials: int = 2, bdata=None, stream=None) -> dict:
