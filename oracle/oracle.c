@@ -95,6 +95,61 @@ static double entry_c(const orc_problem* P, long e, double* c, double* nrm) {
 
 /* Sec. 4.1: boundary state U_i^{d,k} of boundary entry b: slip, eq. (eq:slip_boundary)
  * (m^d = m - 2 (m.n) n, rho and E copied), or the given Dirichlet data. */
+/* Sec. 4.1, in- and outflow: supersonic inflow (v.n < -a) takes the data, supersonic outflow (v.n >= a) the
+ * interior state (eq. (eq:supersonic_inoutflow)); in between, the characteristic variables of
+ * eq. (eq:characteristics) R = {v_n - 2a/(g-1), p/rho^g, v - (v.n) n, v_n + 2a/(g-1)} of the boundary state
+ * are those of the data where the characteristic speed {v_n - a, v_n, v_n, v_n + a} at the interior state
+ * is <= 0 (incoming) and those of the interior state otherwise.  The state is rebuilt from R:
+ * v_n = (R1 + R4)/2, a = (g-1)(R4 - R1)/4, rho = (a^2 / (g R2))^(1/(g-1)), p = R2 rho^g.  The paper leaves
+ * the case where the blend gives no admissible state (a <= 0: a vacuum) to a cited construction; here the
+ * boundary state is then the interior state. */
+static void prim_of(const double* U, int d, double g, double* v, double* p, double* a) {
+  for (int k = 0; k < d; ++k) v[k] = U[1 + k] / U[0];
+  *p = (g - 1.0) * internal_energy(U, d);
+  *a = sqrt(g * *p / U[0]);
+}
+
+void orc_inoutflow_state(const double* Ui, const double* Ud, const double* nrm, int d, double g, double* UB) {
+  int m = d + 2;
+  double vi[3], vd[3], pi, pd, ai, ad;
+  prim_of(Ui, d, g, vi, &pi, &ai);
+  double vni = dot(vi, nrm, d);
+  if (vni < -ai) {
+    for (int q = 0; q < m; ++q) UB[q] = Ud[q];
+    return;
+  }
+  if (vni >= ai) {
+    for (int q = 0; q < m; ++q) UB[q] = Ui[q];
+    return;
+  }
+  prim_of(Ud, d, g, vd, &pd, &ad);
+  double vnd = dot(vd, nrm, d);
+  /* subsonic: v_n - a < 0 (incoming: data), v_n + a > 0 (outgoing: interior); v_n decides the middle ones */
+  const double* vsrc = vni <= 0.0 ? vd : vi;
+  double R1 = vnd - 2.0 * ad / (g - 1.0);
+  double R4 = vni + 2.0 * ai / (g - 1.0);
+  double R2 = vni <= 0.0 ? pd / pow(Ud[0], g) : pi / pow(Ui[0], g);
+  double vnsrc = dot(vsrc, nrm, d);
+  double vt[3];
+  for (int k = 0; k < d; ++k) vt[k] = vsrc[k] - vnsrc * nrm[k];
+  double vn = 0.5 * (R1 + R4);
+  double a = 0.25 * (g - 1.0) * (R4 - R1);
+  if (!(a > 0.0)) {
+    for (int q = 0; q < m; ++q) UB[q] = Ui[q];
+    return;
+  }
+  double rho = pow(a * a / (g * R2), 1.0 / (g - 1.0));
+  double p = R2 * pow(rho, g);
+  double v2 = 0.0;
+  UB[0] = rho;
+  for (int k = 0; k < d; ++k) {
+    double vk = vn * nrm[k] + vt[k];
+    UB[1 + k] = rho * vk;
+    v2 += vk * vk;
+  }
+  UB[d + 1] = p / (g - 1.0) + 0.5 * rho * v2;
+}
+
 static double boundary_state(const orc_problem* P, const double* U, const double* bdata, long b,
                              double* Ui, double* UB, double* c, double* nrm) {
   int d = P->dim, m = d + 2;
@@ -104,6 +159,10 @@ static double boundary_state(const orc_problem* P, const double* U, const double
   gather(U, P->n, P->b_node[b], m, Ui);
   if (P->b_type[b] == ORC_DIRICHLET) {
     for (int q = 0; q < m; ++q) UB[q] = bdata[q * P->nb + b];
+  } else if (P->b_type[b] == ORC_INOUTFLOW) {
+    double Ud[5];
+    for (int q = 0; q < m; ++q) Ud[q] = bdata[q * P->nb + b];
+    orc_inoutflow_state(Ui, Ud, nrm, d, P->gamma, UB);
   } else {
     double mn = dot(Ui + 1, nrm, d);
     UB[0] = Ui[0];

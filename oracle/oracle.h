@@ -19,7 +19,7 @@ extern "C" {
 #endif
 
 enum { ORC_LOW = 0, ORC_HIGH = 1, ORC_LIMITED = 2 };
-enum { ORC_SLIP = 0, ORC_DIRICHLET = 1 };
+enum { ORC_SLIP = 0, ORC_DIRICHLET = 1, ORC_INOUTFLOW = 2 };
 /* stage flags (bitmask) */
 enum { ORC_F_INADMISSIBLE = 1, ORC_F_CFL = 2 };
 
@@ -67,6 +67,9 @@ typedef struct {
 
 /* Upper bound on the maximum wave speed of the 1D Riemann problem (U_L, U_R) along unit n. */
 double orc_lambda_max(const double* UL, const double* UR, const double* nrm, int dim, double gamma);
+/* Boundary state of an in/outflow entry (Sec. 4.1, eqs. (eq:supersonic_inoutflow), (eq:characteristics))
+ * from the interior state Ui, the given data Ud and the outward unit normal nrm; written to UB. */
+void orc_inoutflow_state(const double* Ui, const double* Ud, const double* nrm, int dim, double gamma, double* UB);
 void orc_lambda_max_batch(long count, const double* UL, const double* UR, const double* nrm, int dim,
                           double gamma, double* out); /* UL/UR [count][m], nrm [count][dim] */
 

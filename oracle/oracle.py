@@ -62,6 +62,7 @@ def lib():
     global _lib
     if _lib is None:
         L = C.CDLL(build())
+        L.orc_inoutflow_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.orc_lambda_max_batch.argtypes = [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                            C.c_void_p]
         L.orc_max_dt.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_void_p, C.c_double,
@@ -177,6 +178,17 @@ class Oracle:
         U2, f = self.stage(U1, tau, U_base=U, alpha=0.75, bdata=bd(t + tau)); flags |= f
         U3, f = self.stage(U2, tau, U_base=U, alpha=1.0 / 3.0, bdata=bd(t + 0.5 * tau)); flags |= f
         return U3, flags
+
+
+def inoutflow_state(Ui, Ud, nrm, gamma=1.4):
+    """Boundary state of an in/outflow entry (orc_inoutflow_state) for one interior state Ui [m], data Ud
+    [m] and outward unit normal nrm [d]."""
+    Ui = np.ascontiguousarray(Ui, np.float64)
+    Ud = np.ascontiguousarray(Ud, np.float64)
+    nrm = np.ascontiguousarray(nrm, np.float64)
+    out = np.empty_like(Ui)
+    lib().orc_inoutflow_state(_p(Ui), _p(Ud), _p(nrm), nrm.shape[0], gamma, _p(out))
+    return out
 
 
 def lambda_max(UL, UR, nrm, gamma=1.4):

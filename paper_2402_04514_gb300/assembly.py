@@ -27,7 +27,8 @@ import numpy as np
 
 SLIP = 0
 DIRICHLET = 1
-BC_CODES = {"slip": SLIP, "dirichlet": DIRICHLET}
+INOUTFLOW = 2
+BC_CODES = {"slip": SLIP, "dirichlet": DIRICHLET, "inoutflow": INOUTFLOW}
 
 # Boundary part ids (one per side; corners carry one entry per side, Sec. 4.2).
 PART_LEFT, PART_RIGHT, PART_BOTTOM, PART_TOP = 0, 1, 2, 3
@@ -212,7 +213,7 @@ def assemble_2d(nx: int, ny: int, degree: int, box=(0.0, 1.0, 0.0, 1.0),
                 periodic=(False, False), bc=None) -> Problem:
     """Q^k dG on an nx x ny uniform quad mesh of box = (x0, x1, y0, y1).
 
-    bc maps 'left'/'right'/'bottom'/'top' to 'slip' or 'dirichlet' (sides that are not periodic).
+    bc maps 'left'/'right'/'bottom'/'top' to 'slip', 'dirichlet' or 'inoutflow' (sides that are not periodic).
     """
     k = degree
     p1 = k + 1

@@ -8,6 +8,7 @@ import tempfile
 import pytest
 
 from oracle import oracle as om
+from tests import test_oracle_bc as bc
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(om.__file__), "oracle.c")
@@ -39,6 +40,14 @@ MUTANTS = {
                                   "fmin(P->c_ev * fabs(N[i]), 1.0);"),
     "entropy_gradient_sign": ("grad[d + 1] = pref * ((g - 1.0) / pi);", "grad[d + 1] = -pref * ((g - 1.0) / pi);"),
     "bounds_skip_bar_states": ("lo = fmin(lo, fmin(Uk[0], Ubk[0]));", "lo = fmin(lo, Uk[0]);"),
+    # in/outflow boundary state (Sec. 4.1)
+    "inoutflow_incoming_riemann_invariant_from_interior": ("double R1 = vnd - 2.0 * ad / (g - 1.0);",
+                                                          "double R1 = vni - 2.0 * ai / (g - 1.0);"),
+    "inoutflow_entropy_from_the_wrong_side": (
+        "double R2 = vni <= 0.0 ? pd / pow(Ud[0], g) : pi / pow(Ui[0], g);",
+        "double R2 = vni <= 0.0 ? pi / pow(Ui[0], g) : pd / pow(Ud[0], g);"),
+    "supersonic_inflow_keeps_the_interior": ("  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ud[q];",
+                                             "  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ui[q];"),
 }
 
 FAST_PINS = [
@@ -53,6 +62,13 @@ FAST_PINS = [
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 4.0),
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 0.0),
     lambda O: pins.test_sod_exact_solution(O),
+]
+
+
+BC_PINS = [
+    lambda O: bc.test_supersonic_cases_take_data_or_interior_exactly(),
+    lambda O: bc.test_subsonic_characteristics_come_from_the_right_side(),
+    lambda O: bc.test_shock_leaves_the_domain_without_reflection(2),
 ]
 
 
@@ -76,7 +92,7 @@ def test_pins_reject_mutant(name, monkeypatch):
         monkeypatch.setattr(om, "_lib", None)
         monkeypatch.setattr(om, "build", lambda force=False: so)
         caught = []
-        for pin in FAST_PINS + [_vortex_q1_limited]:
+        for pin in FAST_PINS + BC_PINS + [_vortex_q1_limited]:
             try:
                 pin(om)
             except (AssertionError, ValueError, FloatingPointError):
