@@ -44,7 +44,9 @@ typedef enum {
 } gdg_status_code;
 
 enum { GDG_ORDER_LOW = 0, GDG_ORDER_HIGH = 1, GDG_ORDER_LIMITED = 2 };
-enum { GDG_BC_SLIP = 0, GDG_BC_DIRICHLET = 1 };
+/* boundary entry types (Sec. 4.1): slip wall, Dirichlet data, in/outflow (supersonic and subsonic,
+ * from the characteristic variables of eq. (eq:characteristics); needs data like Dirichlet entries) */
+enum { GDG_BC_SLIP = 0, GDG_BC_DIRICHLET = 1, GDG_BC_INOUTFLOW = 2 };
 /* sticky device flags, read by gdg_status */
 enum { GDG_FLAG_INADMISSIBLE = 1, GDG_FLAG_CFL = 2 };
 
@@ -73,7 +75,8 @@ typedef struct {
  *   - coloc[e] = 1 iff x_i == x_j (face partners across an element face), symmetric;
  *   - m_i > 0 and sum_j MK[e][a][j] == m_i to 1e-12 relative (Sec. 5.3 absorbs the consistent mass into
  *     the fluxes using sum_j (m_ij - delta_ij m_i) = 0); every MK block symmetric positive definite;
- *   - boundary entries: 0 <= b_node < n, |c_i^{d,k}| > 0, b_type GDG_BC_SLIP or GDG_BC_DIRICHLET;
+ *   - boundary entries: 0 <= b_node < n, |c_i^{d,k}| > 0, b_type GDG_BC_SLIP, GDG_BC_DIRICHLET or
+ *     GDG_BC_INOUTFLOW;
  *   - gamma > 1, omega_measure = |Omega| > 0; for the limited order with bounds_mode 0,
  *     r_h^- = 1 - c_r h_i^{p_r} > 0 at every node (h_i = (m_i / |Omega|)^{1/dim}). */
 typedef struct {
@@ -123,8 +126,8 @@ int gdg_set_params(gdg_handle* h, const gdg_params* params);
 
 /* Sec. 3.3, eq. (MaxCFLdt): *tau_out = cfl * min_i (-m_i / (2 d_ii)), d_ii of
  * eq. (eq:dij_low_order_supplement) at the state U (device [m][n]).  bdata (device [m][nb], in the
- * order of gdg_problem's boundary entries) holds the Dirichlet data; it may be NULL when no entry is
- * Dirichlet.  Synchronises the stream (the only call that does).  Flags an inadmissible U. */
+ * order of gdg_problem's boundary entries) holds the data of the Dirichlet and in/outflow entries; it
+ * may be NULL when every entry is a slip wall.  Synchronises the stream.  Flags an inadmissible U. */
 int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, double* tau_out,
                void* stream);
 
@@ -216,8 +219,9 @@ int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
  * Inputs (device pointers owned by the caller, read only):
  *   row_ptr [n+1] and col_idx [nnz] (int32 CSR, as in gdg_problem), cij [dim][nnz], mi [n];
  *   boundary entries ordered by node: those of node i are b_ptr[i] .. b_ptr[i+1]-1 (int32 [n+1]), with
- *   b_c [dim][nb] and b_type [nb] in that order, and bdata [m][nb] (Dirichlet data in the same order;
- *   may be NULL when no entry is Dirichlet: a Dirichlet entry without data makes the result NaN).
+ *   b_c [dim][nb] and b_type [nb] in that order, and bdata [m][nb] (the data of the Dirichlet and
+ *   in/outflow entries in the same order; may be NULL when every entry is a slip wall: an entry that needs
+ *   data and has none makes the result NaN).
  * Output: *tau_out, a device double, written on stream (asynchronous; the call does not synchronise).
  *
  * Scratch: a fixed array of GDG_NOALLOC_MAX_NODES / 256 doubles (128 KB) in the library's own device

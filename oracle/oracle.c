@@ -265,8 +265,8 @@ static double dpsi(const double* U0, const double* Pv, double t, int d, double g
  * B_i.  The paper does not state the line search; the reading taken: the density constraints give l
  * in closed form; for the entropy constraint, keep l_rho if psi(l_rho) >= 0, otherwise bracket the
  * root of psi in [0, l_rho] and iterate with the chord (feasible, psi being concave) and the tangent
- * from the infeasible end (infeasible) until the bracket is at most tol wide; when rounding keeps both
- * points from moving strictly inside the bracket, bisect instead; return the feasible end. */
+ * from the infeasible end (infeasible), bisecting whenever an iteration has not halved the bracket,
+ * until the bracket is at most tol wide; return the feasible end. */
 static double line_search(const double* U0, const double* Pv, double rmin, double rmax, double smin,
                           int d, double g, double tol, int maxit) {
   double l = 1.0;
@@ -280,21 +280,22 @@ static double line_search(const double* U0, const double* Pv, double rmin, doubl
   if (fa < 0.0) return 0.0;
   double a = 0.0, b = l;
   for (int it = 0; it < maxit && b - a > tol; ++it) {
-    int moved = 0;
+    double width = b - a;
     double ts = a + (b - a) * fa / (fa - fb); /* chord root */
     double dfb = dpsi(U0, Pv, b, d, g, smin);
     double tn = dfb < 0.0 ? b - fb / dfb : b; /* tangent root from the infeasible end */
     if (ts > a && ts < b) {
       double fs = psi(U0, Pv, ts, d, g, smin);
       if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; }
-      moved = 1;
     }
     if (tn > a && tn < b) {
       double fn = psi(U0, Pv, tn, d, g, smin);
       if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
-      moved = 1;
     }
-    if (!moved) {
+    /* Near the root psi is evaluated below its rounding resolution (a change of t by an ulp leaves U0 + t P
+     * unchanged), and the chord and tangent points then creep towards one end while the other stays put:
+     * when the bracket has not halved, bisect, so that it always shrinks to tol. */
+    if (b - a > 0.5 * width) {
       double tm = a + 0.5 * (b - a);
       if (!(tm > a && tm < b)) break;
       double fm = psi(U0, Pv, tm, d, g, smin);
@@ -302,6 +303,11 @@ static double line_search(const double* U0, const double* Pv, double rmin, doubl
     }
   }
   return a;
+}
+
+double orc_line_search(const double* U0, const double* Pv, double rmin, double rmax, double smin, int d,
+                       double g, double tol, int maxit) {
+  return line_search(U0, Pv, rmin, rmax, smin, d, g, tol, maxit);
 }
 
 static long transpose_entry(const orc_problem* P, long i, long j) {

@@ -67,6 +67,10 @@ typedef struct {
 
 /* Upper bound on the maximum wave speed of the 1D Riemann problem (U_L, U_R) along unit n. */
 double orc_lambda_max(const double* UL, const double* UR, const double* nrm, int dim, double gamma);
+/* The line search of the limiter (Sec. 5.4): the largest l in [0, 1] with U0 + l Pv inside the bounds
+ * rho in [rmin, rmax], p / rho^g >= smin (see oracle.c for the iteration). */
+double orc_line_search(const double* U0, const double* Pv, double rmin, double rmax, double smin, int dim,
+                       double gamma, double tol, int maxit);
 /* Boundary state of an in/outflow entry (Sec. 4.1, eqs. (eq:supersonic_inoutflow), (eq:characteristics))
  * from the interior state Ui, the given data Ud and the outward unit normal nrm; written to UB. */
 void orc_inoutflow_state(const double* Ui, const double* Ud, const double* nrm, int dim, double gamma, double* UB);

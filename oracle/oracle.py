@@ -63,6 +63,9 @@ def lib():
     if _lib is None:
         L = C.CDLL(build())
         L.orc_inoutflow_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        L.orc_line_search.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
+                                      C.c_double, C.c_double, C.c_int]
+        L.orc_line_search.restype = C.c_double
         L.orc_lambda_max_batch.argtypes = [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                            C.c_void_p]
         L.orc_max_dt.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_void_p, C.c_double,
@@ -178,6 +181,13 @@ class Oracle:
         U2, f = self.stage(U1, tau, U_base=U, alpha=0.75, bdata=bd(t + tau)); flags |= f
         U3, f = self.stage(U2, tau, U_base=U, alpha=1.0 / 3.0, bdata=bd(t + 0.5 * tau)); flags |= f
         return U3, flags
+
+
+def line_search(U0, Pv, rmin, rmax, smin, gamma=1.4, tol=1e-14, maxit=50):
+    """The limiter's line search (orc_line_search) for one state U0 [m] and direction Pv [m]."""
+    U0 = np.ascontiguousarray(U0, np.float64)
+    Pv = np.ascontiguousarray(Pv, np.float64)
+    return lib().orc_line_search(_p(U0), _p(Pv), rmin, rmax, smin, U0.shape[0] - 2, gamma, tol, maxit)
 
 
 def inoutflow_state(Ui, Ud, nrm, gamma=1.4):

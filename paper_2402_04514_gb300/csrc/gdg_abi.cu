@@ -300,8 +300,9 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   std::vector<int> border(nb);
   for (int64_t b = 0; b < nb; ++b) {
     if (P->b_node[b] < 0 || P->b_node[b] >= n) return fail(GDG_ESETUP);
-    if (P->b_type[b] != GDG_BC_SLIP && P->b_type[b] != GDG_BC_DIRICHLET) return fail(GDG_ESETUP);
-    if (P->b_type[b] == GDG_BC_DIRICHLET) h->has_dirichlet = true;
+    if (P->b_type[b] != GDG_BC_SLIP && P->b_type[b] != GDG_BC_DIRICHLET && P->b_type[b] != GDG_BC_INOUTFLOW)
+      return fail(GDG_ESETUP);
+    if (P->b_type[b] != GDG_BC_SLIP) h->has_dirichlet = true;  // Dirichlet and in/outflow entries need data
     double c2 = 0;
     for (int k = 0; k < dim; ++k) c2 += P->b_c[(size_t)k * nb + b] * P->b_c[(size_t)k * nb + b];
     if (!(c2 > 0.0)) return fail(GDG_ESETUP);

@@ -428,7 +428,67 @@ __device__ __forceinline__ double internal_energy(const double* U) {
   return U[DIM + 1] - 0.5 * m2 / U[0];
 }
 
-// Slip (Sec. 4.1, eq. (eq:slip_boundary)) or Dirichlet boundary state of entry b.
+// In- and outflow boundary state (Sec. 4.1) from the interior state Ui, the data Ud and the outward unit
+// normal n: supersonic inflow (v.n < -a) takes the data, supersonic outflow (v.n >= a) the interior state
+// (eq. (eq:supersonic_inoutflow)); in between, the characteristic variables of eq. (eq:characteristics),
+// R = {v_n - 2a/(g-1), p/rho^g, v - (v.n) n, v_n + 2a/(g-1)}, are the data's where the characteristic speed
+// at the interior state {v_n - a, v_n, v_n, v_n + a} is <= 0 and the interior state's otherwise, and the
+// state is rebuilt from them.  Where the blend admits no state (a <= 0, a vacuum) the interior state is
+// used.  Boundary entries only: plain FP64 with CUDA's sqrt and pow.
+template <int DIM>
+__device__ __forceinline__ void inoutflow_state(double g, const double* Ui, const double* Ud, const double* n,
+                                                double* UB) {
+  constexpr int M = DIM + 2;
+  double vi[DIM], vd[DIM], m2i = 0.0, m2d = 0.0, vni = 0.0, vnd = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    vi[k] = Ui[1 + k] / Ui[0];
+    vd[k] = Ud[1 + k] / Ud[0];
+    m2i += Ui[1 + k] * Ui[1 + k];
+    m2d += Ud[1 + k] * Ud[1 + k];
+    vni += vi[k] * n[k];
+    vnd += vd[k] * n[k];
+  }
+  const double pi = (g - 1.0) * (Ui[DIM + 1] - 0.5 * m2i / Ui[0]);
+  const double ai = sqrt(g * pi / Ui[0]);
+  if (vni < -ai) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) UB[q] = Ud[q];
+    return;
+  }
+  if (vni >= ai) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) UB[q] = Ui[q];
+    return;
+  }
+  const double pd = (g - 1.0) * (Ud[DIM + 1] - 0.5 * m2d / Ud[0]);
+  const double ad = sqrt(g * pd / Ud[0]);
+  const bool in = vni <= 0.0;  // the middle characteristics come in
+  const double R1 = vnd - 2.0 * ad / (g - 1.0);
+  const double R4 = vni + 2.0 * ai / (g - 1.0);
+  const double R2 = in ? pd / pow(Ud[0], g) : pi / pow(Ui[0], g);
+  const double vns = in ? vnd : vni;
+  const double vn = 0.5 * (R1 + R4);
+  const double a = 0.25 * (g - 1.0) * (R4 - R1);
+  if (!(a > 0.0)) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) UB[q] = Ui[q];
+    return;
+  }
+  const double rho = pow(a * a / (g * R2), 1.0 / (g - 1.0));
+  const double p = R2 * pow(rho, g);
+  double v2 = 0.0;
+  UB[0] = rho;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const double vk = vn * n[k] + ((in ? vd[k] : vi[k]) - vns * n[k]);
+    UB[1 + k] = rho * vk;
+    v2 += vk * vk;
+  }
+  UB[DIM + 1] = p / (g - 1.0) + 0.5 * rho * v2;
+}
+
+// Slip (Sec. 4.1, eq. (eq:slip_boundary)), Dirichlet or in/outflow boundary state of entry b.
 template <int DIM>
 __device__ __forceinline__ void boundary_state(const Dev& D, int b, const double* Ui, const double* bdata,
                                                const double* n, double* UB) {
@@ -437,6 +497,12 @@ __device__ __forceinline__ void boundary_state(const Dev& D, int b, const double
     int o = D.borig[b];
 #pragma unroll
     for (int q = 0; q < M; ++q) UB[q] = bdata[(size_t)q * D.nb + o];
+  } else if (D.btype[b] == GDG_BC_INOUTFLOW) {
+    const int o = D.borig[b];
+    double Ud[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) Ud[q] = bdata[(size_t)q * D.nb + o];
+    inoutflow_state<DIM>(D.gamma, Ui, Ud, n, UB);
   } else {
     double mn = 0.0;
 #pragma unroll
@@ -561,8 +627,8 @@ __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, 
 // common cases: the entropy constraint holds at l_rho (proved by the FP32 certificate, else by psi in FP64),
 // or psi(0) < 0 (roundoff) and l = 0.  It returns false when psi(l_rho) < 0 <= psi(0); then the tail runs
 // a bracketed iteration on the concave psi from [0, l_rho]: the chord root stays feasible, the tangent root
-// from the infeasible end stays infeasible (bisection when rounding keeps both from moving); it stops when
-// the bracket is at most ls_tol wide and returns the feasible end.  The FP32 certificate only skips FP64
+// from the infeasible end stays infeasible, and a bisection follows every iteration that has not halved the
+// bracket; it stops when the bracket is at most ls_tol wide and returns the feasible end.  The FP32 certificate only skips FP64
 // evaluations whose outcome it proves; the result is that of the FP64 search.
 template <int DIM>
 __device__ __forceinline__ bool line_search_head(const Dev& D, const LsRow<DIM>& c, const double* A, double w,
@@ -604,21 +670,22 @@ __device__ double line_search_tail(const Dev& D, const LsRow<DIM>& c, const doub
   double fa = c.psi0;
   double a = 0.0, b = l;
   for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {
-    bool moved = false;
+    const double width = b - a;
     double ts = a + (b - a) * fa / (fa - fb);
     double dfb = w * ls_dpsi<DIM>(D, U0, A, b * w, smin);
     double tn = dfb < 0.0 ? b - fb / dfb : b;
     if (ts > a && ts < b) {
       double fs = ls_psi<DIM>(D, U0, A, ts * w, smin);
       if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; }
-      moved = true;
     }
     if (tn > a && tn < b) {
       double fn = ls_psi<DIM>(D, U0, A, tn * w, smin);
       if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
-      moved = true;
     }
-    if (!moved) {  // rounding pinned both points to the bracket ends: bisect
+    // Near the root psi is evaluated below its rounding resolution (a change of t by an ulp leaves
+    // U0 + t P unchanged), and the chord and tangent points then creep towards one end while the other
+    // stays put: when the bracket has not halved, bisect, so that it always shrinks to ls_tol.
+    if (b - a > 0.5 * width) {
       double tm = a + 0.5 * (b - a);
       if (!(tm > a && tm < b)) break;
       double fm = ls_psi<DIM>(D, U0, A, tm * w, smin);

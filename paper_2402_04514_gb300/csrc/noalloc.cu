@@ -83,12 +83,18 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_partial(Dev D, gdg_dev_mes
       const double cn = sqrt(c2);
       for (int k = 0; k < DIM; ++k) nv[k] /= cn;
       double UB[Mc];
-      if (M.b_type[b] == GDG_BC_DIRICHLET) {
+      if (M.b_type[b] == GDG_BC_DIRICHLET || M.b_type[b] == GDG_BC_INOUTFLOW) {
         if (!bdata) {
           dsum = NAN;
           break;
         }
-        for (int q = 0; q < Mc; ++q) UB[q] = bdata[(size_t)q * M.nb + b];
+        if (M.b_type[b] == GDG_BC_DIRICHLET) {
+          for (int q = 0; q < Mc; ++q) UB[q] = bdata[(size_t)q * M.nb + b];
+        } else {
+          double Ud[Mc];
+          for (int q = 0; q < Mc; ++q) Ud[q] = bdata[(size_t)q * M.nb + b];
+          inoutflow_state<DIM>(D.gamma, Ui, Ud, nv, UB);
+        }
       } else {
         double mn = 0.0;
         for (int k = 0; k < DIM; ++k) mn += Ui[1 + k] * nv[k];

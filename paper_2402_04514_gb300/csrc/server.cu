@@ -415,7 +415,7 @@ int gdg_server_submit(gdg_server* s, const gdg_problem* P, const double* U0, con
   const int m = P->dim + 2;
   const int64_t n = P->n, nnz = P->nnz, nb = P->nb, nel = P->n / std::max(1, P->n_loc);
   bool dirichlet = false;
-  for (int64_t b = 0; b < nb && P->b_type; ++b) dirichlet = dirichlet || P->b_type[b] == GDG_BC_DIRICHLET;
+  for (int64_t b = 0; b < nb && P->b_type; ++b) dirichlet = dirichlet || P->b_type[b] != GDG_BC_SLIP;  // data needed
   if (dirichlet && !bdata) return GDG_EINVAL;
   r->footprint = arena + (int64_t)sizeof(double) * (3 * m * n + (dirichlet ? m * nb : 0)) + 4096;
   if (r->footprint > s->budget) return GDG_ENOMEM;  // could never be admitted

@@ -14,7 +14,7 @@ from . import build as _build
 
 ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
 KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock", "axpy")  # GDG_K_*
-BC_SLIP, BC_DIRICHLET = 0, 1
+BC_SLIP, BC_DIRICHLET, BC_INOUTFLOW = 0, 1, 2
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 
 _CODES = {0: "GDG_OK", 1: "GDG_EINVAL", 2: "GDG_ENOMEM", 3: "GDG_ECUDA", 4: "GDG_ESETUP", 5: "GDG_EADMISSIBLE",
@@ -237,7 +237,7 @@ class Solver:
         self.nb = int(P.b_node.shape[0])
         self.nnz = int(P.col_idx.shape[0])
         self.gamma = gamma
-        self.has_dirichlet = bool((np.asarray(P.b_type) == BC_DIRICHLET).any())
+        self.has_dirichlet = bool((np.asarray(P.b_type) != BC_SLIP).any())  # Dirichlet or in/outflow data
         cp, keep = _problem_struct(P, gamma, params)
         self._params = cp.params
         h = C.c_void_p()

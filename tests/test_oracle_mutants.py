@@ -62,6 +62,7 @@ FAST_PINS = [
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 4.0),
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 0.0),
     lambda O: pins.test_sod_exact_solution(O),
+    lambda O: pins.test_line_search_converges_to_the_root(O),
 ]
 
 

@@ -277,3 +277,56 @@ def test_vortex_is_a_steady_solution_in_its_frame():
         vt = vel[1]
         assert np.allclose(dp, rho * vt ** 2 / r, rtol=1e-6, atol=1e-12)
         assert np.allclose(p, rho ** g, rtol=1e-13)
+
+
+def _entropy_root(U0, Pv, smin, g, lo, hi):
+    """The largest l in [lo, hi] with psi(l) = eps(U0 + l Pv) - smin rho^g >= 0, in 50-digit arithmetic."""
+    import mpmath as mp
+
+    mp.mp.dps = 50
+    U = [mp.mpf(float(x)) for x in U0]
+    P = [mp.mpf(float(x)) for x in Pv]
+    d = len(U) - 2
+
+    def psi(t):
+        V = [U[q] + t * P[q] for q in range(d + 2)]
+        return V[-1] - sum(V[1 + k] ** 2 for k in range(d)) / (2 * V[0]) - mp.mpf(smin) * V[0] ** mp.mpf(g)
+
+    if psi(mp.mpf(hi)) >= 0:
+        return float(hi)
+    return float(mp.findroot(psi, (mp.mpf(lo), mp.mpf(hi)), solver="anderson"))
+
+
+def test_line_search_converges_to_the_root(oracle_mod):
+    """The limiter's line search (Sec. 5.4; the paper leaves it unstated: the bracketed chord / tangent /
+    bisection iteration of the design notes) returns the feasible end of a bracket at most 1e-14 wide, so
+    its result is within 1e-12 of the exact largest feasible l.  Two kinds of searches: random states and
+    directions, and directions that change only the total energy, where psi is linear in l and the chord
+    and the tangent both land on the root at once."""
+    g = 1.4
+    rng = np.random.default_rng(11)
+    checked = 0
+    for case in range(600):
+        rho = float(np.exp(rng.uniform(-1, 1)))
+        v = rng.uniform(-1, 1, 2)
+        p = float(np.exp(rng.uniform(-1, 1)))
+        U0 = workloads.prim_to_cons(np.array([rho]), v.reshape(2, 1), np.array([p]), g)[:, 0]
+        eps0 = p / (g - 1.0)
+        s0 = eps0 / rho ** g
+        smin = s0 * rng.uniform(0.5, 0.999)
+        if case % 2:  # energy only: psi linear, root inside (0, 1)
+            Pv = np.zeros(4)
+            Pv[3] = -(eps0 - smin * rho ** g) / rng.uniform(0.05, 0.95)
+        else:
+            Pv = rng.normal(size=4) * np.array([0.3 * rho, rho, rho, 2 * p])
+        lres = oracle_mod.line_search(U0, Pv, 0.0, np.inf, smin, gamma=g)
+        V = U0 + min(1.0, lres) * Pv
+        if not (V[0] > 0):
+            continue
+        hi = 1.0
+        while (U0 + hi * Pv)[0] <= 0:
+            hi *= 0.5
+        exact = _entropy_root(U0, Pv, smin, g, 0.0, hi)
+        assert abs(lres - exact) <= 1e-12, (case, lres, exact)
+        checked += 1
+    assert checked > 400

@@ -56,11 +56,13 @@ def _cases():
     P2, U2, bd = dirichlet_vortex_problem(9, 1)
     P3 = assembly.assemble_1d(300, 1)
     U3 = workloads.sod(P3.x[0])
+    P4 = assembly.assemble_1d(120, 2, bc=("inoutflow", "inoutflow"))
+    U4 = workloads.sod(P4.x[0])
     return [("q2_four_quadrant_slip", P1, U1, None, 1.4), ("q1_vortex_dirichlet", P2, U2, bd(0.0), 5.0 / 3.0),
-            ("sod_1d", P3, U3, None, 1.4)]
+            ("sod_1d", P3, U3, None, 1.4), ("sod_1d_inoutflow", P4, U4, workloads.sod(P4.b_x[0]), 1.4)]
 
 
-@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("case", range(4))
 def test_no_alloc_max_dt_matches_handle_max_dt(torch_cuda, case):
     torch = torch_cuda
     from paper_2402_04514_gb300.gdg import Solver, max_dt_noalloc
