@@ -89,6 +89,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (all ranks get it): the job is done when its last rank is."""
+    import torch
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units processed by all ranks (replicas: each rank the same work) per second of the slowest rank."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def oracle_sample_rate(steps, warmup=0, log=None):
     """DoF-stage updates/s of the CPU oracle (single thread) on the 128^2 sample; returns (value, seconds)."""
     from oracle.oracle import Oracle
@@ -413,11 +428,8 @@ def main():
     prof = solver.profile_read()
     solver.profile(False)
     flags = solver.status()
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * n * 3 * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(world, n * 3 * args.steps, ms_max)
     launches = sum(c for _, c in prof.values())
 
     # roofline of the dominant kernel (its own launches' CUDA-event times inside the timed region)
@@ -468,10 +480,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = torch.tensor([e0.elapsed_time(e1)], device="cuda", dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n * 3 * args.steps / (float(ems.item()) / 1e3), "unit": METRIC,
+        ems = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": whole_job_rate(world, n * 3 * args.steps, ems), "unit": METRIC,
                "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(U.numel() * 8)}
 
     if rank != 0:
