@@ -96,7 +96,7 @@ struct Arena {
 // The device arena of a handle: every array with its element type and count (m = dim + 2 components,
 // ne canonical stencil edges, nel elements of nl nodes).  gdg_setup allocates it; gdg_footprint sizes it.
 #define GDG_ARENA(X)                                                                                       \
-  X(rowptr, int, n + 1) X(col, int, nnz) X(tr, int, nnz) X(cnorm, double, nnz) X(cn, double, dim * nnz)   \
+  X(rowptr, int, n + 1) X(sten, int, n) X(col, int, nnz) X(tr, int, nnz) X(cnorm, double, nnz) X(cn, double, dim * nnz)   \
   X(mij, double, nnz) X(mu, double, nnz) X(mi, double, n) X(imi, double, n) X(ikm, double, n)             \
   X(rm, double, n) X(rp, double, n) X(muB, double, n) X(bptr, int, n + 1) X(bnorm, double, nb)           \
   X(bn, double, dim * nb) X(btype, int, nb) X(borig, int, nb) X(minv, double, nel * nl * nl)             \
@@ -249,8 +249,40 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     if (i > 0 && P->row_ptr[i] < P->row_ptr[i - 1]) return fail(GDG_ESETUP);
     h->row_ptr[i] = (int)P->row_ptr[i];
   }
-  h->col.assign(P->col_idx, P->col_idx + nnz);
-  h->coloc.assign(P->coloc, P->coloc + nnz);
+  // Device entry order: within each row the stencil entries (c_ij != 0) come first, then the
+  // m_ij-only entries, each group in the caller's order, so the stencil loops of the sweeps run over a
+  // contiguous prefix of the row with no per-entry test.  eorig[q] is the caller's index of entry q.
+  h->eorig.resize(nnz);
+  std::vector<int> sten_end(n);
+  {
+    auto nz = [&](int64_t q) {  // the test |c_ij| > 0 of the stencil edges below
+      double c2 = 0;
+      for (int k = 0; k < dim; ++k) c2 += P->cij[(size_t)k * nnz + q] * P->cij[(size_t)k * nnz + q];
+      return c2 > 0.0;
+    };
+    parallel_for(n, [&](int64_t b, int64_t e) {
+      for (int64_t i = b; i < e; ++i) {
+        int k = h->row_ptr[i];
+        for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q)
+          if (nz(q)) h->eorig[k++] = q;
+        sten_end[i] = k;
+        for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q)
+          if (!nz(q)) h->eorig[k++] = q;
+      }
+    });
+  }
+  std::vector<double> cijv((size_t)dim * nnz);
+  h->col.resize(nnz);
+  h->coloc.resize(nnz);
+  parallel_for(nnz, [&](int64_t b, int64_t e) {
+    for (int64_t q = b; q < e; ++q) {
+      const int64_t o = h->eorig[q];
+      h->col[q] = P->col_idx[o];
+      h->coloc[q] = P->coloc[o];
+      for (int k = 0; k < dim; ++k) cijv[(size_t)k * nnz + q] = P->cij[(size_t)k * nnz + o];
+    }
+  });
+  const double* cij = cijv.data();
   h->mi.assign(P->mi, P->mi + n);
   {
     std::vector<char> rowbad(n, 0);
@@ -289,7 +321,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
             if (h->col[r] == i) { t = r; break; }
           if (t < 0 || h->coloc[t] != h->coloc[q]) { bad[i] = 1; continue; }
           for (int k = 0; k < dim; ++k)
-            if (P->cij[(size_t)k * nnz + t] != -P->cij[(size_t)k * nnz + q]) bad[i] = 1;
+            if (cij[(size_t)k * nnz + t] != -cij[(size_t)k * nnz + q]) bad[i] = 1;
           h->tr[q] = t;
         }
     });
@@ -321,7 +353,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
         for (int k = 0; k < dim; ++k) {
           double s = 0, a = 0;
           for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
-            double c = P->cij[(size_t)k * nnz + q];
+            double c = cij[(size_t)k * nnz + q];
             s += c;
             a += std::fabs(c);
           }
@@ -364,10 +396,10 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     for (int64_t i = b; i < e; ++i)
       for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q) {
         double c2 = 0;
-        for (int k = 0; k < dim; ++k) c2 += P->cij[(size_t)k * nnz + q] * P->cij[(size_t)k * nnz + q];
+        for (int k = 0; k < dim; ++k) c2 += cij[(size_t)k * nnz + q] * cij[(size_t)k * nnz + q];
         double cm = std::sqrt(c2);
         cnorm[q] = cm;
-        for (int k = 0; k < dim; ++k) cn[(size_t)k * nnz + q] = cm > 0 ? P->cij[(size_t)k * nnz + q] / cm : 0.0;
+        for (int k = 0; k < dim; ++k) cn[(size_t)k * nnz + q] = cm > 0 ? cij[(size_t)k * nnz + q] / cm : 0.0;
         int j = h->col[q];
         if (j / nl == i / nl) mij[q] = P->MK[((size_t)(i / nl) * nl + i % nl) * nl + j % nl];
       }
@@ -425,6 +457,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     return cudaMemcpy(ptr(o), src, bytes, cudaMemcpyHostToDevice);
   };
   if ((ce = up(o_rowptr, h->row_ptr.data(), sizeof(int) * (n + 1))) != cudaSuccess ||
+      (ce = up(o_sten, sten_end.data(), sizeof(int) * n)) != cudaSuccess ||
       (ce = up(o_col, h->col.data(), sizeof(int) * nnz)) != cudaSuccess ||
       (ce = up(o_tr, h->tr.data(), sizeof(int) * nnz)) != cudaSuccess ||
       (ce = up(o_cnorm, cnorm.data(), sizeof(double) * nnz)) != cudaSuccess ||
@@ -450,6 +483,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   D.nb = (int)nb;
   D.n_loc = nl;
   D.row_ptr = (const int*)ptr(o_rowptr);
+  D.sten_end = (const int*)ptr(o_sten);
   D.col = (const int*)ptr(o_col);
   D.tr = (const int*)ptr(o_tr);
   D.cnorm = (const double*)ptr(o_cnorm);
@@ -815,13 +849,14 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count
   const double* src = nullptr;
   int64_t want = -1;
   int kind = 0;  // 0 plain copy, 1 symmetrised per-entry limiter, 2 boundary order
+  bool per_entry = false;
   std::string nm(name);
-  if (nm == "dL") { src = h->S.dL; want = nnz; }
+  if (nm == "dL") { src = h->S.dL; want = nnz; per_entry = true; }
   else if (nm == "dB") { src = h->S.dB; want = nb; kind = 2; }
   else if (nm == "N") { src = h->S.N; want = n; }
   else if (nm == "UL") { src = h->S.UL; want = m * n; }
   else if (nm == "U1") { src = h->S.U1; want = m * n; }
-  else if (nm == "A") { src = h->S.A; want = m * nnz; }
+  else if (nm == "A") { src = h->S.A; want = m * nnz; per_entry = true; }
   else if (nm == "rho_min") { src = h->S.bounds; want = n; }
   else if (nm == "rho_max") { src = h->S.bounds + n; want = n; }
   else if (nm == "s_min") { src = h->S.bounds + 2 * n; want = n; }
@@ -842,10 +877,13 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count
   std::vector<double> tmp(want);
   if (want > 0 && (e = cudaMemcpy(tmp.data(), src, sizeof(double) * want, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e);
-  if (kind == 0) {
+  if (kind == 0 && per_entry) {  // device entry order back to the caller's
+    for (int64_t r = 0; r < want / nnz; ++r)
+      for (int64_t q = 0; q < nnz; ++q) dst[r * nnz + h->eorig[q]] = tmp[r * nnz + q];
+  } else if (kind == 0) {
     std::memcpy(dst, tmp.data(), sizeof(double) * want);
   } else if (kind == 1) {
-    for (int64_t q = 0; q < want; ++q) dst[q] = std::min(tmp[q], tmp[h->tr[q]]);
+    for (int64_t q = 0; q < want; ++q) dst[h->eorig[q]] = std::min(tmp[q], tmp[h->tr[q]]);
   } else {
     for (int64_t t = 0; t < want; ++t) dst[h->borig[t]] = tmp[t];
   }

@@ -13,15 +13,14 @@ namespace gdg {
 // Per-node primitive record written by k_prim and read for every neighbour in the sweeps.
 enum { PR_IRHO = 0, PR_P, PR_A, PR_PME, PR_F, PR_ST, PR_IP, NPRIM };
 
-// Per-entry flag bits.
-enum { EF_STENCIL = 1, EF_COLOC = 2, EF_SAME_ELEM = 4 };
-
 // Everything a kernel needs, passed by value.  Per-entry and per-node arrays are device pointers in
-// CSR order (rows element-contiguous); boundary entries are sorted by node (b_ptr indexes them).
+// CSR order (rows element-contiguous; within a row the stencil entries c_ij != 0 come first, then the
+// m_ij-only entries); boundary entries are sorted by node (b_ptr indexes them).
 struct Dev {
   int n, nnz, nb, n_loc;
   // CSR
   const int* row_ptr;   // [n+1]
+  const int* sten_end;  // [n] end of row i's stencil entries: I(i) is row_ptr[i] .. sten_end[i] - 1
   const int* col;       // [nnz]
   const int* tr;        // [nnz] position of the transposed entry (j, i)
   const double* cnorm;  // [nnz] |c_ij| (0 when c_ij = 0)

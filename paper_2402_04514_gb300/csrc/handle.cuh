@@ -19,6 +19,7 @@ struct gdg_handle {
   gdg::Scratch S{};
   // host copies needed after setup
   std::vector<int> row_ptr, col, tr, borig, bnode_sorted;
+  std::vector<int> eorig;  // caller's index of each device entry (rows are stencil-first on the device)
   std::vector<uint8_t> coloc;
   std::vector<double> mi;
   // device pointers of the parameter-dependent arrays

@@ -8,6 +8,43 @@ namespace gdg {
 namespace {
 
 constexpr int kMaxBlock = kHighMaxBlock;
+constexpr int kMaxLocal = 32;  // n_loc limit of gdg_setup
+
+// Thread-to-node map of an element block.  Lanes that take the same trip counts through the row loops
+// should share a warp, so the block's nodes are dealt out by local index: the epb = npb / n_loc elements
+// of the block take consecutive threads for one local index, and the local indices come in order of
+// decreasing row length (taken from the block's first element; rows of equal length keep their order).
+// When every local index has the same row length the identity map is kept, so that the per-node loads
+// of an element stay contiguous.  Returns the position of thread t's node within the block (the element
+// is slot / n_loc, the local index slot % n_loc); threads past npb keep t.  *pad is set to 1 when the
+// shared arrays should space elements n_loc + 1 apart: under the dealt-out map the lanes of a warp read
+// one node of each of several elements, and an even n_loc would put them in the same shared bank.
+__device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t, int* s_order, int* s_mixed,
+                                            int* pad) {
+  const int nl = D.n_loc;
+  if (t == 0) *s_mixed = 0;
+  __syncthreads();
+  if (t < nl) {
+    const long long first = (long long)lb * npb;  // the block's first element always exists
+    auto len = [&](int l) {
+      const long long v = first + l;
+      return v < D.n ? D.row_ptr[v + 1] - D.row_ptr[v] : 0;
+    };
+    const int mine = len(t);
+    int rank = 0;
+    for (int o = 0; o < nl; ++o) {
+      const int lo = len(o);
+      rank += (lo > mine) || (lo == mine && o < t);
+      if (lo != mine) *s_mixed = 1;
+    }
+    s_order[rank] = t;
+  }
+  __syncthreads();
+  *pad = *s_mixed && !(nl & 1);
+  if (!*s_mixed || t >= npb) return t;
+  const int epb = npb / nl;
+  return (t % epb) * nl + s_order[t / epb];
+}
 
 // Per node i of the block:
 //  1. d_ij^H = max(d^min, d^ev) (Sec. 5, eq. (HighOrderViscosity); Sec. 5.1, eq. (ViscMin); Sec. 5.2),
@@ -25,9 +62,12 @@ constexpr int kMaxBlock = kHighMaxBlock;
 template <int DIM, class Src>
 __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_block) {
   constexpr int M = DIM + 2;
-  __shared__ double sR[M][kMaxBlock];
-  __shared__ double sdU[M][kMaxBlock];
+  constexpr int kShared = kMaxBlock + kMaxBlock / 2;  // room for one pad slot per element of 2+ nodes
+  __shared__ double sR[M][kShared];
+  __shared__ double sdU[M][kShared];
   __shared__ Ctx sctx;
+  __shared__ int s_order[kMaxLocal];
+  __shared__ int s_mixed;
   int lb;
   const Ctx& c = src.get(&sctx, &lb);
   if (finished(c)) return;
@@ -35,9 +75,11 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
   const Scratch& S = c.S;
   const double* U = c.U;
   const double* bdata = c.bdata;
-  const int t = threadIdx.x;
-  const int i = lb * nodes_per_block + t;
-  const bool valid = t < nodes_per_block && i < D.n;
+  int pad;
+  const int slot = element_slot(D, lb, nodes_per_block, threadIdx.x, s_order, &s_mixed, &pad);
+  const int i = lb * nodes_per_block + slot;
+  const bool valid = slot < nodes_per_block && i < D.n;
+  const int sh = slot + pad * (slot / D.n_loc);  // slot in the shared arrays
   const size_t n = D.n;
   const double tau = stage_tau(c);
   double Ui[M], dUi[M];
@@ -48,9 +90,9 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
     double rhs[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) rhs[q] = S.RHSL[(size_t)q * n + i];
-    // min / max of non-negative values and the m_ij-only test on the integer pipe
-    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-      if (is_zero_bits(D.cnorm[e])) continue;  // m_ij-only entry: not in I(i)
+    // min / max of non-negative values on the integer pipe
+    const int e1 = D.sten_end[i];
+    for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
       const double dl = S.dL[e];
       const int j = D.col[e];
       const double dev = dl * pmin(D.c_ev * pmax(Ni, abs_bits(S.N[j])), 1.0);
@@ -77,13 +119,13 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
       }
     }
 #pragma unroll
-    for (int q = 0; q < M; ++q) sR[q][t] = rhs[q];
+    for (int q = 0; q < M; ++q) sR[q][sh] = rhs[q];
   }
   __syncthreads();
   if (valid) {
     const int nl = D.n_loc;
     const int il = i % nl;
-    const int t0 = t - il;  // first node of the element in the block
+    const int t0 = sh - il;  // first node of the element in the shared arrays
     const double* Minv = D.MKinv + ((size_t)(i / nl) * nl + il) * nl;
     double acc[M];
 #pragma unroll
@@ -96,7 +138,7 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
 #pragma unroll
     for (int q = 0; q < M; ++q) {
       dUi[q] = -tau * acc[q];
-      sdU[q][t] = dUi[q];
+      sdU[q][sh] = dUi[q];
     }
     if (D.order == GDG_ORDER_HIGH) {
 #pragma unroll
@@ -115,8 +157,8 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
     hi = pmax(hi, S.bbar[b]);
     sl = pmin(sl, S.bbar[(size_t)D.nb + b]);
   }
-  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-    if (is_zero_bits(D.cnorm[e])) continue;
+  const int se = D.sten_end[i];
+  for (int e = D.row_ptr[i]; e < se; ++e) {
     int j = D.col[e];
     lo = pmin(lo, S.agg[j]);
     hi = pmax(hi, S.agg[n + j]);
@@ -145,11 +187,11 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
   const float ikmf = d2f_fast(ikm);
   const int nl = D.n_loc;
   const int elem = i / nl;
-  const int t0 = t - (i % nl);
+  const int t0 = sh - (i % nl);
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int j = D.col[e];
     double A[M];
-    const bool stencil = !is_zero_bits(D.cnorm[e]);
+    const bool stencil = e < se;
     const bool same = (j / nl) == elem;
     const double mij = same ? D.mij[e] : 0.0;
     const int tj = t0 + (j % nl);

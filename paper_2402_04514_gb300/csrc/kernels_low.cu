@@ -111,9 +111,9 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
     double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], ip_i = P[PR_IP * n + i], a_i = P[PR_A * n + i],
            pme_i = P[PR_PME * n + i];
     double dsum = 0.0;
-    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+    const int e1 = D.sten_end[i];
+    for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
       double cnm = D.cnorm[e];
-      if (is_zero_bits(cnm)) continue;
       int j = D.col[e];
       double nv[DIM], uL = 0.0, uR = 0.0;
 #pragma unroll
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
   double val = INFINITY;
   if (i < D.n) {
     double dsum = 0.0;
-    for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) dsum += S.dL[e];  // m_ij-only entries hold 0
+    for (int e = D.row_ptr[i]; e < D.sten_end[i]; ++e) dsum += S.dL[e];
     const int b0 = D.b_ptr[i], b1 = D.b_ptr[i + 1];
     if (b0 < b1) {
       const size_t n = D.n;
@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   double psum = 0.0, dsum = 0.0;
   double lo = Ui[0], hi = Ui[0], sl = st_i;
   const size_t nnz = D.nnz;
-  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
-    if (is_zero_bits(D.cnorm[e])) continue;  // m_ij-only entry: not in I(i)
+  const int e1 = D.sten_end[i];
+  for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
     const int j = D.col[e], t = D.tr[e];
     const double d = S.dL[e];
     dsum += d;
