@@ -354,6 +354,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-steps", type=int, default=8)
     ap.add_argument("--fp64-rates", action="store_true", help="print the measured arithmetic rates and exit")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the sweep (mixed: GDG_PRECISION_MIXED, reported separately)")
     args = ap.parse_args()
     if args.fp64_rates:
         import torch
@@ -393,7 +395,8 @@ def main():
     spec = WORKLOADS[args.workload]
     P, U0 = make_problem(spec)
     counts = costmodel.Counts.of(P)
-    solver = Solver(P)
+    mixed = args.precision == "mixed"
+    solver = Solver(P, params=dict(precision=1 if mixed else 0))
     solver.set_clock(0.0, float("inf"), 0.5)
     stream = torch.cuda.current_stream()
     U = torch.from_numpy(U0).cuda()
@@ -459,6 +462,8 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                for k, v in prof.items() if v[1]}
+    if mixed:  # the FP64 pipe no longer bounds the mixed path's sweep: report it against HBM
+        roofline, roofline_hbm = roofline_hbm, roofline
 
     # end to end through the public API with host buffers: H2D of the step's input from pinned memory,
     # the step, D2H of its result, every step
@@ -496,9 +501,10 @@ def main():
                          f"SSP-RK3 steps, single thread, {secs:.1f} s"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**config_block(args, n), "schedule": schedule}, "roofline": roofline,
-            "roofline_hbm": roofline_hbm,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed" if mixed else "f64",
+            "data": "synthetic",
+            "config": {**config_block(args, n), "precision": args.precision, "schedule": schedule},
+            "roofline": roofline, "roofline_hbm" if not mixed else "roofline_alu": roofline_hbm,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
             "kernels": kernels, "status_flags": flags}
     print(json.dumps(line), flush=True)

@@ -49,6 +49,20 @@ enum { GDG_ORDER_LOW = 0, GDG_ORDER_HIGH = 1, GDG_ORDER_LIMITED = 2 };
 enum { GDG_BC_SLIP = 0, GDG_BC_DIRICHLET = 1, GDG_BC_INOUTFLOW = 2 };
 /* sticky device flags, read by gdg_status */
 enum { GDG_FLAG_INADMISSIBLE = 1, GDG_FLAG_CFL = 2 };
+/* arithmetic of the sweep (gdg_params.precision).  GDG_PRECISION_FP64: every step in FP64.
+ * GDG_PRECISION_MIXED: a faster path whose results differ from the FP64 path by up to about 1e-5 of
+ * max |U| per stage: the coefficients of the scheme (the primitives behind lambda_max^+ of Sec. 3.1, the
+ * wave-speed bound itself, raised by a margin that covers its FP32 rounding so that d_ij^L still bounds
+ * the FP64 value from above, the entropy-viscosity indicator of Sec. 5.2, the entropy of the bar states
+ * in the bounds of Sec. 5.4, the high-order correction dU^H of Sec. 5 and the antidiffusive fluxes A_ij
+ * of Sec. 5.3) are computed in FP32 and held as FP64 values, while the low-order fluxes and row sums,
+ * every state update and the limiter's acceptance tests stay FP64.  d_ij^L and the limiter coefficients
+ * stay symmetric and A_ij antisymmetric bit for bit, so the limited and low-order schemes conserve to
+ * FP64 rounding and the limiter enforces the local bounds exactly as in the FP64 path (the unlimited
+ * high order, a test setting, conserves only to the FP32 accuracy of dU^H).  States must have rho, p
+ * and the velocities inside the FP32 normal range (about 1e-37 .. 1e37); a wave-speed bound that comes
+ * out infinite or NaN in FP32 is recomputed in FP64. */
+enum { GDG_PRECISION_FP64 = 0, GDG_PRECISION_MIXED = 1 };
 
 /* Method parameters.  gdg_default_params fills the paper's values: c_k = 1 and p_k = 1/2 (k even),
  * 0 (k odd) of Sec. 5.1; c_ev = 1, 0.5, 0.25 for k = 1, 2, >= 3 (Sec. 5.2); c_r = 4, p_r = 1.5
@@ -63,6 +77,7 @@ typedef struct {
   double c_k, p_k, c_ev, c_r, p_r;
   double ls_tol;
   int32_t ls_maxit;
+  int32_t precision;      /* GDG_PRECISION_FP64 (default) or GDG_PRECISION_MIXED */
 } gdg_params;
 
 /* One mesh instance (all host pointers, copied by gdg_setup).
@@ -197,6 +212,14 @@ int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
  * zeros kept, NaN otherwise); x, y: device [n]; 1 <= q <= 16.  Asynchronous on stream.  The tests
  * compare 0 with 2 and 1 with 3 in ulps, and 4 with the truncation done on the host. */
 int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream);
+
+/* Check of the mixed-precision wave-speed bound (GDG_PRECISION_MIXED) against the FP64 one, for gamma
+ * and n one-dimensional Riemann problems states[k] = (rho_L, u_L, p_L, rho_R, u_R, p_R) (device [n][6],
+ * u the normal velocities): out[k] = (lambda_max^+ as the FP64 path computes it, the mixed path's
+ * bound with its margin, the same without the margin, the margin's scale S) (device [n][4]), from the
+ * per-node primitives each path computes.  The mixed bound must not fall below the FP64 one.
+ * Asynchronous on stream.  Errors: GDG_EINVAL (gamma <= 1, n < 0, NULL arrays with n > 0). */
+int gdg_wave_speed_check(double gamma, const double* states, double* out, int64_t n, void* stream);
 
 /* Measured throughput (operations per second over the GPU, timed with CUDA events) of the arithmetic
  * the sweep is made of: op 0 = FP64 FMA, 1 = FP64 division, 2 = FP64 sqrt, 3 = FP64 pow, 4 = FP32 FMA,

@@ -12,6 +12,7 @@
 
 struct gdg_batch {
   int device = 0, dim = 0, n_loc = 0, order = 0, passes = 0, count = 0;
+  bool mixed = false;                  // precision of every member (GDG_PRECISION_MIXED)
   gdg::Sched sched = gdg::default_sched();  // launch shapes (gdg_batch_autotune)
   std::vector<gdg_handle*> hs;
   void* mem = nullptr;                 // device: context tables and block offsets
@@ -43,11 +44,12 @@ cudaError_t launch_many(const gdg_batch* b, int kern, int stage, int arg, cudaSt
   const long long blocks = b->blocks[kern];
   switch (kern) {
     case gdg::KN_HIGH:
-      return gdg::launch_high_file_many(b->dim, m, blocks, gdg::high_nodes_per_block(b->n_loc, b->sched.high_cap), s);
+      return gdg::launch_high_file_many(b->dim, b->mixed, m, blocks,
+                                        gdg::high_nodes_per_block(b->n_loc, b->sched.high_cap), s);
     case gdg::KN_LIMIT2:
     case gdg::KN_FINAL:
     case gdg::KN_LSFIX: return gdg::launch_limit_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], arg, s);
-    default: return gdg::launch_low_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], arg, s);
+    default: return gdg::launch_low_file_many(kern, b->dim, b->mixed, m, blocks, b->sched.bt[kern], arg, s);
   }
 }
 
@@ -145,7 +147,7 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
   for (int k = 0; k < count; ++k) {
     const gdg_handle* h = handles[k];
     if (!h || h->device != dev || h->dim != h0->dim || h->n_loc != h0->n_loc || h->D.order != h0->D.order ||
-        h->D.passes != h0->D.passes)
+        h->D.passes != h0->D.passes || h->D.mixed != h0->D.mixed)
       return GDG_EINVAL;
     if (h->n > 0 && (!U[k] || !T1[k] || !T2[k] || U[k] == T1[k] || U[k] == T2[k] || T1[k] == T2[k]))
       return GDG_EINVAL;
@@ -160,6 +162,7 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
   b->n_loc = h0->n_loc;
   b->order = h0->D.order;
   b->passes = h0->D.passes;
+  b->mixed = h0->D.mixed != 0;
   b->count = count;
   b->hs.assign(handles, handles + count);
   // host tables: contexts of the three stages (Shu-Osher SSP-RK3, the last stage in place) and the

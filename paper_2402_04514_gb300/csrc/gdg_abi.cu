@@ -43,6 +43,7 @@ bool check_params(const gdg_params& p) {
   if (!(p.c_k >= 0) || !(p.c_ev >= 0) || !(p.c_r >= 0) || !std::isfinite(p.p_k) || !std::isfinite(p.p_r))
     return false;
   if (!(p.ls_tol > 0) || p.ls_maxit < 0) return false;
+  if (p.precision != GDG_PRECISION_FP64 && p.precision != GDG_PRECISION_MIXED) return false;
   return true;
 }
 
@@ -172,6 +173,8 @@ int upload_param_arrays(gdg_handle* h, const ParamArrays& A) {
   D.bounds_mode = p.bounds_mode;
   D.ls_tol = p.ls_tol;
   D.ls_maxit = p.ls_maxit;
+  D.mixed = p.precision == GDG_PRECISION_MIXED;
+  D.c_ev_f = (float)p.c_ev;
   return GDG_OK;
 }
 
@@ -191,6 +194,7 @@ void gdg_default_params(int32_t degree, gdg_params* out) {
   out->p_r = 1.5;
   out->ls_tol = 1e-14;
   out->ls_maxit = 50;
+  out->precision = GDG_PRECISION_FP64;
 }
 
 const char* gdg_error_string(int code) {
@@ -505,23 +509,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   D.ne = (int)ne;
   D.edge_e = (const int*)ptr(o_ee);
   D.edge_i = (const int*)ptr(o_ei);
-  D.gamma = P->gamma;
-  D.gm1 = P->gamma - 1.0;
-  D.e_exp = (P->gamma - 1.0) / (2.0 * P->gamma);
-  D.inv_e = 1.0 / D.e_exp;
-  double r = std::round(D.inv_e);
-  D.ie = (std::fabs(D.inv_e - r) < 1e-12 * D.inv_e && r >= 1 && r <= 64) ? (int)r : 0;
-  D.k13 = (P->gamma + 1.0) / (2.0 * P->gamma);
-  D.gp = D.gq = 0;
-  for (int q = 1; q <= 8 && D.gq == 0; ++q) {
-    double pg = std::round(P->gamma * q);
-    if (std::fabs(P->gamma * q - pg) < 1e-12 * pg && pg <= 64) {
-      D.gp = (int)pg;
-      D.gq = q;
-    }
-  }
-  D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
-  D.inv_gp1 = 1.0 / (P->gamma + 1.0);
+  gdg::set_eos(D, P->gamma);
   h->d_mu = (double*)ptr(o_mu);
   h->d_rminus = (double*)ptr(o_rm);
   h->d_rplus = (double*)ptr(o_rp);

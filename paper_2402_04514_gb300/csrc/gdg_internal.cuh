@@ -58,7 +58,37 @@ struct Dev {
   int order, passes, bounds_mode;
   double ls_tol;
   int ls_maxit;
+  // mixed precision (GDG_PRECISION_MIXED): the switch and FP32 copies of the constants it uses
+  int mixed;
+  float gamma_f, gm1h_f, e_exp_f, inv_e_f, k13_f, inv_gp1_f, c_ev_f;
 };
+
+// Equation-of-state constants of Dev for gamma (host side; gdg_setup and the wave-speed check).
+inline void set_eos(Dev& D, double gamma) {
+  D.gamma = gamma;
+  D.gm1 = gamma - 1.0;
+  D.e_exp = (gamma - 1.0) / (2.0 * gamma);
+  D.inv_e = 1.0 / D.e_exp;
+  const double r = __builtin_round(D.inv_e);
+  D.ie = (__builtin_fabs(D.inv_e - r) < 1e-12 * D.inv_e && r >= 1 && r <= 64) ? (int)r : 0;
+  D.k13 = (gamma + 1.0) / (2.0 * gamma);
+  D.gp = D.gq = 0;
+  for (int q = 1; q <= 8 && D.gq == 0; ++q) {
+    const double pg = __builtin_round(gamma * q);
+    if (__builtin_fabs(gamma * q - pg) < 1e-12 * pg && pg <= 64) {
+      D.gp = (int)pg;
+      D.gq = q;
+    }
+  }
+  D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
+  D.inv_gp1 = 1.0 / (gamma + 1.0);
+  D.gamma_f = (float)gamma;
+  D.gm1h_f = (float)(0.5 * D.gm1);
+  D.e_exp_f = (float)D.e_exp;
+  D.inv_e_f = (float)D.inv_e;
+  D.k13_f = (float)D.k13;
+  D.inv_gp1_f = (float)D.inv_gp1;
+}
 
 struct Scratch {
   double* prim;    // [NPRIM][n]
@@ -249,13 +279,14 @@ inline long long kernel_blocks(int k, const Dev& D, const Sched& sc) {
 // Kernel launchers of each file, dim in 1..3: one instance (context by value) or a batch (Many; blocks =
 // the batch's total for that kernel).  arg: write_out for KN_LOW (the stage ends after U^L), last for
 // KN_LIMIT2 (one limiter pass only), the pass (0 or 1) for KN_LSFIX.  threads: the block size of a
-// one-thread-per-row kernel; npb: nodes per element block of KN_HIGH.
+// one-thread-per-row kernel; npb: nodes per element block of KN_HIGH; mixed: the precision of every
+// member (single instances take it from their context).
 cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
                             cudaStream_t s);
-cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads, int arg,
                                  cudaStream_t s);
 cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s);
-cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int npb, cudaStream_t s);
+cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, long long blocks, int npb, cudaStream_t s);
 cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
                               cudaStream_t s);
 cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
@@ -407,6 +438,134 @@ __device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL,
   double l1 = uL - aL * sL;
   double l3 = uR + aR * sR;
   return fmax(fmax(-l1, 0.0), fmax(l3, 0.0));
+}
+
+// ------------------------------------------------------------------------------------------------
+// Mixed precision (GDG_PRECISION_MIXED; the contract is documented at the enum in include/gdg.h).
+
+// FP64 -> FP32 on the integer pipe, for arithmetic: the significand truncated to 23 bits (relative error
+// below 2^-23, and to_f32(-x) = -to_f32(x), which keeps antisymmetric quantities antisymmetric); values
+// below the FP32 normal range flush to +-0, values above it give +-inf, NaN stays NaN.
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned sg = hi & 0x80000000u, ah = hi & 0x7fffffffu;
+  const int e = (int)(ah >> 20) - 1023 + 127;
+  unsigned r = sg | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e <= 0) r = sg;
+  if (e >= 255) r = (ah > 0x7ff00000u || (ah == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : (sg | 0x7f800000u);
+  return __uint_as_float(r);
+}
+
+// FP32 -> FP64 on the integer pipe: exact for normal numbers, zeros, infinities and NaN; FP32 subnormals
+// flush to +-0.
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, mt = u & 0x7fffffu;
+  unsigned hi = sg | ((e + 896u) << 20) | (mt >> 3), lo = mt << 29;
+  if (e == 255u) hi = sg | 0x7ff00000u | (mt >> 3);
+  if (e == 0u) {
+    hi = sg;
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ bool finite_f32(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
+
+__device__ __forceinline__ float ipowf(float x, int k) {
+  float r = 1.f;
+  while (k > 0) {
+    if (k & 1) r *= x;
+    x *= x;
+    k >>= 1;
+  }
+  return r;
+}
+
+// The FP32 primitives the mixed path's wave-speed bound takes from a node: 1/p, a = sqrt(gamma p / rho)
+// and p^{-e} (Sec. 2.2), from the FP64 rho and p.
+struct PrimF {
+  float ip, a, pme;
+};
+__device__ __forceinline__ PrimF prim_mx(const Dev& D, double rho, double p) {
+  const float rf = to_f32(rho), pf = to_f32(p);
+  PrimF o;
+  o.ip = 1.f / pf;
+  o.a = sqrtf(D.gamma_f * pf / rf);
+  o.pme = powf(pf, -D.e_exp_f);
+  return o;
+}
+
+// Margin of the mixed path's wave-speed bound, relative to S = |u_L| + |u_R| + a_L s_L + a_R s_R, which
+// is at least lambda (-lambda_1 <= |u_L| + a_L s_L, lambda_3 <= |u_R| + a_R s_R).  Every FP32 operation
+// and input of lambda_max_mx is within a few ulp (2^-23) of its FP64 counterpart; the largest
+// amplification is the power 1/e of p~ (7 for gamma = 1.4, 5 for 5/3), which reaches s_L, s_R through a
+// square root, so that the FP32 bound differs from the FP64 one by less than 2^-17 S (the largest
+// difference seen over several million states, including near-vacuum and near-equal pairs, is 2^-19.9 S).
+// The margin is twice that bound.
+constexpr float kMxMargin = 1.52587890625e-05f;  // 2^-16
+
+// lambda_max^+ of the FP64 path's formula (lambda_max) evaluated in FP32 and raised by kMxMargin S.  The
+// denominators and S are summed without contraction, so that the bound is symmetric under
+// (L, R, n) -> (R, L, -n) bit for bit like the FP64 one.  raw / scale (optional) receive the value
+// before the margin and S.
+__device__ __forceinline__ float lambda_max_mx(const Dev& D, float uL, float pL, const PrimF& L, float uR, float pR,
+                                               const PrimF& R, float* raw = nullptr, float* scale = nullptr) {
+  const float num = fmaxf(L.a + R.a - D.gm1h_f * (uR - uL), 0.f);
+  const float den = __fadd_rn(__fmul_rn(L.a, L.pme), __fmul_rn(R.a, R.pme));
+  const float r = num / den;
+  const float pt = D.ie > 0 ? ipowf(r, D.ie) : powf(r, D.inv_e_f);
+  const float xL = pt - pL, xR = pt - pR;
+  const float sL = xL > 0.f ? sqrtf(1.f + D.k13_f * xL * L.ip) : 1.f;
+  const float sR = xR > 0.f ? sqrtf(1.f + D.k13_f * xR * R.ip) : 1.f;
+  const float l1 = uL - L.a * sL;
+  const float l3 = uR + R.a * sR;
+  const float lam = fmaxf(fmaxf(-l1, 0.f), fmaxf(l3, 0.f));
+  const float S = __fadd_rn(__fadd_rn(fabsf(uL), fabsf(uR)), __fadd_rn(__fmul_rn(L.a, sL), __fmul_rn(R.a, sR)));
+  if (raw) *raw = lam;
+  if (scale) *scale = S;
+  return fmaf(kMxMargin, S, lam);
+}
+
+// The FP64 primitives of k_prim's FP64 path from rho (as 1/rho) and p.
+__device__ __forceinline__ void prim_fp64(const Dev& D, double irho, double p, double* ip, double* a, double* pme) {
+  *ip = 1.0 / p;
+  *a = sqrt(D.gamma * p * irho);
+  *pme = D.ie_root > 0 ? rootinv(p, D.ie_root) : pow(p, -D.e_exp);
+}
+
+// 1/p, a and p^{-e} of a state that k_prim does not see (a boundary state), as each path computes them.
+template <bool MX>
+__device__ __forceinline__ void prim_of(const Dev& D, double rho, double irho, double p, double* ip, double* a,
+                                        double* pme) {
+  if constexpr (MX) {
+    const PrimF f = prim_mx(D, rho, p);
+    *ip = to_f64(f.ip);
+    *a = to_f64(f.a);
+    *pme = to_f64(f.pme);
+  } else {
+    *ip = 1.0 / p;
+    *a = sqrt(D.gamma * p * irho);
+    *pme = pow(p, -D.e_exp);
+  }
+}
+
+// The wave-speed bound of either path from a pair of nodes' stored primitives (normal velocities u, FP64
+// p and 1/rho, and 1/p, a, p^{-e} as the path's k_prim wrote them).  The mixed path falls back to the FP64
+// formula when its FP32 bound is infinite or NaN (states near the ends of the FP32 range).
+template <bool MX>
+__device__ __forceinline__ double lambda_pair(const Dev& D, double uL, double pL, double irL, double ipL, double aL,
+                                              double pmeL, double uR, double pR, double irR, double ipR, double aR,
+                                              double pmeR) {
+  if constexpr (MX) {
+    const PrimF Lf{to_f32(ipL), to_f32(aL), to_f32(pmeL)}, Rf{to_f32(ipR), to_f32(aR), to_f32(pmeR)};
+    const float lam = lambda_max_mx(D, to_f32(uL), to_f32(pL), Lf, to_f32(uR), to_f32(pR), Rf);
+    if (finite_f32(lam)) return to_f64(lam);
+    prim_fp64(D, irL, pL, &ipL, &aL, &pmeL);
+    prim_fp64(D, irR, pR, &ipR, &aR, &pmeR);
+  }
+  return lambda_max(D, uL, pL, ipL, aL, pmeL, uR, pR, ipR, aR, pmeR);
 }
 
 // f(U) n for a unit vector n, given m.n = mn, v.n = un and p: [m.n, m un + p n, (E + p) un].

@@ -1,6 +1,8 @@
 // Sweep B: high-order update with the consistent element mass, relaxed local bounds, antidiffusive
 // fluxes and the first convex-limiting pass.  One thread per node; a block holds whole elements so the
 // element solve and the m_ij coupling of A_ij stay in shared memory.
+#include <type_traits>
+
 #include "gdg_internal.cuh"
 
 namespace gdg {
@@ -19,10 +21,10 @@ constexpr int kMaxLocal = 32;  // n_loc limit of gdg_setup
 // is slot / n_loc, the local index slot % n_loc); threads past npb keep t.  *pad is set to 1 when the
 // shared arrays should space elements n_loc + 1 apart: under the dealt-out map the lanes of a warp read
 // one node of each of several elements, and an even n_loc would put them in the same shared bank.
-__device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t, int* s_order, int* s_mixed,
+__device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t, int* s_order, int* s_uneven,
                                             int* pad) {
   const int nl = D.n_loc;
-  if (t == 0) *s_mixed = 0;
+  if (t == 0) *s_uneven = 0;
   __syncthreads();
   if (t < nl) {
     const long long first = (long long)lb * npb;  // the block's first element always exists
@@ -35,13 +37,13 @@ __device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t
     for (int o = 0; o < nl; ++o) {
       const int lo = len(o);
       rank += (lo > mine) || (lo == mine && o < t);
-      if (lo != mine) *s_mixed = 1;
+      if (lo != mine) *s_uneven = 1;
     }
     s_order[rank] = t;
   }
   __syncthreads();
-  *pad = *s_mixed && !(nl & 1);
-  if (!*s_mixed || t >= npb) return t;
+  *pad = *s_uneven && !(nl & 1);
+  if (!*s_uneven || t >= npb) return t;
   const int epb = npb / nl;
   return (t % epb) * nl + s_order[t / epb];
 }
@@ -59,15 +61,18 @@ __device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t
 //     pass-1 line search of Sec. 5.4, eq. (ConvexScheme), from U^L with P = A / (kappa_i m_i); the rare
 //     searches that need the bracketed iteration are queued for k_lsfix.
 // With order HIGH the kernel stops after 2 and writes U_out = alpha U_base + (1 - alpha)(U + dU^H).
-template <int DIM, class Src>
+// The mixed path (MX) runs steps 1, 2 and the A_ij of step 4 in FP32 (the differences U_j - U_i in FP64
+// first); the bounds and the line search stay FP64.
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_block) {
   constexpr int M = DIM + 2;
   constexpr int kShared = kMaxBlock + kMaxBlock / 2;  // room for one pad slot per element of 2+ nodes
-  __shared__ double sR[M][kShared];
-  __shared__ double sdU[M][kShared];
+  using R = std::conditional_t<MX, float, double>;    // arithmetic of steps 1, 2 and the A_ij of step 4
+  __shared__ R sR[M][kShared];
+  __shared__ R sdU[M][kShared];
   __shared__ Ctx sctx;
   __shared__ int s_order[kMaxLocal];
-  __shared__ int s_mixed;
+  __shared__ int s_uneven;
   int lb;
   const Ctx& c = src.get(&sctx, &lb);
   if (finished(c)) return;
@@ -76,33 +81,55 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
   const double* U = c.U;
   const double* bdata = c.bdata;
   int pad;
-  const int slot = element_slot(D, lb, nodes_per_block, threadIdx.x, s_order, &s_mixed, &pad);
+  const int slot = element_slot(D, lb, nodes_per_block, threadIdx.x, s_order, &s_uneven, &pad);
   const int i = lb * nodes_per_block + slot;
   const bool valid = slot < nodes_per_block && i < D.n;
   const int sh = slot + pad * (slot / D.n_loc);  // slot in the shared arrays
   const size_t n = D.n;
   const double tau = stage_tau(c);
-  double Ui[M], dUi[M];
+  const R tau_r = MX ? R(to_f32(tau)) : R(tau);
+  double Ui[M];
+  R dUi[M];
   double Ni = 0.0;
   if (valid) {
     load_state<DIM>(U, D.n, i, Ui);
     Ni = abs_bits(S.N[i]);
-    double rhs[M];
+    R rhs[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) rhs[q] = S.RHSL[(size_t)q * n + i];
+    for (int q = 0; q < M; ++q) {
+      if constexpr (MX)
+        rhs[q] = to_f32(S.RHSL[(size_t)q * n + i]);
+      else
+        rhs[q] = S.RHSL[(size_t)q * n + i];
+    }
     // min / max of non-negative values on the integer pipe
     const int e1 = D.sten_end[i];
     for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
-      const double dl = S.dL[e];
       const int j = D.col[e];
-      const double dev = dl * pmin(D.c_ev * pmax(Ni, abs_bits(S.N[j])), 1.0);
-      const double dd = pmax(D.mu[e] * dl, dev) - dl;
-      const double td = tau * dd;
+      if constexpr (MX) {
+        // d^H - d^L from FP32 operands: every factor is symmetric in (i, j), so the same bits come out
+        // of row j, and A_ji = -A_ij holds exactly
+        const float dl = to_f32(S.dL[e]);
+        const float dev = dl * fminf(D.c_ev_f * to_f32(pmax(Ni, abs_bits(S.N[j]))), 1.f);
+        const float dd = fmaxf(to_f32(D.mu[e]) * dl, dev) - dl;
+        const float td = tau_r * dd;
 #pragma unroll
-      for (int q = 0; q < M; ++q) {
-        const double du = U[(size_t)q * n + j] - Ui[q];
-        rhs[q] = fma(-dd, du, rhs[q]);
-        S.A[(size_t)q * D.nnz + e] = td * du;  // viscous part of A_ij, completed below
+        for (int q = 0; q < M; ++q) {
+          const float du = to_f32(U[(size_t)q * n + j] - Ui[q]);
+          rhs[q] = fmaf(-dd, du, rhs[q]);
+          S.A[(size_t)q * D.nnz + e] = to_f64(td * du);  // viscous part of A_ij, completed below
+        }
+      } else {
+        const double dl = S.dL[e];
+        const double dev = dl * pmin(D.c_ev * pmax(Ni, abs_bits(S.N[j])), 1.0);
+        const double dd = pmax(D.mu[e] * dl, dev) - dl;
+        const double td = tau * dd;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+          const double du = U[(size_t)q * n + j] - Ui[q];
+          rhs[q] = fma(-dd, du, rhs[q]);
+          S.A[(size_t)q * D.nnz + e] = td * du;  // viscous part of A_ij, completed below
+        }
       }
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
@@ -114,7 +141,10 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
       double dd = (pmax(D.muB[i], pmin(D.c_ev * Ni, 1.0)) - 1.0) * dl;
 #pragma unroll
       for (int q = 0; q < M; ++q) {
-        rhs[q] -= dd * (UB[q] - Ui[q]);
+        if constexpr (MX)
+          rhs[q] -= to_f32(dd * (UB[q] - Ui[q]));
+        else
+          rhs[q] -= dd * (UB[q] - Ui[q]);
         S.AB[(size_t)q * D.nb + b] = tau * dd * (UB[q] - Ui[q]);
       }
     }
@@ -127,23 +157,32 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
     const int il = i % nl;
     const int t0 = sh - il;  // first node of the element in the shared arrays
     const double* Minv = D.MKinv + ((size_t)(i / nl) * nl + il) * nl;
-    double acc[M];
+    R acc[M];
 #pragma unroll
-    for (int q = 0; q < M; ++q) acc[q] = 0.0;
+    for (int q = 0; q < M; ++q) acc[q] = R(0);
     for (int l = 0; l < nl; ++l) {
-      double w = Minv[l];
+      R w;
+      if constexpr (MX)
+        w = to_f32(Minv[l]);
+      else
+        w = Minv[l];
 #pragma unroll
       for (int q = 0; q < M; ++q) acc[q] += w * sR[q][t0 + l];
     }
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      dUi[q] = -tau * acc[q];
+      dUi[q] = -tau_r * acc[q];
       sdU[q][sh] = dUi[q];
     }
     if (D.order == GDG_ORDER_HIGH) {
 #pragma unroll
       for (int q = 0; q < M; ++q) {
-        c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, Ui[q] + dUi[q]);
+        double du;
+        if constexpr (MX)
+          du = to_f64(dUi[q]);
+        else
+          du = dUi[q];
+        c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, Ui[q] + du);
       }
     }
   }
@@ -193,14 +232,25 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
     double A[M];
     const bool stencil = e < se;
     const bool same = (j / nl) == elem;
-    const double mij = same ? D.mij[e] : 0.0;
     const int tj = t0 + (j % nl);
+    if constexpr (MX) {
+      const float mij = same ? to_f32(D.mij[e]) : 0.f;
 #pragma unroll
-    for (int q = 0; q < M; ++q) {
-      double a = stencil ? S.A[(size_t)q * D.nnz + e] : 0.0;
-      if (same) a = fma(-mij, sdU[q][tj] - dUi[q], a);
-      A[q] = a;
-      S.A[(size_t)q * D.nnz + e] = a;
+      for (int q = 0; q < M; ++q) {
+        float a = stencil ? to_f32(S.A[(size_t)q * D.nnz + e]) : 0.f;
+        if (same) a = fmaf(-mij, sdU[q][tj] - dUi[q], a);
+        A[q] = to_f64(a);
+        S.A[(size_t)q * D.nnz + e] = A[q];
+      }
+    } else {
+      const double mij = same ? D.mij[e] : 0.0;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        double a = stencil ? S.A[(size_t)q * D.nnz + e] : 0.0;
+        if (same) a = fma(-mij, sdU[q][tj] - dUi[q], a);
+        A[q] = a;
+        S.A[(size_t)q * D.nnz + e] = a;
+      }
     }
     double l, fb;
     if (line_search_head<DIM>(D, ls, A, ikm, ikmf, &l, &fb))
@@ -220,34 +270,36 @@ __global__ void __launch_bounds__(kMaxBlock, 3) k_high(Src src, int nodes_per_bl
   }
 }
 
-template <int DIM, class Src>
+template <int DIM, bool MX, class Src>
 cudaError_t high_launch(const Src& src, long long blocks, int npb, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (npb < 1 || npb > kMaxBlock) return cudaErrorInvalidValue;
-  k_high<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
+  k_high<DIM, MX, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
   return cudaGetLastError();
+}
+
+template <class Src>
+cudaError_t high_dispatch(int dim, bool mx, const Src& src, long long blocks, int npb, cudaStream_t s) {
+  switch (dim * 2 + (mx ? 1 : 0)) {
+    case 2: return high_launch<1, false, Src>(src, blocks, npb, s);
+    case 3: return high_launch<1, true, Src>(src, blocks, npb, s);
+    case 4: return high_launch<2, false, Src>(src, blocks, npb, s);
+    case 5: return high_launch<2, true, Src>(src, blocks, npb, s);
+    case 6: return high_launch<3, false, Src>(src, blocks, npb, s);
+    case 7: return high_launch<3, true, Src>(src, blocks, npb, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 // npb: nodes per block, whole elements (all instances of a batch share n_loc, hence the block shape).
 cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s) {
-  const One src{c};
-  switch (dim) {
-    case 1: return high_launch<1, One>(src, blocks, npb, s);
-    case 2: return high_launch<2, One>(src, blocks, npb, s);
-    case 3: return high_launch<3, One>(src, blocks, npb, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return high_dispatch(dim, c.D.mixed != 0, One{c}, blocks, npb, s);
 }
 
-cudaError_t launch_high_file_many(int dim, const Many& m, long long blocks, int npb, cudaStream_t s) {
-  switch (dim) {
-    case 1: return high_launch<1, Many>(m, blocks, npb, s);
-    case 2: return high_launch<2, Many>(m, blocks, npb, s);
-    case 3: return high_launch<3, Many>(m, blocks, npb, s);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, long long blocks, int npb, cudaStream_t s) {
+  return high_dispatch(dim, mixed, m, blocks, npb, s);
 }
 
 }  // namespace gdg

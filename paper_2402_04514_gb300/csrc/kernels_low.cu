@@ -1,6 +1,8 @@
 // Low-order sweep: per-node primitives, the time-step reduction (Sec. 3.3, eq. (MaxCFLdt)) and the
 // first stage sweep (low-order update, entropy-viscosity indicator, one-hop bound aggregates).
 // Every kernel takes its context from a source (One: a single instance, Many: a batch; gdg_internal.cuh).
+#include <type_traits>
+
 #include "gdg_internal.cuh"
 
 namespace gdg {
@@ -12,8 +14,9 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // Per-node primitives (Sec. 2.2): 1/rho, p, 1/p, a = sqrt(gamma p / rho), p^{-e}, the entropy function
 // f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
 // Flags a state outside the admissible set of eq. (AddSet).  Being the first kernel of every stage, it
-// also empties the stage's deferred line-search queues.
-template <int DIM, class Src>
+// also empties the stage's deferred line-search queues.  The mixed path (MX) keeps 1/rho and p in FP64
+// (the fluxes use them) and computes the rest in FP32.
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   __shared__ Ctx sctx;
   int lb;
@@ -29,17 +32,35 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   if (i >= D.n) return;
   double Ui[DIM + 2];
   load_state<DIM>(c.U, D.n, i, Ui);
-  double irho = 1.0 / Ui[0];
+  double irho = MX ? rcp64(Ui[0]) : 1.0 / Ui[0];
   double m2 = 0.0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) m2 += Ui[1 + k] * Ui[1 + k];
   double eps = Ui[DIM + 1] - 0.5 * m2 * irho;
   if (!(Ui[0] > 0.0) || !(eps > 0.0)) atomicOr(S.flags, (unsigned)GDG_FLAG_INADMISSIBLE);
   double p = D.gm1 * eps;
-  double ir;
-  double st = rho_neg_gamma(D, Ui[0], &ir) * eps;
   double* P = S.prim;
   size_t n = D.n;
+  if constexpr (MX) {
+    const PrimF f = prim_mx(D, Ui[0], p);
+    float st = powf(to_f32(Ui[0]), -D.gamma_f) * to_f32(eps);
+    double st64 = to_f64(st);
+    if (!finite_f32(st)) {  // rho^{-gamma} beyond the FP32 range
+      double ir;
+      st64 = rho_neg_gamma(D, Ui[0], &ir) * eps;
+      st = to_f32(st64);
+    }
+    P[PR_IRHO * n + i] = irho;
+    P[PR_P * n + i] = p;
+    P[PR_IP * n + i] = to_f64(f.ip);
+    P[PR_A * n + i] = to_f64(f.a);
+    P[PR_PME * n + i] = to_f64(f.pme);
+    P[PR_F * n + i] = to_f64(powf(2.f * D.gm1h_f * st, D.inv_gp1_f));
+    P[PR_ST * n + i] = st64;
+    return;
+  }
+  double ir;
+  double st = rho_neg_gamma(D, Ui[0], &ir) * eps;
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
   P[PR_IP * n + i] = 1.0 / p;
@@ -53,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
 
 // d_i^{d,k} = |c_i^{d,k}| lambda_max^+(U_i, U^{d,k}, n_i^k) of boundary entry b (Sec. 4.2,
 // eq. (eq:dij_low_order_modified); interior state on the left), from node i's primitives.
-template <int DIM>
+template <int DIM, bool MX>
 __device__ __forceinline__ double boundary_viscosity(const Dev& D, int b, const double* Ui, const double* bdata,
                                                      double irho_i, double p_i, double ip_i, double a_i,
                                                      double pme_i) {
@@ -70,8 +91,10 @@ __device__ __forceinline__ double boundary_viscosity(const Dev& D, int b, const 
     uL += Ui[1 + k] * nv[k];
     uR += UB[1 + k] * nv[k];
   }
-  return D.bnorm[b] * lambda_max(D, uL * irho_i, p_i, ip_i, a_i, pme_i, uR * irB, pB, 1.0 / pB,
-                                 sqrt(D.gamma * pB * irB), pow(pB, -D.e_exp));
+  double ipB, aB, pmeB;
+  prim_of<MX>(D, UB[0], irB, pB, &ipB, &aB, &pmeB);
+  return D.bnorm[b] *
+         lambda_pair<MX>(D, uL * irho_i, p_i, irho_i, ip_i, a_i, pme_i, uR * irB, pB, irB, ipB, aB, pmeB);
 }
 
 // Block minimum of val, then one 64-bit atomicMin per block on the bit pattern (positive doubles order
@@ -91,7 +114,7 @@ __device__ __forceinline__ void block_min_to(double val, unsigned long long* dst
 // Sum over the row of d_ij^L plus the boundary viscosities, i.e. -d_ii of
 // eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|), with d_ij^L evaluated here
 // (gdg_max_dt, before any stage).
-template <int DIM, class Src>
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
@@ -122,13 +145,14 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
         uL += Ui[1 + k] * nv[k];
         uR += U[(size_t)(1 + k) * n + j] * nv[k];
       }
+      const double irho_j = P[PR_IRHO * n + j];
       uL *= irho_i;
-      uR *= P[PR_IRHO * n + j];
-      dsum += cnm * lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], P[PR_IP * n + j], P[PR_A * n + j],
-                               P[PR_PME * n + j]);
+      uR *= irho_j;
+      dsum += cnm * lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], irho_j,
+                                    P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b)
-      dsum += boundary_viscosity<DIM>(D, b, Ui, c.bdata, irho_i, p_i, ip_i, a_i, pme_i);
+      dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, irho_i, p_i, ip_i, a_i, pme_i);
     if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
   }
   block_min_to(val, S.tau_bits);
@@ -136,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
 
 // The same bound inside the fused SSP-RK3 step, after the edge sweep of the step's first stage: the row
 // sums of the stored d_ij^L plus the boundary viscosities, reduced into the instance's clock.
-template <int DIM, class Src>
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
@@ -157,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
       double Ui[M];
       load_state<DIM>(c.U, D.n, i, Ui);
       for (int b = b0; b < b1; ++b)
-        dsum += boundary_viscosity<DIM>(D, b, Ui, c.bdata, P[PR_IRHO * n + i], P[PR_P * n + i], P[PR_IP * n + i],
+        dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, P[PR_IRHO * n + i], P[PR_P * n + i], P[PR_IP * n + i],
                                         P[PR_A * n + i], P[PR_PME * n + i]);
     }
     if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
@@ -172,7 +196,9 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
 //  - the bar state Ubar_ij = Ubar_ji (eq. (UsualBarState)), of which only rho and s~ are kept (for the
 //    local bounds of eq. (eq:local_bounds));
 //  - G_ij = f(U_j) c_ij and G_ji = f(U_i) c_ji = -|c_ij| f(U_i) n_ij for the row sums of sweep A.
-template <int DIM, class Src>
+// The mixed path (MX) takes lambda from lambda_pair<true> and the entropy power of the bar state in FP32;
+// the fluxes, G and the bar state itself stay FP64.
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
@@ -199,16 +225,17 @@ __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
     mnR += Uj[1 + q] * nv[q];
   }
   const double p_i = P[PR_P * n + i], p_j = P[PR_P * n + j];
-  const double uL = mnL * P[PR_IRHO * n + i], uR = mnR * P[PR_IRHO * n + j];
-  const double lam = lambda_max(D, uL, p_i, P[PR_IP * n + i], P[PR_A * n + i], P[PR_PME * n + i], uR, p_j,
-                                P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
+  const double ir_i = P[PR_IRHO * n + i], ir_j = P[PR_IRHO * n + j];
+  const double uL = mnL * ir_i, uR = mnR * ir_j;
+  const double lam = lambda_pair<MX>(D, uL, p_i, ir_i, P[PR_IP * n + i], P[PR_A * n + i], P[PR_PME * n + i], uR, p_j,
+                                     ir_j, P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
   const double d = cnm * lam;
   S.dL[e] = d;
   S.dL[t] = d;
   double fi[M], fj[M];
   flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
   flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
-  const double h = 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
+  const double h = MX ? to_f64(0.5f / to_f32(lam)) : 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
   double Ub[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
@@ -219,8 +246,23 @@ __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
   double mb2 = 0.0, irb;
 #pragma unroll
   for (int q = 0; q < DIM; ++q) mb2 += Ub[1 + q] * Ub[1 + q];
-  const double rgb = rho_neg_gamma(D, Ub[0], &irb);  // sets irb = 1 / rho(Ubar) before its use below
-  const double stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+  double stb;
+  if constexpr (MX) {
+    // eps(Ubar) in FP64 (E - |m|^2 / (2 rho) cancels at high Mach numbers) with 1/rho(Ubar) from one
+    // Newton step on the FP32 reciprocal; rho(Ubar)^{-gamma} in FP32
+    const float rbf = to_f32(Ub[0]);
+    const double y = to_f64(1.f / rbf);
+    irb = y * fma(-Ub[0], y, 2.0);
+    const float rg = powf(rbf, -D.gamma_f);
+    stb = to_f64(rg * to_f32(Ub[DIM + 1] - 0.5 * mb2 * irb));
+    if (!finite_f32(rg)) {
+      const double rgb = rho_neg_gamma(D, Ub[0], &irb);
+      stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+    }
+  } else {
+    const double rgb = rho_neg_gamma(D, Ub[0], &irb);  // sets irb = 1 / rho(Ubar) before its use below
+    stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+  }
   S.barR[e] = Ub[0];
   S.barR[t] = Ub[0];
   S.barS[e] = stb;
@@ -236,7 +278,9 @@ __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
 //    rho(Ubar_jk), rho_k and min of s~ over node j's stencil, with the bar states of
 //    eq. (UsualBarState); and rho, s~ of node i's boundary bar states (eq. (BoundaryBarState)).
 // With order LOW (or no limiter pass) it also writes U_out = alpha U_base + (1 - alpha) U^L.
-template <int DIM, class Src>
+// The mixed path (MX) computes the indicator in FP32 (its sums from FP64 flux differences) and the
+// boundary wave-speed bounds with lambda_pair<true>; the low-order update stays FP64.
+template <int DIM, bool MX, class Src>
 __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
@@ -255,10 +299,16 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   load_state<DIM>(U, D.n, i, Ui);
   const double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], ip_i = P[PR_IP * n + i],
                a_i = P[PR_A * n + i], pme_i = P[PR_PME * n + i], f_i = P[PR_F * n + i], st_i = P[PR_ST * n + i];
-  double rhs[M], Fsum[M];
+  using Acc = std::conditional_t<MX, float, double>;  // arithmetic of the indicator's sums
+  double rhs[M];
+  Acc Fsum[M];
 #pragma unroll
-  for (int q = 0; q < M; ++q) rhs[q] = Fsum[q] = 0.0;
-  double psum = 0.0, dsum = 0.0;
+  for (int q = 0; q < M; ++q) {
+    rhs[q] = 0.0;
+    Fsum[q] = Acc(0);
+  }
+  Acc psum = Acc(0);
+  double dsum = 0.0;
   double lo = Ui[0], hi = Ui[0], sl = st_i;
   const size_t nnz = D.nnz;
   const int e1 = D.sten_end[i];
@@ -272,9 +322,15 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
     for (int q = 0; q < M; ++q) {
       const double ge = S.G[q * nnz + e];
       rhs[q] += ge - d * (Uj[q] - Ui[q]);
-      Fsum[q] += ge + S.G[q * nnz + t];  // (f(U_j) - f(U_i)) c_ij
+      if constexpr (MX)
+        Fsum[q] += to_f32(ge + S.G[q * nnz + t]);
+      else
+        Fsum[q] += ge + S.G[q * nnz + t];  // (f(U_j) - f(U_i)) c_ij
     }
-    psum += S.G[e] * (P[PR_F * n + j] - f_i);  // (m_j . c_ij) (f_j - f_i)
+    if constexpr (MX)
+      psum += to_f32(S.G[e]) * (to_f32(P[PR_F * n + j]) - to_f32(f_i));
+    else
+      psum += S.G[e] * (P[PR_F * n + j] - f_i);  // (m_j . c_ij) (f_j - f_i)
     lo = pmin(lo, pmin(Uj[0], S.barR[e]));
     hi = pmax(hi, pmax(Uj[0], S.barR[e]));
     sl = pmin(sl, pmin(P[PR_ST * n + j], S.barS[e]));
@@ -296,8 +352,9 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
     uL *= irho_i;
     uR *= irB;
     double cnm = D.bnorm[b];
-    double d = cnm * lambda_max(D, uL, p_i, ip_i, a_i, pme_i, uR, pB, 1.0 / pB, sqrt(D.gamma * pB * irB),
-                                pow(pB, -D.e_exp));
+    double ipB, aB, pmeB;
+    prim_of<MX>(D, UB[0], irB, pB, &ipB, &aB, &pmeB);
+    double d = cnm * lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, pB, irB, ipB, aB, pmeB);
     S.dB[b] = d;
     dsum += d;
     double fi[M], fB[M];
@@ -308,7 +365,10 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
 #pragma unroll
     for (int q = 0; q < M; ++q) {
       rhs[q] += cnm * fB[q] - d * (UB[q] - Ui[q]);
-      Fsum[q] -= cnm * fi[q];
+      if constexpr (MX)
+        Fsum[q] -= to_f32(cnm * fi[q]);
+      else
+        Fsum[q] -= cnm * fi[q];
       Ub[q] = 0.5 * (Ui[q] + UB[q]) - t * (fB[q] - fi[q]);
     }
     S.bbar[b] = Ub[0];
@@ -336,63 +396,90 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   // equals sum_j f_k(U_j) c_ij by the partition of unity (Lemma LemPart) and vanishes exactly on a
   // stencil holding one state; grad Phi_i = rho_i f'(s_i) grad_U s(U_i), f' = f / (gamma + 1),
   // grad_U s = grad_U p / p - (gamma / rho) e_rho, grad_U p = (gamma - 1)[|v|^2 / 2, -v, 1]
-  double pref = f_i * D.inv_gp1 / irho_i;
-  double ip = 1.0 / p_i;
-  double v2 = 0.0;
+  if constexpr (MX) {
+    const float irf = to_f32(irho_i), ipf = to_f32(ip_i), gm1 = 2.f * D.gm1h_f;
+    const float pref = to_f32(f_i) * D.inv_gp1_f * to_f32(Ui[0]);
+    float v[DIM], v2 = 0.f;
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) v2 += (Ui[1 + k] * irho_i) * (Ui[1 + k] * irho_i);
-  double grad[M];
-  grad[0] = pref * (D.gm1 * 0.5 * v2 * ip - D.gamma * irho_i);
+    for (int k = 0; k < DIM; ++k) {
+      v[k] = to_f32(Ui[1 + k]) * irf;
+      v2 += v[k] * v[k];
+    }
+    float grad[M];
+    grad[0] = pref * (D.gm1h_f * v2 * ipf - D.gamma_f * irf);
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-D.gm1 * (Ui[1 + k] * irho_i) * ip);
-  grad[DIM + 1] = pref * (D.gm1 * ip);
-  double R = psum, Dn = fabs(psum);
+    for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-gm1 * v[k] * ipf);
+    grad[DIM + 1] = pref * (gm1 * ipf);
+    float R = psum, Dn = fabsf(psum);
 #pragma unroll
-  for (int q = 0; q < M; ++q) {
-    R -= grad[q] * Fsum[q];
-    Dn += fabs(grad[q]) * fabs(Fsum[q]);
+    for (int q = 0; q < M; ++q) {
+      R -= grad[q] * Fsum[q];
+      Dn += fabsf(grad[q]) * fabsf(Fsum[q]);
+    }
+    S.N[i] = Dn > 0.f ? to_f64(R / Dn) : 0.0;
+  } else {
+    double pref = f_i * D.inv_gp1 / irho_i;
+    double ip = 1.0 / p_i;
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) v2 += (Ui[1 + k] * irho_i) * (Ui[1 + k] * irho_i);
+    double grad[M];
+    grad[0] = pref * (D.gm1 * 0.5 * v2 * ip - D.gamma * irho_i);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-D.gm1 * (Ui[1 + k] * irho_i) * ip);
+    grad[DIM + 1] = pref * (D.gm1 * ip);
+    double R = psum, Dn = fabs(psum);
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      R -= grad[q] * Fsum[q];
+      Dn += fabs(grad[q]) * fabs(Fsum[q]);
+    }
+    S.N[i] = Dn > 0.0 ? R / Dn : 0.0;
   }
-  S.N[i] = Dn > 0.0 ? R / Dn : 0.0;
 }
 
-template <int DIM, class Src>
+template <int DIM, bool MX, class Src>
 cudaError_t low_launch(int kern, const Src& src, long long blocks, int threads, int arg, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
-    case KN_PRIM: k_prim<DIM, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_MAXDT: k_maxdt<DIM, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_TAU: k_tau<DIM, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_EDGE: k_edge<DIM, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_LOW: k_low<DIM, Src><<<g, threads, 0, s>>>(src, arg); break;
+    case KN_PRIM: k_prim<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_MAXDT: k_maxdt<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_TAU: k_tau<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_EDGE: k_edge<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_LOW: k_low<DIM, MX, Src><<<g, threads, 0, s>>>(src, arg); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-}  // namespace
-
-// Launchers of this file's kernels, dispatched on the dimension (called by launch_kernel*).
-cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
-                            cudaStream_t s) {
-  const One src{c};
-  switch (dim) {
-    case 1: return low_launch<1, One>(kern, src, blocks, threads, arg, s);
-    case 2: return low_launch<2, One>(kern, src, blocks, threads, arg, s);
-    case 3: return low_launch<3, One>(kern, src, blocks, threads, arg, s);
+template <class Src>
+cudaError_t low_dispatch(int kern, int dim, bool mx, const Src& src, long long blocks, int threads, int arg,
+                         cudaStream_t s) {
+  switch (dim * 2 + (mx ? 1 : 0)) {
+    case 2: return low_launch<1, false, Src>(kern, src, blocks, threads, arg, s);
+    case 3: return low_launch<1, true, Src>(kern, src, blocks, threads, arg, s);
+    case 4: return low_launch<2, false, Src>(kern, src, blocks, threads, arg, s);
+    case 5: return low_launch<2, true, Src>(kern, src, blocks, threads, arg, s);
+    case 6: return low_launch<3, false, Src>(kern, src, blocks, threads, arg, s);
+    case 7: return low_launch<3, true, Src>(kern, src, blocks, threads, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_low_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
+}  // namespace
+
+// Launchers of this file's kernels, dispatched on the dimension and the precision (called by
+// launch_kernel*).
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+                            cudaStream_t s) {
+  return low_dispatch(kern, dim, c.D.mixed != 0, One{c}, blocks, threads, arg, s);
+}
+
+cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads, int arg,
                                  cudaStream_t s) {
-  switch (dim) {
-    case 1: return low_launch<1, Many>(kern, m, blocks, threads, arg, s);
-    case 2: return low_launch<2, Many>(kern, m, blocks, threads, arg, s);
-    case 3: return low_launch<3, Many>(kern, m, blocks, threads, arg, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return low_dispatch(kern, dim, mixed, m, blocks, threads, arg, s);
 }
 
 }  // namespace gdg

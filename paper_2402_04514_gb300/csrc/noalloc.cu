@@ -213,14 +213,7 @@ extern "C" int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, con
   double* partial = nullptr;
   if (int rc = gdg::partial_buffer(&partial); rc != GDG_OK) return rc;
   gdg::Dev D{};
-  D.gamma = M.gamma;
-  D.gm1 = M.gamma - 1.0;
-  D.e_exp = (M.gamma - 1.0) / (2.0 * M.gamma);
-  D.inv_e = 1.0 / D.e_exp;
-  double r = std::round(D.inv_e);
-  D.ie = (std::fabs(D.inv_e - r) < 1e-12 * D.inv_e && r >= 1 && r <= 64) ? (int)r : 0;
-  D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
-  D.k13 = (M.gamma + 1.0) / (2.0 * M.gamma);
+  gdg::set_eos(D, M.gamma);
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = (int)((M.n + gdg::kThreads - 1) / gdg::kThreads);
   if (blocks > 0 && gdg::dispatch_partial(M.dim, D, M, U, bdata, partial, blocks, s) != cudaSuccess) return GDG_ECUDA;

@@ -32,6 +32,47 @@ extern "C" int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double*
 }
 
 // ------------------------------------------------------------------------------------------------
+// The mixed path's wave-speed bound against the FP64 path's (gdg_wave_speed_check): both from the
+// primitives their own k_prim computes, for one-dimensional states (rho, u, p) on each side.
+namespace gdg {
+namespace {
+
+__global__ void k_wave(Dev D, const double* __restrict__ st, double* __restrict__ out, long long n) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double* s = st + 6 * k;
+  const double rL = s[0], uL = s[1], pL = s[2], rR = s[3], uR = s[4], pR = s[5];
+  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  double ipL, aL, pmeL, ipR, aR, pmeR;
+  prim_fp64(D, irL, pL, &ipL, &aL, &pmeL);
+  prim_fp64(D, irR, pR, &ipR, &aR, &pmeR);
+  const double lam64 = lambda_max(D, uL, pL, ipL, aL, pmeL, uR, pR, ipR, aR, pmeR);
+  const PrimF Lf = prim_mx(D, rL, pL), Rf = prim_mx(D, rR, pR);
+  float raw = 0.f, scale = 0.f;
+  lambda_max_mx(D, to_f32(uL), to_f32(pL), Lf, to_f32(uR), to_f32(pR), Rf, &raw, &scale);
+  const double lmx = lambda_pair<true>(D, uL, pL, irL, to_f64(Lf.ip), to_f64(Lf.a), to_f64(Lf.pme), uR, pR, irR,
+                                       to_f64(Rf.ip), to_f64(Rf.a), to_f64(Rf.pme));
+  out[4 * k + 0] = lam64;
+  out[4 * k + 1] = lmx;
+  out[4 * k + 2] = to_f64(raw);
+  out[4 * k + 3] = to_f64(scale);
+}
+
+}  // namespace
+}  // namespace gdg
+
+extern "C" int gdg_wave_speed_check(double gamma, const double* states, double* out, int64_t n, void* stream) {
+  if (!(gamma > 1.0) || n < 0 || (n > 0 && (!states || !out))) return GDG_EINVAL;
+  if (n == 0) return GDG_OK;
+  gdg::Dev D{};
+  gdg::set_eos(D, gamma);
+  const int threads = 256;
+  const long long blocks = (n + threads - 1) / threads;
+  gdg::k_wave<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(D, states, out, n);
+  return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Throughput of the arithmetic the sweep is made of (gdg_fp64_throughput): every thread runs ILP
 // independent chains of one operation; the result is operations per second over the whole GPU.
 namespace gdg {

@@ -49,7 +49,7 @@ struct Request {
   bool done = false;
 };
 
-using Key = std::tuple<int, int, int, int>;  // dim, n_loc, order, passes: members of one batch share them
+using Key = std::tuple<int, int, int, int, int>;  // dim, n_loc, order, passes, precision: a batch's members share them
 
 struct Lane {
   std::vector<Request*> members;
@@ -243,7 +243,8 @@ void loop_main(gdg_server* s) {
       while (!s->ready.empty()) {
         Request* r = s->ready.front();
         s->ready.pop_front();
-        const Key key{r->prob.dim, r->prob.n_loc, r->prob.params.order, r->prob.params.limiter_passes};
+        const Key key{r->prob.dim, r->prob.n_loc, r->prob.params.order, r->prob.params.limiter_passes,
+                      r->prob.params.precision};
         Lane& L = lanes[key];
         L.members.push_back(r);
         L.dirty = true;

@@ -16,6 +16,7 @@ ORDER_LOW, ORDER_HIGH, ORDER_LIMITED = 0, 1, 2
 KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "tau", "clock", "axpy")  # GDG_K_*
 BC_SLIP, BC_DIRICHLET, BC_INOUTFLOW = 0, 1, 2
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
+PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 _CODES = {0: "GDG_OK", 1: "GDG_EINVAL", 2: "GDG_ENOMEM", 3: "GDG_ECUDA", 4: "GDG_ESETUP", 5: "GDG_EADMISSIBLE",
           6: "GDG_ECFL", 7: "GDG_ETIMEOUT", 8: "GDG_ENOTSUP"}
@@ -30,7 +31,7 @@ class GdgError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("order", C.c_int32), ("limiter_passes", C.c_int32), ("bounds_mode", C.c_int32),
                 ("c_k", C.c_double), ("p_k", C.c_double), ("c_ev", C.c_double), ("c_r", C.c_double),
-                ("p_r", C.c_double), ("ls_tol", C.c_double), ("ls_maxit", C.c_int32)]
+                ("p_r", C.c_double), ("ls_tol", C.c_double), ("ls_maxit", C.c_int32), ("precision", C.c_int32)]
 
 
 class _Problem(C.Structure):
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = False):
     L.gdg_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.gdg_profile.argtypes = [vp, i32]
     L.gdg_math_selftest.argtypes = [i32, i32, vp, vp, i64, vp]
+    L.gdg_wave_speed_check.argtypes = [d, vp, vp, i64, vp]
     L.gdg_fp64_throughput.argtypes = [i32, C.POINTER(d), vp]
     L.gdg_max_dt_noalloc.argtypes = [C.POINTER(DevMesh), vp, vp, d, vp, vp]
     L.gdg_profile_read.argtypes = [vp, vp, vp]
@@ -140,7 +142,7 @@ def load(build_if_missing: bool = False):
               "gdg_batch_set_schedule",
               "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
-              "gdg_max_dt_noalloc"):
+              "gdg_max_dt_noalloc", "gdg_wave_speed_check"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -175,6 +177,17 @@ def math_selftest(fn: int, q: int, x, stream=None):
     y = torch.empty_like(x)
     _check(load().gdg_math_selftest(fn, q, _ptr(x), _ptr(y), x.numel(), _stream(stream)), "gdg_math_selftest")
     return y
+
+
+def wave_speed_check(gamma: float, states, stream=None):
+    """gdg_wave_speed_check on the device tensor states [n, 6] (float64): returns [n, 4] with the FP64
+    bound, the mixed-precision bound, the same without its margin, and the margin's scale."""
+    import torch
+
+    out = torch.empty((states.shape[0], 4), dtype=torch.float64, device=states.device)
+    _check(load().gdg_wave_speed_check(gamma, _ptr(states), _ptr(out), states.shape[0], _stream(stream)),
+           "gdg_wave_speed_check")
+    return out
 
 
 def max_dt_noalloc(mesh: DevMesh, U, cfl: float, tau_out, bdata=None, stream=None) -> int:
