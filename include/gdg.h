@@ -221,6 +221,13 @@ int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t
  * Asynchronous on stream.  Errors: GDG_EINVAL (gamma <= 1, n < 0, NULL arrays with n > 0). */
 int gdg_wave_speed_check(double gamma, const double* states, double* out, int64_t n, void* stream);
 
+/* Check of the FP32 certificate that lets the line search of Sec. 5.4 skip an FP64 evaluation of the
+ * entropy constraint psi(s) = eps(U0 + s A) - s_min rho(U0 + s A)^gamma: for n rows
+ * in[k] = (U0[m], A[m], s_min, s) (device [n][2m + 2], m = dim + 2), out[k] = (1 if the certificate proves
+ * psi(s) >= 0 else 0, psi(s) in FP64) (device [n][2]).  A certified row must have psi(s) >= 0.
+ * Asynchronous on stream.  Errors: GDG_EINVAL (dim outside 1..3, gamma <= 1, n < 0, NULL arrays). */
+int gdg_certificate_check(int32_t dim, double gamma, const double* in, double* out, int64_t n, void* stream);
+
 /* Measured throughput (operations per second over the GPU, timed with CUDA events) of the arithmetic
  * the sweep is made of: op 0 = FP64 FMA, 1 = FP64 division, 2 = FP64 sqrt, 3 = FP64 pow, 4 = FP32 FMA,
  * 5 = this library's FP64 reciprocal, 6 = this library's x^{-1/5}, 7 = an FP64 -> FP32 -> FP64

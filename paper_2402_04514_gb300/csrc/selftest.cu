@@ -73,6 +73,51 @@ extern "C" int gdg_wave_speed_check(double gamma, const double* states, double* 
 }
 
 // ------------------------------------------------------------------------------------------------
+// The FP32 entropy certificate of the line search (gdg_certificate_check): for given U0, A, s_min and s,
+// whether ls_certified proves psi(s) >= 0, and psi(s) in FP64.
+namespace gdg {
+namespace {
+
+template <int DIM>
+__global__ void k_cert(Dev D, const double* __restrict__ in, double* __restrict__ out, long long n) {
+  constexpr int M = DIM + 2;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double* r = in + (2 * M + 2) * k;
+  double U0[M], A[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    U0[q] = r[q];
+    A[q] = r[M + q];
+  }
+  const double smin = r[2 * M], sv = r[2 * M + 1];
+  LsRow<DIM> c;
+  ls_row<DIM>(D, c, U0, 0.0, INFINITY, smin);
+  out[2 * k] = ls_certified<DIM>(D, c, A, d2f_fast(sv)) ? 1.0 : 0.0;
+  out[2 * k + 1] = ls_psi<DIM>(D, U0, A, sv, smin);
+}
+
+}  // namespace
+}  // namespace gdg
+
+extern "C" int gdg_certificate_check(int32_t dim, double gamma, const double* in, double* out, int64_t n,
+                                     void* stream) {
+  if (dim < 1 || dim > 3 || !(gamma > 1.0) || n < 0 || (n > 0 && (!in || !out))) return GDG_EINVAL;
+  if (n == 0) return GDG_OK;
+  gdg::Dev D{};
+  gdg::set_eos(D, gamma);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (dim) {
+    case 1: gdg::k_cert<1><<<blocks, threads, 0, s>>>(D, in, out, n); break;
+    case 2: gdg::k_cert<2><<<blocks, threads, 0, s>>>(D, in, out, n); break;
+    default: gdg::k_cert<3><<<blocks, threads, 0, s>>>(D, in, out, n); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Throughput of the arithmetic the sweep is made of (gdg_fp64_throughput): every thread runs ILP
 // independent chains of one operation; the result is operations per second over the whole GPU.
 namespace gdg {

@@ -128,6 +128,7 @@ def load(build_if_missing: bool = False):
     L.gdg_profile.argtypes = [vp, i32]
     L.gdg_math_selftest.argtypes = [i32, i32, vp, vp, i64, vp]
     L.gdg_wave_speed_check.argtypes = [d, vp, vp, i64, vp]
+    L.gdg_certificate_check.argtypes = [i32, d, vp, vp, i64, vp]
     L.gdg_fp64_throughput.argtypes = [i32, C.POINTER(d), vp]
     L.gdg_max_dt_noalloc.argtypes = [C.POINTER(DevMesh), vp, vp, d, vp, vp]
     L.gdg_profile_read.argtypes = [vp, vp, vp]
@@ -142,7 +143,7 @@ def load(build_if_missing: bool = False):
               "gdg_batch_set_schedule",
               "gdg_status", "gdg_debug_export",
               "gdg_get_info", "gdg_profile", "gdg_profile_read", "gdg_math_selftest", "gdg_fp64_throughput",
-              "gdg_max_dt_noalloc", "gdg_wave_speed_check"):
+              "gdg_max_dt_noalloc", "gdg_wave_speed_check", "gdg_certificate_check"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -187,6 +188,17 @@ def wave_speed_check(gamma: float, states, stream=None):
     out = torch.empty((states.shape[0], 4), dtype=torch.float64, device=states.device)
     _check(load().gdg_wave_speed_check(gamma, _ptr(states), _ptr(out), states.shape[0], _stream(stream)),
            "gdg_wave_speed_check")
+    return out
+
+
+def certificate_check(dim: int, gamma: float, rows, stream=None):
+    """gdg_certificate_check on the device tensor rows [n, 2m + 2] (float64): returns [n, 2] with 1/0
+    (certified) and psi(s) in FP64."""
+    import torch
+
+    out = torch.empty((rows.shape[0], 2), dtype=torch.float64, device=rows.device)
+    _check(load().gdg_certificate_check(dim, gamma, _ptr(rows), _ptr(out), rows.shape[0], _stream(stream)),
+           "gdg_certificate_check")
     return out
 
 
