@@ -356,6 +356,8 @@ def main():
     ap.add_argument("--fp64-rates", action="store_true", help="print the measured arithmetic rates and exit")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the sweep (mixed: GDG_PRECISION_MIXED, reported separately)")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the separately reported mixed-precision measurement of the fp64 run")
     args = ap.parse_args()
     if args.fp64_rates:
         import torch
@@ -395,99 +397,113 @@ def main():
     spec = WORKLOADS[args.workload]
     P, U0 = make_problem(spec)
     counts = costmodel.Counts.of(P)
-    mixed = args.precision == "mixed"
-    solver = Solver(P, params=dict(precision=1 if mixed else 0))
-    solver.set_clock(0.0, float("inf"), 0.5)
-    stream = torch.cuda.current_stream()
-    U = torch.from_numpy(U0).cuda()
-    work = (torch.empty_like(U), torch.empty_like(U))
     n = P.n
-
-    def step():
-        solver.step(U, work)  # gdg_ssprk3_step: tau chosen on the device, U updated in place
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
-    schedule = solver.schedule() if args.no_autotune else solver.autotune(U, work, trials=1)  # state restored
-
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    barrier()
-    torch.cuda.synchronize()
-    if sampler:
-        sampler.start()
-        time.sleep(0.3)
-    solver.profile(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    prof = solver.profile_read()
-    solver.profile(False)
-    flags = solver.status()
-    ms_max = max_over_ranks(ms, dist, "cuda")
-    value = whole_job_rate(world, n * 3 * args.steps, ms_max)
-    launches = sum(c for _, c in prof.values())
-
-    # roofline of the dominant kernel (its own launches' CUDA-event times inside the timed region)
-    top = max(prof, key=lambda k: prof[k][0])
-    top_ms, top_cnt = prof[top]
-    avg_s = top_ms / top_cnt / 1e3
-    fl = costmodel.flops_per_launch(counts)[top]
-    by = costmodel.bytes_per_launch(counts)[top]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # DRAM bytes per launch of the top kernel from the committed ncu table, scaled to this mesh by its node
-    # count; None when the table was taken from other library sources than the ones built here
-    traffic = costmodel.measured_traffic(os.path.join(ROOT, "profiles", "dram_traffic_q2_512_four_quadrant.txt"),
-                                         top, n)
-    roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": fl / avg_s / 1e12,
-                "peak": costmodel.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "alg_flops_per_launch": fl}
-    roofline_hbm = {"bound": "hbm", "kernel": f"k_{top}", "achieved": by / avg_s / 1e9, "peak": hbm_peak,
-                    "unit": "GB/s", "frac": by / avg_s / 1e9 / hbm_peak, "alg_bytes_per_launch": by,
-                    "traffic": traffic,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
-               for k, v in prof.items() if v[1]}
-    if mixed:  # the FP64 pipe no longer bounds the mixed path's sweep: report it against HBM
-        roofline, roofline_hbm = roofline_hbm, roofline
 
-    # end to end through the public API with host buffers: H2D of the step's input from pinned memory,
-    # the step, D2H of its result, every step
-    e2e = None
-    if not args.no_e2e:
-        hin = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
-        hin.copy_(U)
-        hout = torch.empty_like(hin, pin_memory=True)
-        torch.cuda.synchronize()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            U.copy_(hin, non_blocking=True)
+    def measure(mixed, with_e2e):
+        """Times args.steps fused SSP-RK3 steps of one instance (after warm-up and autotuning) and, with
+        with_e2e, the same through host buffers; returns the pieces of the JSON line."""
+        solver = Solver(P, params=dict(precision=1 if mixed else 0))
+        solver.set_clock(0.0, float("inf"), 0.5)
+        stream = torch.cuda.current_stream()
+        U = torch.from_numpy(U0).cuda()
+        work = (torch.empty_like(U), torch.empty_like(U))
+
+        def step():
+            solver.step(U, work)  # gdg_ssprk3_step: tau chosen on the device, U updated in place
+
+        for _ in range(args.warmup):
             step()
-            hout.copy_(U, non_blocking=True)
-            stream.synchronize()
-            hin, hout = hout, hin
-        e1.record(stream)
+        torch.cuda.synchronize()
+        assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
+        schedule = solver.schedule() if args.no_autotune else solver.autotune(U, work, trials=1)  # state restored
+
+        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        solver.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-        e2e = {"value": whole_job_rate(world, n * 3 * args.steps, ems), "unit": METRIC,
-               "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(U.numel() * 8)}
+        clocks = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1)
+        prof = solver.profile_read()
+        solver.profile(False)
+        flags = solver.status()
+        ms_max = max_over_ranks(ms, dist, "cuda")
+        value = whole_job_rate(world, n * 3 * args.steps, ms_max)
+        launches = sum(c for _, c in prof.values())
+
+        # roofline of the dominant kernel (its own launches' CUDA-event times inside the timed region)
+        top = max(prof, key=lambda k: prof[k][0])
+        top_ms, top_cnt = prof[top]
+        avg_s = top_ms / top_cnt / 1e3
+        fl = costmodel.flops_per_launch(counts)[top]
+        by = costmodel.bytes_per_launch(counts)[top]
+        # DRAM bytes per launch of the top kernel from the committed ncu table, scaled to this mesh by its
+        # node count; None when the table was taken from other library sources than the ones built here
+        traffic = costmodel.measured_traffic(
+            os.path.join(ROOT, "profiles", "dram_traffic_q2_512_four_quadrant.txt"), top, n,
+            "mixed" if mixed else "fp64")
+        alu = {"bound": "alu", "kernel": f"k_{top}", "achieved": fl / avg_s / 1e12,
+               "peak": costmodel.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": traffic,
+               "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+               "alg_flops_per_launch": fl}
+        hbm = {"bound": "hbm", "kernel": f"k_{top}", "achieved": by / avg_s / 1e9, "peak": hbm_peak,
+               "unit": "GB/s", "frac": by / avg_s / 1e9 / hbm_peak, "alg_bytes_per_launch": by,
+               "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        kernels = {k: {"ms_total": v[0], "launches": v[1],
+                       "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+                   for k, v in prof.items() if v[1]}
+
+        # end to end through the public API with host buffers: H2D of the step's input from pinned memory,
+        # the step, D2H of its result, every step
+        e2e = None
+        if with_e2e:
+            hin = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+            hin.copy_(U)
+            hout = torch.empty_like(hin, pin_memory=True)
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                U.copy_(hin, non_blocking=True)
+                step()
+                hout.copy_(U, non_blocking=True)
+                stream.synchronize()
+                hin, hout = hout, hin
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            ems = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+            e2e = {"value": whole_job_rate(world, n * 3 * args.steps, ems), "unit": METRIC,
+                   "h2d_bytes_per_step": int(U.numel() * 8), "d2h_bytes_per_step": int(U.numel() * 8)}
+        solver.close()
+        # the mixed path is not bound by the FP64 pipe: its roofline is the HBM one
+        roofline, other = (hbm, alu) if mixed else (alu, hbm)
+        return {"value": value, "ms_per_step": ms_max / args.steps, "schedule": schedule, "roofline": roofline,
+                "other": other, "kernels": kernels, "e2e": e2e, "launches": launches, "clocks": clocks,
+                "flags": flags}
+
+    main_mixed = args.precision == "mixed"
+    res = measure(main_mixed, not args.no_e2e)
+    mixed_res = None
+    if not main_mixed and not args.no_mixed:
+        mixed_res = measure(True, False)
 
     if rank != 0:
         if dist is not None:
@@ -499,14 +515,22 @@ def main():
         cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.cpu_baseline_steps} "
                          f"SSP-RK3 steps, single thread, {secs:.1f} s"}
-    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed" if mixed else "f64",
+    line = {"metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed" if main_mixed else "f64",
             "data": "synthetic",
-            "config": {**config_block(args, n), "precision": args.precision, "schedule": schedule},
-            "roofline": roofline, "roofline_hbm" if not mixed else "roofline_alu": roofline_hbm,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
-            "kernels": kernels, "status_flags": flags}
+            "config": {**config_block(args, n), "precision": args.precision, "schedule": res["schedule"]},
+            "roofline": res["roofline"], "roofline_hbm" if not main_mixed else "roofline_alu": res["other"],
+            "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["launches"] * world,
+            "clocks": res["clocks"], "kernels": res["kernels"], "status_flags": res["flags"]}
+    if mixed_res is not None:
+        # the mixed-precision path (GDG_PRECISION_MIXED) on the same workload, reported on its own: its
+        # results differ from the FP64 path's by up to ~1e-5 of max |U| per stage
+        line["mixed_precision"] = {
+            "value": mixed_res["value"], "unit": METRIC, "ms_per_step": mixed_res["ms_per_step"],
+            "dtype": "f32/f64 mixed", "schedule": mixed_res["schedule"], "roofline": mixed_res["roofline"],
+            "kernels": mixed_res["kernels"], "gpu_launches": mixed_res["launches"] * world,
+            "clocks": mixed_res["clocks"], "status_flags": mixed_res["flags"]}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

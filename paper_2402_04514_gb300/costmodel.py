@@ -107,16 +107,22 @@ def library_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(path: str, kernel: str, n_nodes: int):
+def measured_traffic(path: str, kernel: str, n_nodes: int, precision: str = "fp64"):
     """DRAM bytes (read + write) per launch of `kernel` from an ncu summary table (lines
-    `kernel nodes dram_read_bytes dram_write_bytes source_digest`), scaled from the captured mesh to
-    `n_nodes` (every array a sweep kernel touches grows in proportion to the node count).  None when the
-    table is missing, has no row for the kernel, or was taken from other sources."""
+    `kernel nodes dram_read_bytes dram_write_bytes source_digest [precision]`, precision fp64 when absent),
+    scaled from the captured mesh to `n_nodes` (every array a sweep kernel touches grows in proportion to
+    the node count).  None when the table is missing, has no row for the kernel and precision, or was
+    taken from other sources."""
     try:
         with open(path) as fh:
             lines = [ln.split() for ln in fh if ln.strip() and not ln.lstrip().startswith("#")]
     except OSError:
         return None
+    digest = library_source_digest()
+    for f in lines:
+        if len(f) in (5, 6) and f[0] == kernel and f[4] == digest and (f[5] if len(f) == 6 else "fp64") == precision:
+            return (float(f[2]) + float(f[3])) * n_nodes / float(f[1])
+    return None
     digest = library_source_digest()
     for f in lines:
         if len(f) == 5 and f[0] == kernel and f[4] == digest:
