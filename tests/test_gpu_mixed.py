@@ -225,3 +225,71 @@ def test_batch_of_mixed_members_equals_alone(torch_cuda):
     Ua = _dev(torch, U)
     with pytest.raises(GdgError):
         Batch([solvers[0], S64], [states[0], Ua], [works[0], (torch.empty_like(Ua), torch.empty_like(Ua))])
+
+
+def test_open_and_dirichlet_boundaries(torch_cuda):
+    """In/outflow (a supersonic stream with subsonic sides) and exact Dirichlet data (the Q3 vortex at
+    gamma = 5/3): one limited stage of the mixed path against the oracle."""
+    torch = torch_cuda
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Solver
+
+    sides = dict(left="inoutflow", right="inoutflow", bottom="inoutflow", top="inoutflow")
+    P = assembly.assemble_2d(16, 16, 1, bc=sides)
+    x, y = P.x
+    rho = 1.0 + 0.5 * np.exp(-40 * ((x - 0.4) ** 2 + (y - 0.5) ** 2))
+    U = workloads.prim_to_cons(rho, np.stack([np.full(P.n, 3.0), np.full(P.n, 0.5)]), np.full(P.n, 1.0), 1.4)
+    bd = workloads.prim_to_cons(np.full(P.nb, 1.0), np.stack([np.full(P.nb, 3.0), np.full(P.nb, 0.5)]),
+                                np.full(P.nb, 1.0), 1.4)
+    Pv, Uv, bdv = dirichlet_vortex_problem(6, 3)
+    for P, U, bd, g in ((P, U, bd, 1.4), (Pv, Uv, bdv(0.0), 5.0 / 3.0)):
+        S, O = Solver(P, gamma=g, params=MIXED), Oracle(P, gamma=g)
+        tau = O.max_dt(U, 0.5, bdata=bd)
+        out = S.stage(_dev(torch, U), tau, bdata=_dev(torch, bd))
+        ref, flags = O.stage(U, tau, bdata=bd)
+        e = rel_err(out.cpu().numpy(), ref)
+        print(f"boundaries: stage rel err {e:.3e}")
+        assert e <= MIXED_STAGE_TOL and S.status() == flags == 0
+
+
+def test_ssprk54_step(torch_cuda):
+    """One fused SSPRK(5,4) step of the mixed path against the oracle's step with the dt the device chose
+    (five stages, so five times the stage tolerance)."""
+    torch = torch_cuda
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Solver
+
+    P, U = four_quadrant_problem(13, 2, seed=0)
+    S, O = Solver(P, params=MIXED), Oracle(P)
+    S.set_clock(0.0, float("inf"), 0.5)
+    Ud = _dev(torch, U)
+    work = (torch.empty_like(Ud), torch.empty_like(Ud), torch.empty_like(Ud))
+    S.step(Ud, work)
+    _, dt, steps = S.clock()
+    ref, flags = O.ssprk54_step(U, dt)
+    e = rel_err(Ud.cpu().numpy(), ref)
+    print(f"ssprk54: step rel err {e:.3e}")
+    assert steps == 1 and flags == 0 and S.status() == 0 and e <= 5 * MIXED_STAGE_TOL
+
+
+def test_served_mixed_request_equals_alone(torch_cuda):
+    """Requests of both precisions through the serving loop: each result equals, bit for bit, the same
+    request solved alone with its own precision (the two precisions never share a batch)."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import Server, Solver
+
+    reqs = [(four_quadrant_problem(9, 2, seed=s), prec, 0.01) for s, prec in ((1, 1), (2, 0), (3, 1))]
+    srv = Server()
+    ids = [srv.submit(P, U, t_end, params=dict(precision=prec)) for (P, U), prec, t_end in reqs]
+    got = [srv.wait(r, timeout=300.0) for r in ids]
+    srv.close()
+    for ((P, U), prec, t_end), (res, info) in zip(reqs, got):
+        S = Solver(P, params=dict(precision=prec))
+        S.set_clock(0.0, t_end, 0.5)
+        Ud = _dev(torch, U)
+        work = (torch.empty_like(Ud), torch.empty_like(Ud))
+        for _ in range(100000):
+            S.step(Ud, work)
+            if S.clock()[0] >= t_end:
+                break
+        assert info["status"] == 0 and np.array_equal(res, Ud.cpu().numpy())
