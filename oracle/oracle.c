@@ -15,6 +15,7 @@
 #include <string.h>
 
 #define MAXM 5
+#define MAXNL 32 /* nodes per element (Q2 in 3D has 27); the Python wrapper rejects more */
 
 static double dot(const double* a, const double* b, int d) {
   double s = 0.0;
@@ -320,7 +321,7 @@ static long transpose_entry(const orc_problem* P, long i, long j) {
  * pivoting.  For discontinuous elements the consistent mass of Sec. 5, eq. (HighScheme), is block
  * diagonal, so the high-order update is one such solve per element. */
 static void element_solve(const double* MK, int nl, int m, double* B /* [nl][m]: in B, out X */) {
-  double A[16 * 16];
+  double A[MAXNL * MAXNL];
   memcpy(A, MK, sizeof(double) * nl * nl);
   for (int c = 0; c < nl; ++c) {
     int piv = c;
@@ -514,7 +515,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
       }
       for (int q = 0; q < m; ++q) rhs[q * n + i] = acc[q];
     }
-    double Bblk[16 * MAXM];
+    double Bblk[MAXNL * MAXM];
     for (long K = 0; K < n / nl; ++K) {
       for (int a = 0; a < nl; ++a)
         for (int q = 0; q < m; ++q) Bblk[a * m + q] = -tau * rhs[q * n + K * nl + a];

@@ -101,6 +101,8 @@ class Oracle:
 
     def __post_init__(self):
         P = self.problem
+        if not (1 <= P.dim <= 3 and 1 <= P.n_loc <= 32):
+            raise ValueError("the oracle takes dim 1..3 and at most 32 nodes per element")
         self.params = {**default_params(P.degree), **(self.params or {})}
         self._keep = dict(
             row_ptr=np.ascontiguousarray(P.row_ptr, np.int64),

@@ -13,7 +13,9 @@ hold exactly, and face coupling only links collocated nodes.  The consistent mas
 exactly (Gauss-Legendre with k+1 points per direction).
 
 Node numbering is element-contiguous: element e owns nodes [e*n_loc, (e+1)*n_loc); in 2D the local
-node (a, b) (a along x, b along y) has local index b*(k+1) + a and elements are numbered ey*nx + ex.
+node (a, b) (a along x, b along y) has local index b*(k+1) + a and elements are numbered ey*nx + ex; in 3D
+the local node (a, b, c) has local index (c*(k+1) + b)*(k+1) + a and elements are numbered
+(ez*ny + ey)*nx + ex.
 Each CSR row i lists every other node of its element (m_ij != 0 couples them all) and its collocated
 face partners; entries whose c_ij is zero (the in-element nodes that share neither the x-line nor the
 y-line of i) are kept because the consistent mass couples them in the high-order update (Eq. (5.1)).
@@ -31,7 +33,7 @@ INOUTFLOW = 2
 BC_CODES = {"slip": SLIP, "dirichlet": DIRICHLET, "inoutflow": INOUTFLOW}
 
 # Boundary part ids (one per side; corners carry one entry per side, Sec. 4.2).
-PART_LEFT, PART_RIGHT, PART_BOTTOM, PART_TOP = 0, 1, 2, 3
+PART_LEFT, PART_RIGHT, PART_BOTTOM, PART_TOP, PART_FRONT, PART_BACK = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
@@ -329,3 +331,121 @@ def assemble_2d(nx: int, ny: int, degree: int, box=(0.0, 1.0, 0.0, 1.0),
                    b_node=b_node, b_c=np.stack([b_cx, b_cy]),
                    b_type=types[b_part] if len(b_part) else np.zeros(0, np.int32), b_part=b_part,
                    omega_measure=float((x1 - x0) * (y1 - y0)), x=x, b_x=x[:, b_node])
+
+
+def assemble_3d(nx: int, ny: int, nz: int, degree: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0),
+                periodic=(False, False, False), bc=None) -> Problem:
+    """Q^k dG on an nx x ny x nz uniform hexahedral mesh of box = (x0, x1, y0, y1, z0, z1), the
+    three-dimensional counterpart of assemble_2d.
+
+    bc maps 'left'/'right' (x), 'bottom'/'top' (y) and 'front'/'back' (z) to 'slip', 'dirichlet' or
+    'inoutflow' (sides that are not periodic)."""
+    k = degree
+    p1 = k + 1
+    nl = p1 ** 3
+    x0, x1, y0, y1, z0, z1 = box
+    h = np.array([(x1 - x0) / nx, (y1 - y0) / ny, (z1 - z0) / nz])
+    ns = (nx, ny, nz)
+    bc = {**dict(left="slip", right="slip", bottom="slip", top="slip", front="slip", back="slip"), **(bc or {})}
+    xi, wi = gauss_lobatto(k)
+    Q = sbp_matrix(xi, wi)
+    Mr = ref_mass(xi)
+    E = nx * ny * nz
+    n = E * nl
+    e = np.arange(E, dtype=np.int64)
+    eidx = (e % nx, (e // nx) % ny, e // (nx * ny))
+    maxr = nl - 1 + 3
+    col = np.zeros((E, nl, maxr), np.int64)
+    cc = np.zeros((3, E, nl, maxr))
+    co = np.zeros((E, nl, maxr), np.uint8)
+    valid = np.zeros((E, nl, maxr), bool)
+    bnodes, bcs, bparts = [], [], []
+
+    def loc(a, b, c):
+        return (c * p1 + b) * p1 + a
+
+    parts = ((PART_LEFT, PART_RIGHT), (PART_BOTTOM, PART_TOP), (PART_FRONT, PART_BACK))
+    for c in range(p1):
+        for b in range(p1):
+            for a in range(p1):
+                ijk = (a, b, c)
+                l = loc(a, b, c)
+                s = 0
+                for ax in range(3):  # the line of l along axis ax: c = Q[ijk_ax, t] times the other weights
+                    o1, o2 = [d for d in range(3) if d != ax]
+                    wt = wi[ijk[o1]] * wi[ijk[o2]] * h[o1] * h[o2]
+                    for t in range(p1):
+                        if t == ijk[ax]:
+                            continue
+                        q = list(ijk)
+                        q[ax] = t
+                        col[:, l, s] = e * nl + loc(*q)
+                        cc[ax, :, l, s] = wt * Q[ijk[ax], t]
+                        valid[:, l, s] = True
+                        s += 1
+                for ax in range(3):  # face partners (collocated); sides of the domain become boundary entries
+                    if ijk[ax] not in (0, k):
+                        continue
+                    lo = ijk[ax] == 0
+                    o1, o2 = [d for d in range(3) if d != ax]
+                    val = 0.5 * wi[ijk[o1]] * wi[ijk[o2]] * h[o1] * h[o2] * (-1.0 if lo else 1.0)
+                    nidx = [eidx[0].copy(), eidx[1].copy(), eidx[2].copy()]
+                    nidx[ax] = nidx[ax] - 1 if lo else nidx[ax] + 1
+                    if periodic[ax]:
+                        nidx[ax] = nidx[ax] % ns[ax]
+                    inside = (nidx[ax] >= 0) & (nidx[ax] < ns[ax])
+                    ne = (nidx[2] * ny + nidx[1]) * nx + nidx[0]
+                    q = list(ijk)
+                    q[ax] = k if lo else 0
+                    col[inside, l, s] = ne[inside] * nl + loc(*q)
+                    cc[ax, inside, l, s] = val
+                    co[inside, l, s] = 1
+                    valid[inside, l, s] = True
+                    s += 1
+                    bnd = ~inside
+                    if bnd.any():
+                        cnt = int(bnd.sum())
+                        bnodes.append(e[bnd] * nl + l)
+                        bv = np.zeros((3, cnt))
+                        bv[ax] = val
+                        bcs.append(bv)
+                        bparts.append(np.full(cnt, parts[ax][0 if lo else 1]))
+                for cz in range(p1):  # mass-only entries (c_ij = 0): on none of the three lines of l
+                    for by in range(p1):
+                        for ax_ in range(p1):
+                            if sum((ax_ != a, by != b, cz != c)) >= 2:
+                                col[:, l, s] = e * nl + loc(ax_, by, cz)
+                                valid[:, l, s] = True
+                                s += 1
+    counts = valid.reshape(n, maxr).sum(1)
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col_c, cx_c, cy_c, cz_c, co_c = _compress(valid, col, cc[0], cc[1], cc[2], co)
+    wloc = np.einsum("c,b,a->cba", wi, wi, wi).reshape(-1)  # index (c*p1 + b)*p1 + a
+    vol = h.prod()
+    mi = np.tile(wloc * vol, E)
+    MK = np.broadcast_to(np.kron(np.kron(Mr, Mr), Mr) * vol, (E, nl, nl)).copy()
+    if bnodes:
+        b_node = np.concatenate(bnodes).astype(np.int32)
+        b_c = np.concatenate(bcs, axis=1)
+        b_part = np.concatenate(bparts).astype(np.int32)
+        order = np.lexsort((b_part, b_node))
+        b_node, b_c, b_part = b_node[order], b_c[:, order], b_part[order]
+    else:
+        b_node = np.zeros(0, np.int32)
+        b_c = np.zeros((3, 0))
+        b_part = np.zeros(0, np.int32)
+    types = np.array([BC_CODES[bc[sd]] for sd in ("left", "right", "bottom", "top", "front", "back")], np.int32)
+    la = np.tile(np.arange(p1), p1 * p1)
+    lb = np.tile(np.repeat(np.arange(p1), p1), p1)
+    lc = np.repeat(np.arange(p1), p1 * p1)
+    X = (x0 + (eidx[0][:, None] + xi[la][None, :]) * h[0]).reshape(-1)
+    Y = (y0 + (eidx[1][:, None] + xi[lb][None, :]) * h[1]).reshape(-1)
+    Z = (z0 + (eidx[2][:, None] + xi[lc][None, :]) * h[2]).reshape(-1)
+    x = np.stack([X, Y, Z])
+    return Problem(dim=3, degree=k, n=n, n_loc=nl, row_ptr=row_ptr, col_idx=col_c.astype(np.int32),
+                   cij=np.stack([cx_c, cy_c, cz_c]), coloc=co_c.astype(np.uint8), mi=mi, MK=MK,
+                   b_node=b_node, b_c=b_c, b_type=types[b_part] if len(b_part) else np.zeros(0, np.int32),
+                   b_part=b_part, omega_measure=float((x1 - x0) * (y1 - y0) * (z1 - z0)), x=x,
+                   b_x=x[:, b_node])
+

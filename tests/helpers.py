@@ -27,6 +27,18 @@ def four_quadrant_problem(ne, degree, seed=0, gamma=1.4):
     return P, U
 
 
+def octant_problem(shape, degree, seed=0, gamma=1.4, bc=None):
+    """A 3D Riemann problem on [0,1]^3: eight octants split at 0.5 with states drawn from default_rng(seed)
+    (rho, p ~ U[0.1, 2], velocity components ~ U[-1, 1])."""
+    P = assembly.assemble_3d(*shape, degree, bc=bc)
+    rng = np.random.default_rng(seed)
+    x, y, z = P.x
+    o = (x > 0.5).astype(int) + 2 * (y > 0.5) + 4 * (z > 0.5)
+    rho, p = rng.uniform(0.1, 2.0, 8)[o], rng.uniform(0.1, 2.0, 8)[o]
+    U = workloads.prim_to_cons(rho, rng.uniform(-1.0, 1.0, (3, 8))[:, o], p, gamma)
+    return P, U
+
+
 def periodic_vortex_problem(ne, degree, gamma=1.4):
     P = assembly.assemble_2d(ne, ne, degree, box=(-5.0, 5.0, -5.0, 5.0), periodic=(True, True))
     U = workloads.vortex(P.x[0], P.x[1], 0.0, gamma=gamma)

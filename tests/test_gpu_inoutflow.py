@@ -1,6 +1,7 @@
 """In- and outflow boundaries (Sec. 4.1) on the GPU against the oracle: stages of the first-order and
 limited schemes, and fused steps, on a shock tube whose shock leaves the domain, a four-quadrant problem
-with open sides, and a supersonic stream (supersonic inflow, supersonic outflow and subsonic sides)."""
+with open sides, a supersonic stream (supersonic inflow, supersonic outflow and subsonic sides) and a 3D
+octant problem with three open sides."""
 import numpy as np
 import pytest
 
@@ -30,6 +31,10 @@ def _case(name):
         P = assembly.assemble_1d(200, 1, bc=("inoutflow", "inoutflow"))
         U = workloads.sod(P.x[0])
         return P, U, np.ascontiguousarray(workloads.sod(P.b_x[0]))
+    if name == "oct_q1_3d_open":
+        from tests.helpers import octant_problem
+        P, U = octant_problem((5, 4, 4), 1, seed=3, bc=dict(left="inoutflow", right="inoutflow", back="inoutflow"))
+        return P, U, np.ascontiguousarray(U[:, P.b_node])
     if name == "fq_q2_open_sides":
         P = assembly.assemble_2d(13, 13, 2, bc=dict(left="inoutflow", right="inoutflow"))
         U = workloads.four_quadrant(P.x[0], P.x[1], seed=0)
@@ -45,7 +50,7 @@ def _case(name):
     return P, U, np.ascontiguousarray(bd)
 
 
-NAMES = ["sod1d_open", "fq_q2_open_sides", "supersonic_stream"]
+NAMES = ["sod1d_open", "fq_q2_open_sides", "supersonic_stream", "oct_q1_3d_open"]
 
 
 @pytest.mark.parametrize("name", NAMES)

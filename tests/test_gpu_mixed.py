@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from paper_2402_04514_gb300 import assembly, workloads
-from tests.helpers import consolidated_l1, dirichlet_vortex_problem, four_quadrant_problem, periodic_vortex_problem, rel_err
+from tests.helpers import (consolidated_l1, dirichlet_vortex_problem, four_quadrant_problem, octant_problem,
+                           periodic_vortex_problem, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -87,6 +88,7 @@ CASES = [
     ("fq_q2_slip", lambda: four_quadrant_problem(13, 2, seed=0)),
     ("fq_q1_slip", lambda: four_quadrant_problem(19, 1, seed=4)),
     ("fq_q3_slip", lambda: four_quadrant_problem(7, 3, seed=2)),
+    ("oct_q2_3d", lambda: octant_problem((4, 3, 3), 2, seed=2)),
 ]
 
 

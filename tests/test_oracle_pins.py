@@ -330,3 +330,65 @@ def test_line_search_converges_to_the_root(oracle_mod):
         assert abs(lres - exact) <= 1e-12, (case, lres, exact)
         checked += 1
     assert checked > 400
+
+
+def _line_problem_3d(axis, cells):
+    """A 3D Q1 mesh with `cells` elements along `axis` and one across the other two (slip walls), and
+    the map from its nodes to the nodes of the 1D Q1 mesh of the same cells."""
+    shape = [1, 1, 1]
+    shape[axis] = cells
+    P3 = assembly.assemble_3d(*shape, 1)
+    e = np.arange(P3.n) // P3.n_loc
+    ijk = [(e % shape[0]), (e // shape[0]) % shape[1], e // (shape[0] * shape[1])]
+    l = np.arange(P3.n) % P3.n_loc
+    loc = [l % 2, (l // 2) % 2, l // 4]
+    return P3, ijk[axis] * 2 + loc[axis]
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+@pytest.mark.parametrize("order", ["LOW", "HIGH"])
+def test_3d_reduces_to_1d(oracle_mod, axis, order):
+    """Sod data varying along one axis of a 3D Q1 mesh (one element across the other two, slip walls):
+    on every node line along that axis the 3D stage equals the 1D stage to roundoff, with the same tau;
+    the transverse momenta stay at roundoff.  With Q1 the minimal viscosity factor c_k h^{p_k} is 1 in any
+    dimension, so the high order matches too (Sec. 5.1); the bounds of the limited scheme depend on the
+    dimension through h and are not compared."""
+    cells = 24
+    P1 = assembly.assemble_1d(cells, 1)
+    P3, to1 = _line_problem_3d(axis, cells)
+    U1 = workloads.sod(P1.x[0])
+    U3 = np.zeros((5, P3.n))
+    U3[0], U3[1 + axis], U3[4] = U1[0][to1], U1[1][to1], U1[2][to1]
+    od = getattr(oracle_mod, order)
+    O1, O3 = oracle_mod.Oracle(P1, params=dict(order=od)), oracle_mod.Oracle(P3, params=dict(order=od))
+    tau = O3.max_dt(U3, 0.5)
+    assert tau <= O1.max_dt(U1, 0.5)  # the transverse directions add viscosity to d_ii, not to U
+    out1, f1 = O1.stage(U1, tau)
+    out3, f3 = O3.stage(U3, tau)
+    assert f1 == f3 == 0
+    scale = np.abs(U1).max()  # Sod starts at rest, so the momentum is measured against the whole state
+    for q1, q3 in ((0, 0), (1, 1 + axis), (2, 4)):
+        assert np.abs(out3[q3] - out1[q1][to1]).max() <= 1e-13 * scale
+    assert np.abs(out3[1:4][np.arange(3) != axis]).max() <= 1e-13 * scale
+
+
+def test_3d_limited_stage_invariants(oracle_mod):
+    """A limited stage on eight-octant data (Q1 and Q2 hexahedra, slip walls): rho and E conserved, every
+    state admissible, and the result inside the local bounds of eq. (eq:local_bounds)."""
+    for k in (1, 2):
+        P = assembly.assemble_3d(4, 3, 3, k)
+        rng = np.random.default_rng(3 + k)
+        x, y, z = P.x
+        oct_ = (x > 0.5).astype(int) + 2 * (y > 0.5) + 4 * (z > 0.5)
+        rho, p = rng.uniform(0.1, 2, 8)[oct_], rng.uniform(0.1, 2, 8)[oct_]
+        U = workloads.prim_to_cons(rho, rng.uniform(-1, 1, (3, 8))[:, oct_], p, 1.4)
+        O = oracle_mod.Oracle(P)
+        out, flags, tr = O.stage(U, O.max_dt(U, 0.5), trace=True)
+        assert flags == 0
+        tot0, tot1 = (P.mi * U).sum(1), (P.mi * out).sum(1)
+        assert (np.abs(tot1 - tot0)[[0, 4]] <= 1e-14 * np.abs(tot0)[[0, 4]]).all()
+        r = out[0]
+        eps = out[4] - 0.5 * (out[1:4] ** 2).sum(0) / r
+        assert (r > 0).all() and (eps > 0).all()
+        assert (r >= tr["rho_min"] * (1 - 1e-13)).all() and (r <= tr["rho_max"] * (1 + 1e-13)).all()
+        assert (r ** -1.4 * eps >= tr["s_min"] * (1 - 1e-12)).all()
