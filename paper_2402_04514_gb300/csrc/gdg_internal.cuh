@@ -53,6 +53,7 @@ struct Dev {
   double k13;           // (gamma + 1) / (2 gamma)
   int gp, gq;           // gamma = gp / gq with gq <= 8 (7/5, 5/3, ...); gq = 0 when gamma is not such a ratio
   int ie_root;          // 1 / e when it is an integer <= 16 (p^{-e} by a Newton root), else 0
+  double rcp_gq, rcp_ie_root, rcp_gpq;  // 1 / gq, 1 / ie_root, 1 / (gp + gq) (0 where undefined)
   double inv_gp1;       // 1 / (gamma + 1)
   double c_ev;
   int order, passes, bounds_mode;
@@ -81,6 +82,9 @@ inline void set_eos(Dev& D, double gamma) {
     }
   }
   D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
+  D.rcp_gq = D.gq > 0 ? 1.0 / D.gq : 0.0;
+  D.rcp_ie_root = D.ie_root > 0 ? 1.0 / D.ie_root : 0.0;
+  D.rcp_gpq = D.gq > 0 ? 1.0 / (D.gp + D.gq) : 0.0;
   D.inv_gp1 = 1.0 / (gamma + 1.0);
   D.gamma_f = (float)gamma;
   D.gm1h_f = (float)(0.5 * D.gm1);
@@ -311,12 +315,18 @@ inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sc
 // ------------------------------------------------------------------------------------------------
 // Device helpers (Euler equations of Sec. 2.2 and the pieces of Sec. 3-5 used by several kernels).
 
+// x^k for an integer k >= 0 by binary powering without a trailing square (k = 5, 7, 12 take 3, 4, 4
+// multiplications).
 __device__ __forceinline__ double ipow(double x, int k) {
-  double r = 1.0;
-  while (k > 0) {
-    if (k & 1) r *= x;
+  if (k <= 0) return 1.0;
+  while (!(k & 1)) {
     x *= x;
     k >>= 1;
+  }
+  double r = x;
+  while (k >>= 1) {
+    x *= x;
+    if (k & 1) r *= x;
   }
   return r;
 }
@@ -375,11 +385,11 @@ __device__ __forceinline__ double rcp64(double x) {
 // y <- y + y (1 - x y^q) / q, from the FP32 seed exp2(-log2(x) / q); two steps take the seed's 2^-22
 // relative error below FP64 rounding (the error contracts as (q+1)/2 e^2).  Arguments outside the FP32
 // normal range use pow.
-__device__ __forceinline__ double rootinv(double x, int q) {
+// iq = 1.0 / q, precomputed by the caller (Dev holds it for the exponents of the equation of state).
+__device__ __forceinline__ double rootinv(double x, int q, double iq) {
   float xf = d2f_fast(x);
-  if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -1.0 / q);
+  if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -iq);
   double y = f2d_fast(exp2f(-log2f(xf) / (float)q));
-  const double iq = 1.0 / q;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     double t = fma(-x, ipow(y, q), 1.0);
@@ -387,11 +397,12 @@ __device__ __forceinline__ double rootinv(double x, int q) {
   }
   return y;
 }
+__device__ __forceinline__ double rootinv(double x, int q) { return rootinv(x, q, 1.0 / q); }
 
 // rho^{-gamma} and 1/rho together.  With gamma = p/q: y = rho^{-1/q}, rho^{-gamma} = y^p, 1/rho = y^q.
 __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double* inv_rho) {
   if (D.gq > 0) {
-    double y = rootinv(rho, D.gq);
+    double y = rootinv(rho, D.gq, D.rcp_gq);
     *inv_rho = ipow(y, D.gq);
     return ipow(y, D.gp);
   }
@@ -402,7 +413,7 @@ __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double
 // rho^gamma and 1/rho together.  With gamma = p/q and k = ceil(p/q): rho^gamma = rho^k y^{kq - p}.
 __device__ __forceinline__ double rho_pow_gamma(const Dev& D, double rho, double* inv_rho) {
   if (D.gq > 0) {
-    double y = rootinv(rho, D.gq);
+    double y = rootinv(rho, D.gq, D.rcp_gq);
     *inv_rho = ipow(y, D.gq);
     int k = (D.gp + D.gq - 1) / D.gq;
     return ipow(rho, k) * ipow(y, k * D.gq - D.gp);
@@ -474,11 +485,15 @@ __device__ __forceinline__ double to_f64(float f) {
 __device__ __forceinline__ bool finite_f32(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
 __device__ __forceinline__ float ipowf(float x, int k) {
-  float r = 1.f;
-  while (k > 0) {
-    if (k & 1) r *= x;
+  if (k <= 0) return 1.f;
+  while (!(k & 1)) {
     x *= x;
     k >>= 1;
+  }
+  float r = x;
+  while (k >>= 1) {
+    x *= x;
+    if (k & 1) r *= x;
   }
   return r;
 }
@@ -532,7 +547,7 @@ __device__ __forceinline__ float lambda_max_mx(const Dev& D, float uL, float pL,
 __device__ __forceinline__ void prim_fp64(const Dev& D, double irho, double p, double* ip, double* a, double* pme) {
   *ip = 1.0 / p;
   *a = sqrt(D.gamma * p * irho);
-  *pme = D.ie_root > 0 ? rootinv(p, D.ie_root) : pow(p, -D.e_exp);
+  *pme = D.ie_root > 0 ? rootinv(p, D.ie_root, D.rcp_ie_root) : pow(p, -D.e_exp);
 }
 
 // 1/p, a and p^{-e} of a state that k_prim does not see (a boundary state), as each path computes them.
