@@ -13,6 +13,19 @@ namespace gdg {
 // Per-node primitive record written by k_prim and read for every neighbour in the sweeps.
 enum { PR_IRHO = 0, PR_P, PR_A, PR_PME, PR_F, PR_ST, PR_IP, NPRIM };
 
+// Constants of the Newton roots x^{-1/q} (rootinv, below).
+struct RootQ {
+  int q;
+  double iq, c2;  // 1 / q and (q + 1) / (2 q^2)
+};
+__host__ __device__ inline RootQ root_q(int q) {
+  RootQ r;
+  r.q = q;
+  r.iq = 1.0 / q;
+  r.c2 = 0.5 * r.iq * (1.0 + r.iq);
+  return r;
+}
+
 // Everything a kernel needs, passed by value.  Per-entry and per-node arrays are device pointers in
 // CSR order (rows element-contiguous; within a row the stencil entries c_ij != 0 come first, then the
 // m_ij-only entries); boundary entries are sorted by node (b_ptr indexes them).
@@ -53,7 +66,7 @@ struct Dev {
   double k13;           // (gamma + 1) / (2 gamma)
   int gp, gq;           // gamma = gp / gq with gq <= 8 (7/5, 5/3, ...); gq = 0 when gamma is not such a ratio
   int ie_root;          // 1 / e when it is an integer <= 16 (p^{-e} by a Newton root), else 0
-  double rcp_gq, rcp_ie_root, rcp_gpq;  // 1 / gq, 1 / ie_root, 1 / (gp + gq) (0 where undefined)
+  RootQ root_gq, root_ie, root_gpq;  // rootinv constants for gq, ie_root, gp + gq (q = 1, unused, where undefined)
   double inv_gp1;       // 1 / (gamma + 1)
   double c_ev;
   int order, passes, bounds_mode;
@@ -82,9 +95,9 @@ inline void set_eos(Dev& D, double gamma) {
     }
   }
   D.ie_root = (D.ie > 0 && D.ie <= 16) ? D.ie : 0;
-  D.rcp_gq = D.gq > 0 ? 1.0 / D.gq : 0.0;
-  D.rcp_ie_root = D.ie_root > 0 ? 1.0 / D.ie_root : 0.0;
-  D.rcp_gpq = D.gq > 0 ? 1.0 / (D.gp + D.gq) : 0.0;
+  D.root_gq = root_q(D.gq > 0 ? D.gq : 1);
+  D.root_ie = root_q(D.ie_root > 0 ? D.ie_root : 1);
+  D.root_gpq = root_q(D.gq > 0 ? D.gp + D.gq : 1);
   D.inv_gp1 = 1.0 / (gamma + 1.0);
   D.gamma_f = (float)gamma;
   D.gm1h_f = (float)(0.5 * D.gm1);
@@ -381,28 +394,31 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(y, e, y);
 }
 
-// y = x^{-1/q} for x > 0 and 1 <= q <= 16, by the Newton-Raphson iteration for f(y) = y^{-q} - x,
-// y <- y + y (1 - x y^q) / q, from the FP32 seed exp2(-log2(x) / q); two steps take the seed's 2^-22
-// relative error below FP64 rounding (the error contracts as (q+1)/2 e^2).  Arguments outside the FP32
-// normal range use pow.
-// iq = 1.0 / q, precomputed by the caller (Dev holds it for the exponents of the equation of state).
-__device__ __forceinline__ double rootinv(double x, int q, double iq) {
+// y = x^{-1/q} for x > 0 and 1 <= q <= 16.  From the FP32 seed y0 = exp2(-log2(x) / q), with
+// t = 1 - x y0^q and x^{-1/q} = y0 (1 - t)^{-1/q}, one step y0 (1 + t/q + (q+1)/(2q^2) t^2) sums the
+// binomial series through t^2; the rest, |binom(-1/q, 3)| |t|^3 (1 + O(t)) with |binom(-1/q, 3)| <= 1
+// (0.09 for q >= 5), is below 2^-56 when |t| <= 2^-19, which the seed's 2^-22 relative error (times q)
+// gives for arguments near 1.  Far
+// from 1 log2f's absolute error grows with |log2 x| and the seed can be worse; then one Newton step
+// y <- y + y (1 - x y^q) / q squares the remaining error.  Arguments outside the FP32 normal range use pow.
+__device__ __forceinline__ double rootinv(double x, const RootQ& r) {
   float xf = d2f_fast(x);
-  if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -iq);
-  double y = f2d_fast(exp2f(-log2f(xf) / (float)q));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    double t = fma(-x, ipow(y, q), 1.0);
-    y = fma(y * t, iq, y);
+  if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -r.iq);
+  double y = f2d_fast(exp2f(-log2f(xf) / (float)r.q));
+  const double t = fma(-x, ipow(y, r.q), 1.0);
+  y = fma(y * t, fma(r.c2, t, r.iq), y);
+  // |t| > 2^-19, compared on the bit patterns (integer pipe)
+  if ((__double_as_longlong(t) & 0x7fffffffffffffffLL) > 0x3ec0000000000000LL) {
+    const double t2 = fma(-x, ipow(y, r.q), 1.0);
+    y = fma(y * t2, r.iq, y);
   }
   return y;
 }
-__device__ __forceinline__ double rootinv(double x, int q) { return rootinv(x, q, 1.0 / q); }
 
 // rho^{-gamma} and 1/rho together.  With gamma = p/q: y = rho^{-1/q}, rho^{-gamma} = y^p, 1/rho = y^q.
 __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double* inv_rho) {
   if (D.gq > 0) {
-    double y = rootinv(rho, D.gq, D.rcp_gq);
+    double y = rootinv(rho, D.root_gq);
     *inv_rho = ipow(y, D.gq);
     return ipow(y, D.gp);
   }
@@ -413,7 +429,7 @@ __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double
 // rho^gamma and 1/rho together.  With gamma = p/q and k = ceil(p/q): rho^gamma = rho^k y^{kq - p}.
 __device__ __forceinline__ double rho_pow_gamma(const Dev& D, double rho, double* inv_rho) {
   if (D.gq > 0) {
-    double y = rootinv(rho, D.gq, D.rcp_gq);
+    double y = rootinv(rho, D.root_gq);
     *inv_rho = ipow(y, D.gq);
     int k = (D.gp + D.gq - 1) / D.gq;
     return ipow(rho, k) * ipow(y, k * D.gq - D.gp);
@@ -547,7 +563,7 @@ __device__ __forceinline__ float lambda_max_mx(const Dev& D, float uL, float pL,
 __device__ __forceinline__ void prim_fp64(const Dev& D, double irho, double p, double* ip, double* a, double* pme) {
   *ip = 1.0 / p;
   *a = sqrt(D.gamma * p * irho);
-  *pme = D.ie_root > 0 ? rootinv(p, D.ie_root, D.rcp_ie_root) : pow(p, -D.e_exp);
+  *pme = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
 }
 
 // 1/p, a and p^{-e} of a state that k_prim does not see (a boundary state), as each path computes them.

@@ -65,11 +65,11 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   P[PR_P * n + i] = p;
   P[PR_IP * n + i] = 1.0 / p;
   P[PR_A * n + i] = sqrt(D.gamma * p * irho);
-  P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.ie_root, D.rcp_ie_root) : pow(p, -D.e_exp);
+  P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
   // f = (gm1 s~)^{1/(gamma+1)} = x^{q/(p+q)} = x (x^{-1/(p+q)})^p for gamma = p/q
   double x = D.gm1 * st;
   P[PR_F * n + i] =
-      (D.gq > 0 && D.gp + D.gq <= 16) ? x * ipow(rootinv(x, D.gp + D.gq, D.rcp_gpq), D.gp) : pow(x, D.inv_gp1);
+      (D.gq > 0 && D.gp + D.gq <= 16) ? x * ipow(rootinv(x, D.root_gpq), D.gp) : pow(x, D.inv_gp1);
   P[PR_ST * n + i] = st;
 }
 

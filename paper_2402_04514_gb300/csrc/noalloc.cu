@@ -33,7 +33,7 @@ __device__ __forceinline__ NodePrim node_prim(const Dev& D, const double* U, int
   r.p = D.gm1 * (U[dim + 1] - 0.5 * m2 * r.irho);
   r.ip = 1.0 / r.p;
   r.a = sqrt(D.gamma * r.p * r.irho);
-  r.pme = D.ie_root > 0 ? rootinv(r.p, D.ie_root, D.rcp_ie_root) : pow(r.p, -D.e_exp);
+  r.pme = D.ie_root > 0 ? rootinv(r.p, D.root_ie) : pow(r.p, -D.e_exp);
   return r;
 }
 

@@ -11,7 +11,7 @@ __global__ void k_math(int fn, int q, const double* __restrict__ x, double* __re
   double v = x[i];
   switch (fn) {
     case 0: y[i] = rcp64(v); break;
-    case 1: y[i] = rootinv(v, q); break;
+    case 1: y[i] = rootinv(v, root_q(q)); break;
     case 2: y[i] = 1.0 / v; break;
     case 3: y[i] = pow(v, -1.0 / q); break;
     case 4: y[i] = f2d_fast(d2f_fast(v)); break;
@@ -142,7 +142,7 @@ __global__ void k_rate(double* out, int iters, double a, double b) {
       if (OP == 3) x[k] = pow(x[k], a) + b;                // FP64 power
       if (OP == 4) xf[k] = fmaf(xf[k], (float)a, (float)b);  // FFMA
       if (OP == 5) x[k] = rcp64(x[k]) + b;                 // reciprocal of this library
-      if (OP == 6) x[k] = rootinv(x[k], 5) + b;            // x^{-1/5} of this library
+      if (OP == 6) x[k] = rootinv(x[k], root_q(5)) + b;            // x^{-1/5} of this library
       if (OP == 7) x[k] = (double)((float)x[k] * 0.5f) + b;  // FP64 -> FP32 -> FP64 conversion pair
     }
   }
