@@ -301,11 +301,13 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   const double irho_i = P[PR_IRHO * n + i], p_i = P[PR_P * n + i], ip_i = P[PR_IP * n + i],
                a_i = P[PR_A * n + i], pme_i = P[PR_PME * n + i], f_i = P[PR_F * n + i], st_i = P[PR_ST * n + i];
   using Acc = std::conditional_t<MX, float, double>;  // arithmetic of the indicator's sums
-  double rhs[M];
+  // RHS^L = sum_j f(U_j) c_ij - sum_j d_ij (U_j - U_i) + boundary terms, accumulated as its two sums
+  // (sg, sdu); the indicator's Fsum reuses sg
+  double sg[M], sdu[M];
   Acc Fsum[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
-    rhs[q] = 0.0;
+    sg[q] = sdu[q] = 0.0;
     Fsum[q] = Acc(0);
   }
   Acc psum = Acc(0);
@@ -322,11 +324,15 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
 #pragma unroll
     for (int q = 0; q < M; ++q) {
       const double ge = S.G[q * nnz + e];
-      rhs[q] += ge - d * (Uj[q] - Ui[q]);
+      sg[q] += ge;
+      sdu[q] = fma(d, Uj[q] - Ui[q], sdu[q]);
+      // Fsum = sum_j (f(U_j) - f(U_i)) c_ij: here the f(U_i) c_ij terms, sg is added after the loop (the
+      // two sums are exact negatives of each other term by term on a stencil holding one state); the
+      // mixed path sums the FP64 differences in FP32
       if constexpr (MX)
         Fsum[q] += to_f32(ge + S.G[q * nnz + t]);
       else
-        Fsum[q] += ge + S.G[q * nnz + t];  // (f(U_j) - f(U_i)) c_ij
+        Fsum[q] += S.G[q * nnz + t];
     }
     if constexpr (MX)
       psum += to_f32(S.G[e]) * (to_f32(P[PR_F * n + j]) - to_f32(f_i));
@@ -335,6 +341,10 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
     lo = pmin(lo, pmin(Uj[0], S.barR[e]));
     hi = pmax(hi, pmax(Uj[0], S.barR[e]));
     sl = pmin(sl, pmin(P[PR_ST * n + j], S.barS[e]));
+  }
+  if constexpr (!MX) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) Fsum[q] += sg[q];
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double nv[DIM], UB[M];
@@ -365,7 +375,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
     double Ub[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      rhs[q] += cnm * fB[q] - d * (UB[q] - Ui[q]);
+      sg[q] = fma(cnm, fB[q], sg[q]);
+      sdu[q] = fma(d, UB[q] - Ui[q], sdu[q]);
       if constexpr (MX)
         Fsum[q] -= to_f32(cnm * fi[q]);
       else
@@ -377,6 +388,9 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   }
   const double inv_mi = D.inv_mi[i];
   if (2.0 * tau * dsum * inv_mi > 1.0 + 1e-12) atomicOr(S.flags, (unsigned)GDG_FLAG_CFL);
+  double rhs[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) rhs[q] = sg[q] - sdu[q];
   double UL[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
