@@ -378,20 +378,18 @@ __device__ __forceinline__ double abs_bits(double x) {
 __device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ bool is_one_bits(double x) { return __double_as_longlong(x) == 0x3ff0000000000000LL; }
 
-// FP64 reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (Muller et al., Handbook of
-// Floating-Point Arithmetic, ch. 5) started from the FP32 reciprocal: the relative error squares at
-// each step (2^-23 -> 2^-46 -> below FP64 rounding), and the last step is a fused update, so the result
-// is within 2 ulp of 1/x.  Costs 4 FP64 FMAs instead of a full FP64 division on a chip whose FP64 pipe is
-// the bottleneck.  Arguments outside the FP32 normal range take the IEEE division.
+// FP64 reciprocal from the FP32 reciprocal y0 of x in FP32 (relative error e = 1 - x y0 below 2^-22):
+// 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...), summed through e^2 in one fused update, leaves
+// e^3 < 2^-66 plus the rounding of the last FMA, so the result is within 2 ulp of 1/x.  Costs 3 FP64
+// operations instead of a full FP64 division on a chip whose FP64 pipe is the bottleneck.  Arguments
+// outside the FP32 normal range take the IEEE division.
 __device__ __forceinline__ double rcp64(double x) {
   float xf = d2f_fast(x);
   float ax = fabsf(xf);
   if (!(ax > 1e-37f && ax < 1e37f)) return 1.0 / x;
-  double y = f2d_fast(__frcp_rn(xf));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double y = f2d_fast(__frcp_rn(xf));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // y = x^{-1/q} for x > 0 and 1 <= q <= 16.  From the FP32 seed y0 = exp2(-log2(x) / q), with
