@@ -802,7 +802,7 @@ __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, 
   float den = 2.f * c.r0 * r1;
   float dK = (c.r0 * (2.f * mb + bb) - a * c.m0sq) / den;
   float SK = (c.r0 * (2.f * nb2 + bb) + fabsf(a) * c.m0sq) / den;
-  float dG = c.sg0 * expm1f((float)D.gamma * log1pf(a / c.r0));
+  float dG = c.sg0 * expm1f(D.gamma_f * log1pf(a / c.r0));
   float dpsi = eE - dK - dG;
   float scale = fabsf(eE) + SK + fabsf(dG);
   float t = c.psi0f + dpsi;
