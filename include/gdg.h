@@ -279,9 +279,9 @@ int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, const double* 
                        double* tau_out, void* stream);
 
 /* Launch schedule: threads per block of the one-thread-per-row (per-edge) kernels (128, 256 or 512),
- * the largest element block of the element sweep (whole elements, 1..160 nodes) and the queue slots per
+ * the largest element block of the element sweep (whole elements, 1..288 nodes) and the queue slots per
  * thread of the deferred line-search grid (1..1024).  Defaults: 256 threads, 160 nodes, 4 slots.
- * gdg_autotune picks them for one handle by timing: it saves U and the clock, runs 3 + 4 + 3 candidate
+ * gdg_autotune picks them for one handle by timing: it saves U and the clock, runs 3 + 5 + 3 candidate
  * schedules of (trials + 1) gdg_ssprk3_step each from that saved state (coordinate descent: row-kernel
  * block sizes, then the element block, then the queue grid; each kernel keeps its fastest candidate),
  * and restores U, the clock and the status flags.  It allocates one temporary state copy and

@@ -251,7 +251,8 @@ struct Many {
 enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL, KN_LSFIX, KN_TAU, KN_AXPY,
             KN_COUNT };
 constexpr int kRowMaxThreads = 512;  // one-thread-per-row / per-edge kernels: 128, 256 or 512 threads
-constexpr int kHighMaxBlock = 160;   // element sweep: whole elements, at most this many nodes per block
+constexpr int kHighMaxBlock = 288;   // element sweep: whole elements, at most this many nodes per block
+constexpr int kHighDefaultCap = 160;  // the element block of an untuned schedule
 constexpr int kLsfixThreads = 128;
 
 // The launch schedule: threads per block of each one-thread-per-row kernel (KN_EDGE: per edge), the
@@ -266,7 +267,7 @@ struct Sched {
 inline Sched default_sched() {
   Sched sc;
   for (int k = 0; k < KN_COUNT; ++k) sc.bt[k] = 256;
-  sc.high_cap = kHighMaxBlock;
+  sc.high_cap = kHighDefaultCap;
   sc.lsfix_slots = 4;
   return sc;
 }

@@ -134,7 +134,7 @@ int autotune_schedule(gdg::Sched& sched, int n_loc, int trials, Apply apply, Ste
   // 2. element sweep block cap
   double best = 1e300;
   int last_npb = -1, best_cap = sc.high_cap;
-  for (int cap : {64, 96, 128, gdg::kHighMaxBlock}) {
+  for (int cap : {64, 96, 128, 160, gdg::kHighMaxBlock}) {
     const int npb = gdg::high_nodes_per_block(n_loc, cap);
     if (npb < 1 || npb == last_npb) continue;
     last_npb = npb;

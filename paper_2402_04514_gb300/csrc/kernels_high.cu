@@ -64,7 +64,7 @@ __device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t
 // The mixed path (MX) runs steps 1, 2 and the A_ij of step 4 in FP32 (the differences U_j - U_i in FP64
 // first); the bounds and the line search stay FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kMaxBlock, 4) k_high(Src src, int nodes_per_block) {
+__global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
   constexpr int M = DIM + 2;
   constexpr int kShared = kMaxBlock + kMaxBlock / 2;  // room for one pad slot per element of 2+ nodes
   using R = std::conditional_t<MX, float, double>;    // arithmetic of steps 1, 2 and the A_ij of step 4
