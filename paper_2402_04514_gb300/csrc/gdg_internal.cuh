@@ -710,7 +710,7 @@ template <int DIM>
 struct LsRow {
   double U0[DIM + 2];
   double rmin, rmax, smin, psi0;
-  float r0, m0[DIM], m0sq, sg0, psi0f, dlo, dhi;
+  float r0, ir0, m0[DIM], m0sq, sg0, psi0f, dlo, dhi;
 };
 
 template <int DIM>
@@ -728,6 +728,7 @@ __device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double
   double rg = (U0[0] > 0.0) ? rho_pow_gamma(D, U0[0], &ir) : 0.0;
   c.psi0 = (U0[0] > 0.0) ? U0[DIM + 1] - 0.5 * m2 * ir - smin * rg : -1.0;
   c.r0 = d2f_fast(U0[0]);
+  c.ir0 = __frcp_rn(c.r0);
 #pragma unroll
   for (int k = 0; k < DIM; ++k) c.m0[k] = d2f_fast(U0[1 + k]);
   c.m0sq = d2f_fast(m2);
@@ -780,7 +781,11 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
 //   dpsi = s A_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
 //   dG = s_min rho0^gamma expm1(gamma log1p(a / rho0)),   a = s A_rho, b = s A_m.
 // sf is s in FP32 with relative error at most 3 2^-23.  Every other FP32 operation and conversion has
-// relative error <= 2^-23 and log1pf / expm1f a few ulp, so the FP32 dpsi is within 2e-6 S of the exact
+// relative error <= 2^-23 (the two quotients by the denominator and a / rho0 are products with correctly
+// rounded reciprocals, two roundings of at most 2^-24 each; a denominator above 1e36 fails the
+// certificate, so that its reciprocal stays a normal number) and log1pf / expm1f a few ulp.  The
+// quotients never take FP32 division's slow path, which a zero numerator (A = 0) would otherwise take.
+// So the FP32 dpsi is within 2e-6 S of the exact
 // increment, S = |s A_E| + S_K + |dG| and S_K the magnitude of dK's terms.  With t = psi0f + dpsi in FP32
 // (psi0f = psi(0) truncated to FP32, relative error < 2^-23), certifying only when
 // t > 1e-4 S + 1e-6 |psi0f| leaves a factor of 50 on every error term, so psi(s) > 0 exactly.  Requires
@@ -801,9 +806,11 @@ __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, 
   float eE = sf * d2f_fast(A[DIM + 1]);
   float r1 = c.r0 + a;
   float den = 2.f * c.r0 * r1;
-  float dK = (c.r0 * (2.f * mb + bb) - a * c.m0sq) / den;
-  float SK = (c.r0 * (2.f * nb2 + bb) + fabsf(a) * c.m0sq) / den;
-  float dG = c.sg0 * expm1f(D.gamma_f * log1pf(a / c.r0));
+  if (!(den < 1e36f)) return false;
+  const float iden = __frcp_rn(den);
+  float dK = (c.r0 * (2.f * mb + bb) - a * c.m0sq) * iden;
+  float SK = (c.r0 * (2.f * nb2 + bb) + fabsf(a) * c.m0sq) * iden;
+  float dG = c.sg0 * expm1f(D.gamma_f * log1pf(a * c.ir0));
   float dpsi = eE - dK - dG;
   float scale = fabsf(eE) + SK + fabsf(dG);
   float t = c.psi0f + dpsi;
