@@ -102,31 +102,37 @@ __global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
       else
         rhs[q] = S.RHSL[(size_t)q * n + i];
     }
-    // min / max of non-negative values on the integer pipe
+    // min / max of non-negative values on the integer pipe; every input of the loop is read-only in this
+    // kernel, so its loads take the read-only path and may move ahead of the stores of A
     const int e1 = D.sten_end[i];
+#pragma unroll 2
     for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
-      const int j = D.col[e];
+      const int j = __ldg(D.col + e);
+      const double dl64 = __ldg(S.dL + e), mu = __ldg(D.mu + e), Nj = abs_bits(__ldg(S.N + j));
+      double Uj[M];
+#pragma unroll
+      for (int q = 0; q < M; ++q) Uj[q] = __ldg(U + (size_t)q * n + j);
       if constexpr (MX) {
         // d^H - d^L from FP32 operands: every factor is symmetric in (i, j), so the same bits come out
         // of row j, and A_ji = -A_ij holds exactly
-        const float dl = to_f32(S.dL[e]);
-        const float dev = dl * fminf(D.c_ev_f * to_f32(pmax(Ni, abs_bits(S.N[j]))), 1.f);
-        const float dd = fmaxf(to_f32(D.mu[e]) * dl, dev) - dl;
+        const float dl = to_f32(dl64);
+        const float dev = dl * fminf(D.c_ev_f * to_f32(pmax(Ni, Nj)), 1.f);
+        const float dd = fmaxf(to_f32(mu) * dl, dev) - dl;
         const float td = tau_r * dd;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
-          const float du = to_f32(U[(size_t)q * n + j] - Ui[q]);
+          const float du = to_f32(Uj[q] - Ui[q]);
           rhs[q] = fmaf(-dd, du, rhs[q]);
           S.A[(size_t)q * D.nnz + e] = to_f64(td * du);  // viscous part of A_ij, completed below
         }
       } else {
-        const double dl = S.dL[e];
-        const double dev = dl * pmin(D.c_ev * pmax(Ni, abs_bits(S.N[j])), 1.0);
-        const double dd = pmax(D.mu[e] * dl, dev) - dl;
+        const double dl = dl64;
+        const double dev = dl * pmin(D.c_ev * pmax(Ni, Nj), 1.0);
+        const double dd = pmax(mu * dl, dev) - dl;
         const double td = tau * dd;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
-          const double du = U[(size_t)q * n + j] - Ui[q];
+          const double du = Uj[q] - Ui[q];
           rhs[q] = fma(-dd, du, rhs[q]);
           S.A[(size_t)q * D.nnz + e] = td * du;  // viscous part of A_ij, completed below
         }
