@@ -205,12 +205,13 @@ enum { GDG_K_PRIM = 0, GDG_K_MAXDT = 1, GDG_K_LOW = 2, GDG_K_HIGH = 3, GDG_K_LIM
 int gdg_profile(gdg_handle* h, int32_t enable);
 int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
 
-/* Self-test of the FP64 helpers that replace CUDA's division and power on the sweep's hot loops:
- * fn 0 = reciprocal by Newton-Raphson from an FP32 seed, 1 = x^{-1/q} by Newton-Raphson from an FP32
- * seed, 2 = CUDA's 1.0 / x, 3 = CUDA's pow(x, -1.0 / q), 4 = the integer-only FP64 -> FP32 -> FP64
- * conversion pair of the FP32 certificates (truncation to 23 significand bits in the FP32 normal range,
- * zeros kept, NaN otherwise); x, y: device [n]; 1 <= q <= 16.  Asynchronous on stream.  The tests
- * compare 0 with 2 and 1 with 3 in ulps, and 4 with the truncation done on the host. */
+/* Self-test of the FP64 helpers that replace CUDA's division, power and square root on the sweep's hot
+ * loops: fn 0 = reciprocal from an FP32 seed, 1 = x^{-1/q} from an FP32 seed, 2 = CUDA's 1.0 / x,
+ * 3 = CUDA's pow(x, -1.0 / q), 4 = the integer-only FP64 -> FP32 -> FP64 conversion pair of the FP32
+ * certificates (truncation to 23 significand bits in the FP32 normal range, zeros kept, NaN otherwise),
+ * 5 = square root from the FP32 reciprocal square root, 6 = CUDA's sqrt; x, y: device [n];
+ * 1 <= q <= 16.  Asynchronous on stream.  The tests compare 0 with 2, 1 with 3 and 5 with 6 in ulps,
+ * and 4 with the truncation done on the host. */
 int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream);
 
 /* Check of the mixed-precision wave-speed bound (GDG_PRECISION_MIXED) against the FP64 one, for gamma

@@ -393,6 +393,21 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(y, fma(e, e, e), y);
 }
 
+// sqrt(x) for x in the FP32 normal range by two Heron corrections s <- s + (x - s^2) h from s0 = x y0,
+// with y0 the FP32 reciprocal square root (relative error below 2^-21) and h = y0 / 2 held fixed: each
+// correction multiplies the relative error by about that of h and adds half its square
+// (2^-21 -> 2^-41 -> 2^-61), so the result is within an ulp or so of sqrt(x).  5 FP64 operations instead of
+// CUDA's square root with its special-case handling.  Other arguments take sqrt.
+__device__ __forceinline__ double sqrt64(double x) {
+  const float xf = d2f_fast(x);
+  if (!(xf > 1e-37f && xf < 1e37f)) return sqrt(x);
+  const float yf = rsqrtf(xf);
+  const double h = f2d_fast(0.5f * yf);
+  double s = x * f2d_fast(yf);
+  s = fma(fma(-s, s, x), h, s);
+  return fma(fma(-s, s, x), h, s);
+}
+
 // y = x^{-1/q} for x > 0 and 1 <= q <= 16.  From the FP32 seed y0 = exp2(-log2(x) / q), with
 // t = 1 - x y0^q and x^{-1/q} = y0 (1 - t)^{-1/q}, one step y0 (1 + t/q + (q+1)/(2q^2) t^2) sums the
 // binomial series through t^2; the rest, |binom(-1/q, 3)| |t|^3 (1 + O(t)) with |binom(-1/q, 3)| <= 1
@@ -459,8 +474,8 @@ __device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL,
   double r = num * rcp64(aL * pmeL + aR * pmeR);
   double pt = D.ie > 0 ? ipow(r, D.ie) : pow(r, D.inv_e);
   double xL = pt - pL, xR = pt - pR;
-  double sL = xL > 0.0 ? sqrt(1.0 + D.k13 * xL * ipL) : 1.0;
-  double sR = xR > 0.0 ? sqrt(1.0 + D.k13 * xR * ipR) : 1.0;
+  double sL = xL > 0.0 ? sqrt64(1.0 + D.k13 * xL * ipL) : 1.0;
+  double sR = xR > 0.0 ? sqrt64(1.0 + D.k13 * xR * ipR) : 1.0;
   double l1 = uL - aL * sL;
   double l3 = uR + aR * sR;
   return fmax(fmax(-l1, 0.0), fmax(l3, 0.0));
@@ -561,7 +576,7 @@ __device__ __forceinline__ float lambda_max_mx(const Dev& D, float uL, float pL,
 // The FP64 primitives of k_prim's FP64 path from rho (as 1/rho) and p.
 __device__ __forceinline__ void prim_fp64(const Dev& D, double irho, double p, double* ip, double* a, double* pme) {
   *ip = 1.0 / p;
-  *a = sqrt(D.gamma * p * irho);
+  *a = sqrt64(D.gamma * p * irho);
   *pme = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
 }
 
@@ -576,7 +591,7 @@ __device__ __forceinline__ void prim_of(const Dev& D, double rho, double irho, d
     *pme = to_f64(f.pme);
   } else {
     *ip = 1.0 / p;
-    *a = sqrt(D.gamma * p * irho);
+    *a = sqrt64(D.gamma * p * irho);
     *pme = pow(p, -D.e_exp);
   }
 }

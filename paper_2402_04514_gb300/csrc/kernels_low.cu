@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
   P[PR_IP * n + i] = 1.0 / p;
-  P[PR_A * n + i] = sqrt(D.gamma * p * irho);
+  P[PR_A * n + i] = sqrt64(D.gamma * p * irho);
   P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
   // f = (gm1 s~)^{1/(gamma+1)} = x^{q/(p+q)} = x (x^{-1/(p+q)})^p for gamma = p/q
   double x = D.gm1 * st;

@@ -15,6 +15,8 @@ __global__ void k_math(int fn, int q, const double* __restrict__ x, double* __re
     case 2: y[i] = 1.0 / v; break;
     case 3: y[i] = pow(v, -1.0 / q); break;
     case 4: y[i] = f2d_fast(d2f_fast(v)); break;
+    case 5: y[i] = sqrt64(v); break;
+    case 6: y[i] = sqrt(v); break;
     default: y[i] = 0.0;
   }
 }
@@ -23,7 +25,7 @@ __global__ void k_math(int fn, int q, const double* __restrict__ x, double* __re
 }  // namespace gdg
 
 extern "C" int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream) {
-  if (fn < 0 || fn > 4 || q < 1 || q > 16 || n < 0 || (n > 0 && (!x || !y))) return GDG_EINVAL;
+  if (fn < 0 || fn > 6 || q < 1 || q > 16 || n < 0 || (n > 0 && (!x || !y))) return GDG_EINVAL;
   if (n == 0) return GDG_OK;
   int threads = 256;
   long long blocks = (n + threads - 1) / threads;

@@ -267,6 +267,22 @@ def test_fp64_helpers_against_cuda(torch_cuda, q):
         assert (np.abs(mine_q - cuda_q) <= 8 * np.spacing(np.abs(cuda_q))).all()
 
 
+def test_square_root_against_cuda(torch_cuda):
+    """The square root of the wave-speed bound and the sound speed (two Heron corrections from the FP32
+    reciprocal square root) is within 1 ulp of CUDA's correctly rounded sqrt over the FP32 normal range,
+    and takes sqrt itself outside it."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import math_selftest
+
+    rng = np.random.default_rng(9)
+    x = np.concatenate([np.exp(rng.uniform(np.log(1e-30), np.log(1e30), 400000)),
+                        1.0 + rng.uniform(0, 1e-6, 10000), [1.0, 2.0, 4.0, 0.25, 1e-300, 1e300, 0.0]])
+    xd = torch.from_numpy(x).cuda()
+    mine, ref = math_selftest(5, 1, xd).cpu().numpy(), math_selftest(6, 1, xd).cpu().numpy()
+    assert (np.abs(mine - ref) <= np.spacing(ref)).all()
+    assert mine[-3:].tolist() == ref[-3:].tolist()
+
+
 def test_integer_float_conversions(torch_cuda):
     """The FP64 -> FP32 -> FP64 conversions of the FP32 certificates, done with integer operations only:
     truncation to 23 significand bits in the FP32 normal range, signed zeros kept, NaN for everything
