@@ -433,8 +433,9 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
     }
     S.N[i] = Dn > 0.f ? to_f64(R / Dn) : 0.0;
   } else {
-    double pref = f_i * D.inv_gp1 / irho_i;
-    double ip = 1.0 / p_i;
+    // rho f / (gamma + 1) from rho itself and 1/p from k_prim, so that no division is needed here
+    const double pref = f_i * D.inv_gp1 * Ui[0];
+    const double ip = ip_i;
     double v2 = 0.0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) v2 += (Ui[1 + k] * irho_i) * (Ui[1 + k] * irho_i);
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
       R -= grad[q] * Fsum[q];
       Dn += fabs(grad[q]) * fabs(Fsum[q]);
     }
-    S.N[i] = Dn > 0.0 ? R / Dn : 0.0;
+    S.N[i] = Dn > 0.0 ? R * rcp64(Dn) : 0.0;
   }
 }
 
