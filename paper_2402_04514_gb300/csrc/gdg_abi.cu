@@ -486,6 +486,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   D.nnz = (int)nnz;
   D.nb = (int)nb;
   D.n_loc = nl;
+  gdg::set_nl_division(D, nl);
   D.row_ptr = (const int*)ptr(o_rowptr);
   D.sten_end = (const int*)ptr(o_sten);
   D.col = (const int*)ptr(o_col);

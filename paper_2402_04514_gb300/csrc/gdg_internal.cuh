@@ -31,6 +31,8 @@ __host__ __device__ inline RootQ root_q(int q) {
 // m_ij-only entries); boundary entries are sorted by node (b_ptr indexes them).
 struct Dev {
   int n, nnz, nb, n_loc;
+  unsigned long long nl_mul;  // floor(x / n_loc) = (x * nl_mul) >> nl_shift for 0 <= x < 2^31 (div_nl)
+  int nl_shift;
   // CSR
   const int* row_ptr;   // [n+1]
   const int* sten_end;  // [n] end of row i's stencil entries: I(i) is row_ptr[i] .. sten_end[i] - 1
@@ -76,6 +78,19 @@ struct Dev {
   int mixed;
   float gamma_f, gm1h_f, e_exp_f, inv_e_f, k13_f, inv_gp1_f, c_ev_f;
 };
+
+// The multiplier and shift of div_nl for n_loc in 1..32: with s = ceil(log2 n_loc) and
+// M = ceil(2^(31+s) / n_loc) < 2^32, x M / 2^(31+s) exceeds x / n_loc by less than 2^-s < 1 / n_loc for
+// x < 2^31, which never reaches the next integer, so the shifted product is floor(x / n_loc).
+inline void set_nl_division(Dev& D, int nl) {
+  int s = 0;
+  while ((1 << s) < nl) ++s;
+  D.nl_shift = 31 + s;
+  D.nl_mul = ((1ULL << D.nl_shift) + (unsigned long long)nl - 1) / (unsigned long long)nl;
+}
+__device__ __forceinline__ int div_nl(const Dev& D, int x) {
+  return (int)(((unsigned long long)(unsigned)x * D.nl_mul) >> D.nl_shift);
+}
 
 // Equation-of-state constants of Dev for gamma (host side; gdg_setup and the wave-speed check).
 inline void set_eos(Dev& D, double gamma) {

@@ -160,9 +160,10 @@ __global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
   __syncthreads();
   if (valid) {
     const int nl = D.n_loc;
-    const int il = i % nl;
+    const int ei = div_nl(D, i);
+    const int il = i - ei * nl;
     const int t0 = sh - il;  // first node of the element in the shared arrays
-    const double* Minv = D.MKinv + ((size_t)(i / nl) * nl + il) * nl;
+    const double* Minv = D.MKinv + ((size_t)ei * nl + il) * nl;
     R acc[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] = R(0);
@@ -231,14 +232,15 @@ __global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
   const double ikm = D.inv_km[i];
   const float ikmf = d2f_fast(ikm);
   const int nl = D.n_loc;
-  const int elem = i / nl;
-  const int t0 = sh - (i % nl);
+  const int elem = div_nl(D, i);
+  const int t0 = sh - (i - elem * nl);
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int j = D.col[e];
     double A[M];
     const bool stencil = e < se;
-    const bool same = (j / nl) == elem;
-    const int tj = t0 + (j % nl);
+    const int ej = div_nl(D, j);
+    const bool same = ej == elem;
+    const int tj = t0 + (j - ej * nl);
     if constexpr (MX) {
       const float mij = same ? to_f32(D.mij[e]) : 0.f;
 #pragma unroll

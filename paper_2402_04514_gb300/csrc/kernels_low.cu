@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   if (i >= D.n) return;
   double Ui[DIM + 2];
   load_state<DIM>(c.U, D.n, i, Ui);
-  double irho = MX ? rcp64(Ui[0]) : 1.0 / Ui[0];
+  double irho = rcp64(Ui[0]);
   double m2 = 0.0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) m2 += Ui[1 + k] * Ui[1 + k];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   double st = rho_neg_gamma(D, Ui[0], &ir) * eps;
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
-  P[PR_IP * n + i] = 1.0 / p;
+  P[PR_IP * n + i] = rcp64(p);
   P[PR_A * n + i] = sqrt64(D.gamma * p * irho);
   P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
   // f = (gm1 s~)^{1/(gamma+1)} = x^{q/(p+q)} = x (x^{-1/(p+q)})^p for gamma = p/q
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b)
       dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, irho_i, p_i, ip_i, a_i, pme_i);
-    if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
+    if (dsum > 0.0) val = 0.5 * D.mi[i] * rcp64(dsum);
   }
   block_min_to(val, S.tau_bits);
 }
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
         dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, P[PR_IRHO * n + i], P[PR_P * n + i], P[PR_IP * n + i],
                                         P[PR_A * n + i], P[PR_PME * n + i]);
     }
-    if (dsum > 0.0) val = D.mi[i] / (2.0 * dsum);
+    if (dsum > 0.0) val = 0.5 * D.mi[i] * rcp64(dsum);
   }
   block_min_to(val, &c.clk->tau_bits);
 }
