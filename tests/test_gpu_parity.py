@@ -2,7 +2,8 @@
 
 Tolerance: per component, max |U_gpu - U_oracle| / max |U_oracle| <= 1e-12 after one stage and <= 1e-10
 after 100 SSP-RK3 steps; invariant-domain checks (rho > 0, eps > 0, local bounds) hold exactly.
-Sizes span several thread blocks with a ragged tail (blocks of 256 nodes, 153-160 for the element sweep)."""
+Sizes span several thread blocks with a ragged tail (blocks of 256 nodes, 153-160 nodes for the element sweep
+under the default schedule)."""
 import numpy as np
 import pytest
 
