@@ -48,6 +48,12 @@ MUTANTS = {
         "double R2 = vni <= 0.0 ? pi / pow(Ui[0], g) : pd / pow(Ud[0], g);"),
     "supersonic_inflow_keeps_the_interior": ("  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ud[q];",
                                              "  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ui[q];"),
+    # dimension handling that only a 3D mesh exercises
+    "flux_pressure_only_in_the_first_two_directions": (
+        "for (int k = 0; k < d; ++k) out[1 + k] = U[1 + k] * vc + p * c[k];",
+        "for (int k = 0; k < d; ++k) out[1 + k] = U[1 + k] * vc + (k < 2 ? p * c[k] : 0.0);"),
+    "kinetic_energy_of_the_first_two_components": ("for (int k = 0; k < d; ++k) m2 += U[1 + k] * U[1 + k];",
+                                                   "for (int k = 0; k < d && k < 2; ++k) m2 += U[1 + k] * U[1 + k];"),
 }
 
 FAST_PINS = [
@@ -63,6 +69,12 @@ FAST_PINS = [
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 0.0),
     lambda O: pins.test_sod_exact_solution(O),
     lambda O: pins.test_line_search_converges_to_the_root(O),
+]
+
+
+DIM3_PINS = [
+    lambda O: pins.test_3d_reduces_to_1d(O, 2, "LOW"),
+    lambda O: pins.test_3d_limited_stage_invariants(O),
 ]
 
 
@@ -93,7 +105,7 @@ def test_pins_reject_mutant(name, monkeypatch):
         monkeypatch.setattr(om, "_lib", None)
         monkeypatch.setattr(om, "build", lambda force=False: so)
         caught = []
-        for pin in FAST_PINS + BC_PINS + [_vortex_q1_limited]:
+        for pin in FAST_PINS + BC_PINS + DIM3_PINS + [_vortex_q1_limited]:
             try:
                 pin(om)
             except (AssertionError, ValueError, FloatingPointError):
