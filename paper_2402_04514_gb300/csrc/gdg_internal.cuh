@@ -62,6 +62,7 @@ struct Dev {
   const int* edge_i;    // [ne] row i
   // equation of state and method constants
   double gamma, gm1;    // gamma, gamma - 1
+  double gm1h;          // (gamma - 1) / 2
   double e_exp;         // e = (gamma - 1) / (2 gamma)
   double inv_e;         // 1 / e
   int ie;               // 1 / e when it is an integer (7 for gamma = 1.4, 5 for gamma = 5/3), else 0
@@ -96,6 +97,7 @@ __device__ __forceinline__ int div_nl(const Dev& D, int x) {
 inline void set_eos(Dev& D, double gamma) {
   D.gamma = gamma;
   D.gm1 = gamma - 1.0;
+  D.gm1h = 0.5 * D.gm1;
   D.e_exp = (gamma - 1.0) / (2.0 * gamma);
   D.inv_e = 1.0 / D.e_exp;
   const double r = __builtin_round(D.inv_e);
@@ -485,15 +487,18 @@ __device__ __forceinline__ double pmax(double a, double b) {
 __device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL, double ipL, double aL,
                                              double pmeL, double uR, double pR, double ipR, double aR,
                                              double pmeR) {
-  double num = fmax(aL + aR - 0.5 * D.gm1 * (uR - uL), 0.0);
+  // max(x, 0), the tests x > 0 and the final maximum of two non-negative values on the integer pipe
+  // (a positive double is a positive int64)
+  auto pos = [](double x) { return __double_as_longlong(x) > 0 ? x : 0.0; };
+  double num = pos(aL + aR - D.gm1h * (uR - uL));
   double r = num * rcp64(aL * pmeL + aR * pmeR);
   double pt = D.ie > 0 ? ipow(r, D.ie) : pow(r, D.inv_e);
   double xL = pt - pL, xR = pt - pR;
-  double sL = xL > 0.0 ? sqrt64(1.0 + D.k13 * xL * ipL) : 1.0;
-  double sR = xR > 0.0 ? sqrt64(1.0 + D.k13 * xR * ipR) : 1.0;
+  double sL = __double_as_longlong(xL) > 0 ? sqrt64(1.0 + D.k13 * xL * ipL) : 1.0;
+  double sR = __double_as_longlong(xR) > 0 ? sqrt64(1.0 + D.k13 * xR * ipR) : 1.0;
   double l1 = uL - aL * sL;
   double l3 = uR + aR * sR;
-  return fmax(fmax(-l1, 0.0), fmax(l3, 0.0));
+  return pmax(pos(-l1), pos(l3));
 }
 
 // ------------------------------------------------------------------------------------------------
