@@ -64,7 +64,7 @@ __device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t
 // The mixed path (MX) runs steps 1, 2 and the A_ij of step 4 in FP32 (the differences U_j - U_i in FP64
 // first); the bounds and the line search stay FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
+__device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) {
   constexpr int M = DIM + 2;
   constexpr int kShared = kMaxBlock + kMaxBlock / 2;  // room for one pad slot per element of 2+ nodes
   using R = std::conditional_t<MX, float, double>;    // arithmetic of steps 1, 2 and the A_ij of step 4
@@ -278,11 +278,26 @@ __global__ void __maxnreg__(96) k_high(Src src, int nodes_per_block) {
   }
 }
 
+// The element sweep as two kernels, because they want different register budgets: the FP64 path, bound by
+// the FP64 pipe and memory latency, runs fastest at 72 registers (three 288-thread blocks per SM, a few
+// spills); the mixed path, whose FP32 work needs more live values, at 96.
+template <int DIM, class Src>
+__global__ void __maxnreg__(72) k_high(Src src, int nodes_per_block) {
+  high_sweep<DIM, false, Src>(src, nodes_per_block);
+}
+template <int DIM, class Src>
+__global__ void __maxnreg__(96) k_high_mixed(Src src, int nodes_per_block) {
+  high_sweep<DIM, true, Src>(src, nodes_per_block);
+}
+
 template <int DIM, bool MX, class Src>
 cudaError_t high_launch(const Src& src, long long blocks, int npb, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (npb < 1 || npb > kMaxBlock) return cudaErrorInvalidValue;
-  k_high<DIM, MX, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
+  if constexpr (MX)
+    k_high_mixed<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
+  else
+    k_high<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
   return cudaGetLastError();
 }
 
