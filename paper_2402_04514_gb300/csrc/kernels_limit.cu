@@ -27,13 +27,16 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
 #pragma unroll
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
   const int r0 = D.row_ptr[i], r1 = D.row_ptr[i + 1];
+  bool remainder = false;  // some entry has l1 < 1, so that pass 2 has a remainder to limit
   for (int e = r0; e < r1; ++e) {
     double l = pmin(S.l1[e], S.l1[D.tr[e]]);  // limiter coefficients are in [0, 1]: integer min
+    remainder |= !is_one_bits(l);
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += l * S.A[q * nnz + e];
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
     double l = S.l1B[b];
+    remainder |= !is_one_bits(l);
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += l * S.AB[q * nb + b];
   }
@@ -48,6 +51,11 @@ __global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
   }
 #pragma unroll
   for (int q = 0; q < M; ++q) S.U1[q * n + i] = U1[q];
+  if (!remainder) {  // every l2 multiplies a zero remainder: no row context, no search
+    for (int e = r0; e < r1; ++e) S.l2[e] = 1.0;
+    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) S.l2B[b] = 1.0;
+    return;
+  }
   LsRow<DIM> ls;
   ls_row<DIM>(D, ls, U1, S.bounds[i], S.bounds[n + i], S.bounds[2 * n + i]);
   const double ikm = D.inv_km[i];
