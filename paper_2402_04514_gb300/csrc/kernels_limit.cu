@@ -150,13 +150,17 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
   double acc[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
+  // an entry with l1 = 1 has no remainder (its weight is 0): skipped, with the loads of its A
   for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
     int t = D.tr[e];
-    double w = pmin(S.l2[e], S.l2[t]) * (1.0 - pmin(S.l1[e], S.l1[t]));
+    const double l1s = pmin(S.l1[e], S.l1[t]);
+    if (is_one_bits(l1s)) continue;
+    double w = pmin(S.l2[e], S.l2[t]) * (1.0 - l1s);
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += w * S.A[q * nnz + e];
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+    if (is_one_bits(S.l1B[b])) continue;
     double w = S.l2B[b] * (1.0 - S.l1B[b]);
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] += w * S.AB[q * nb + b];
