@@ -260,6 +260,15 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
         S.A[(size_t)q * D.nnz + e] = a;
       }
     }
+    // A = 0 (a uniform neighbourhood): the search's outcome is l = 1 exactly when the FP32 tests it
+    // starts with pass, which here reduce to a density gap above and psi(0) > 0; then skip them
+    unsigned long long abits = 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q) abits |= (unsigned long long)__double_as_longlong(A[q]) << 1;
+    if (abits == 0 && ls.dhi > 0.f && ls.psi0f > 0.f) {
+      S.l1[e] = 1.0;
+      continue;
+    }
     double l, fb;
     if (line_search_head<DIM>(D, ls, A, ikm, ikmf, &l, &fb))
       S.l1[e] = l;
