@@ -376,6 +376,23 @@ __device__ __forceinline__ float d2f_fast(double x) {
   return __uint_as_float(r);
 }
 
+// d2f_fast for an increment x that the FP64 line search adds to a state component u0 as fma(s, x, u0).
+// A nonzero x below the FP32 normal range (|x| < 2^-126) gives +-0 instead of NaN when that fma cannot see
+// it, which the caller asserts with fz: s_f 2^-71 < |u0| in FP32 (s_f = s in FP32, relative error below
+// 3 2^-23; |u0| truncated, so at most |u0|) gives s 2^-72 < |u0|, hence s |x| < s 2^-126 < 2^-54 |u0|,
+// less than half an ulp of u0, and fma(s, x, u0) = u0 = fma(s, 0, u0): the FP64 search evaluates the same
+// point as for x = 0.  Without fz, and above the FP32 range, the result is NaN, which fails a certificate.
+// (Antidiffusive fluxes of a uniform neighbourhood are rounding residuals, some of them products of two
+// residuals far below 2^-126.)
+__device__ __forceinline__ float d2f_incr(double x, bool fz) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  unsigned r = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e <= 0 || e >= 255) r = (e <= 0 && fz) ? (hi & 0x80000000u) : 0x7fc00000u;
+  return __uint_as_float(r);
+}
+
 // FP32 -> FP64 by integer operations only: exact for normal numbers, zeros, infinities and NaN; an FP32
 // subnormal gives NaN (no caller produces one where a result is needed: the seeds below are normal, and
 // a NaN certificate fails).
@@ -746,6 +763,7 @@ struct LsRow {
   double U0[DIM + 2];
   double rmin, rmax, smin, psi0;
   float r0, ir0, m0[DIM], m0sq, sg0, psi0f, dlo, dhi;
+  float fl;  // min(rho0, |m0_k|, psi0f) in FP32, 0 unless all are positive: the bound of d2f_incr's guard
 };
 
 template <int DIM>
@@ -775,6 +793,12 @@ __device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double
   const float dlo = d2f_fast(U0[0] - rmin), dhi = d2f_fast(rmax - U0[0]), gap = 1e-6f * c.r0;
   c.dlo = dlo > gap ? dlo : 0.f;
   c.dhi = dhi > gap ? dhi : 0.f;
+  // |E0| >= psi(0) >= psi0f, so that psi0f bounds |E0| from below where it is positive
+  float fl = c.psi0f;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) fl = fminf(fl, fabsf(c.m0[k]));
+  fl = fminf(fl, c.r0);
+  c.fl = fl > 0.f ? fl : 0.f;  // NaN (a value outside the FP32 range) also gives 0
 }
 
 // psi(s) = eps(U0 + s A) - s_min rho(s)^gamma (the entropy constraint of the set B_i, Sec. 5.4,
@@ -828,17 +852,19 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
 // range) fails the final comparison.
 template <int DIM>
 __device__ __forceinline__ bool ls_certified(const Dev& D, const LsRow<DIM>& c, const double* A, float sf) {
-  float a = sf * d2f_fast(A[0]);
+  // components of A below the FP32 range count as 0 where the FP64 search cannot see them (d2f_incr)
+  const bool fz = sf * 0x1p-71f < c.fl;
+  float a = sf * d2f_incr(A[0], fz);
   if (!(a > -0.5f * c.r0)) return false;
   float mb = 0.f, bb = 0.f, nb2 = 0.f;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    float b = sf * d2f_fast(A[1 + k]);
+    float b = sf * d2f_incr(A[1 + k], fz);
     mb = fmaf(c.m0[k], b, mb);
     bb = fmaf(b, b, bb);
     nb2 = fmaf(fabsf(c.m0[k]), fabsf(b), nb2);
   }
-  float eE = sf * d2f_fast(A[DIM + 1]);
+  float eE = sf * d2f_incr(A[DIM + 1], fz);
   float r1 = c.r0 + a;
   float den = 2.f * c.r0 * r1;
   if (!(den < 1e36f)) return false;
@@ -867,8 +893,9 @@ __device__ __forceinline__ bool line_search_head(const Dev& D, const LsRow<DIM>&
   // proved in FP32 (wf = w in FP32): the products and conversions have relative error below 4e-7, so a
   // relative margin of 1e-6 on both sides leaves the exact distance to the bound above 8e-7 times a gap
   // of at least 1e-6 rho (ls_row), far beyond the FP64 rounding of the closed form's comparisons, which
-  // therefore agree with it.
-  const float pr = wf * d2f_fast(A[0]);
+  // therefore agree with it.  An A_rho below the FP32 range counts as 0 under the guard of d2f_incr, which
+  // also makes rho(U0) + w A_rho round to rho(U0) in the closed form.
+  const float pr = wf * d2f_incr(A[0], wf * 0x1p-71f < c.fl);
   const bool inside = pr >= 0.f ? pr * 1.000001f < c.dhi * 0.999999f : -pr * 1.000001f < c.dlo * 0.999999f;
   double l = 1.0;
   float sf = wf;

@@ -11,8 +11,11 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // Sweep C: l_ij = min(l_ij^(i), l_ji^(j)) (Lemma ConsInvariants needs l_ij = l_ji);
 // U^(1)_i = U^L_i + (sum_j l_ij A_ij + sum_k l_i^k A_i^k) / m_i; then the second pass limits the
 // remainder (1 - l) A from U^(1) against the same bounds.  With one pass it writes U_out from U^(1).
+// Capped at 72 registers (seven 128-thread blocks per SM; a few bytes of spills in the search): the row
+// sums, which every row runs, need far fewer, and the searches of the rare rows with a remainder would
+// otherwise set the kernel's occupancy.
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kThreads) k_limit2(Src src, int last) {
+__global__ void __maxnreg__(72) k_limit2(Src src, int last) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;

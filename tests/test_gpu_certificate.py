@@ -68,3 +68,36 @@ def test_certified_rows_are_feasible(torch_cuda, gamma):
         rate = cert[easy & sel].mean()
         print(f"gamma {gamma} {branch}: {(easy & sel).sum()} comfortably feasible rows, certified {rate:.4f}")
         assert (easy & sel).sum() > 1000 and rate > 0.99
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_increments_below_fp32_range(torch_cuda, gamma):
+    """Components of A below the FP32 normal range (|A_q| < 2^-126, rounding residuals of a uniform
+    neighbourhood) count as 0 when s |A_q| is below half an ulp of U0_q: the FP64 search then evaluates
+    psi at the same point as for A_q = 0, so the certificate decides both alike.  Where U0_q is 0 the guard
+    cannot hold and the row is not certified."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import certificate_check
+
+    rng = np.random.default_rng(11)
+    n, m = 200000, 4
+    rows = _rows(rng, n, gamma)
+    tiny = rng.random((n, m)) < 0.5
+    mag = np.exp(rng.uniform(np.log(1e-300), np.log(1e-39), (n, m))) * rng.choice([-1.0, 1.0], (n, m))
+    A = rows[:, m:2 * m]
+    A[tiny] = mag[tiny]
+    flushed = rows.copy()
+    flushed[:, m:2 * m][tiny] = 0.0
+    out = certificate_check(2, gamma, torch.from_numpy(rows).cuda()).cpu().numpy()
+    ref = certificate_check(2, gamma, torch.from_numpy(flushed).cuda()).cpu().numpy()
+    assert np.array_equal(out[:, 1], ref[:, 1])  # the FP64 evaluation point does not see them
+    assert np.array_equal(out[:, 0], ref[:, 0])
+    assert out[:, 0].sum() > 10000
+    psi = _psi_ld(rows, gamma)
+    assert (psi[out[:, 0] == 1.0] >= 0).all()
+    # a zero momentum component with a tiny increment: no guard, no certificate
+    z = rows[:2000].copy()
+    z[:, 1] = 0.0
+    z[:, m + 1] = 1e-40
+    out_z = certificate_check(2, gamma, torch.from_numpy(z).cuda()).cpu().numpy()
+    assert (out_z[:, 0] == 0.0).all()
