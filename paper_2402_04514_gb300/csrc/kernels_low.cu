@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
     return;
   }
   double ir;
-  double st = rho_neg_gamma(D, Ui[0], &ir) * eps;
+  double st = rho_neg_gamma<false>(D, Ui[0], &ir) * eps;
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
   P[PR_IP * n + i] = rcp64(p);
@@ -160,9 +160,11 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
 }
 
 // The same bound inside the fused SSP-RK3 step, after the edge sweep of the step's first stage: the row
-// sums of the stored d_ij^L plus the boundary viscosities, reduced into the instance's clock.
+// sums of the stored d_ij^L plus the boundary viscosities, reduced into the instance's clock.  Capped at
+// 48 registers: the row sum, which every row runs, is latency-bound and wants many warps; the boundary
+// viscosities of the few boundary rows would otherwise take 117 and spill at the cap.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_tau(Src src) {
+__global__ void __maxnreg__(48) k_tau(Src src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -174,7 +176,9 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
   double val = INFINITY;
   if (i < D.n) {
     double dsum = 0.0;
-    for (int e = D.row_ptr[i]; e < D.sten_end[i]; ++e) dsum += S.dL[e];
+    const int e0 = D.row_ptr[i], e1 = D.sten_end[i];
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) dsum += __ldg(S.dL + e);  // loads issued ahead of the in-order sum
     const int b0 = D.b_ptr[i], b1 = D.b_ptr[i + 1];
     if (b0 < b1) {
       const size_t n = D.n;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_tau(Src src) {
 // The mixed path (MX) takes lambda from lambda_pair<true> and the entropy power of the bar state in FP32;
 // the fluxes, G and the bar state itself stay FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_edge(Src src) {
+__global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -233,20 +237,28 @@ __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
   const double d = cnm * lam;
   S.dL[e] = d;
   S.dL[t] = d;
-  double fi[M], fj[M];
-  flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
-  flux_n<DIM>(Uj, nv, mnR, uR, p_j, fj);
-  const double h = MX ? to_f64(0.5f / to_f32(lam)) : 0.5 * rcp64(lam);  // |c_ij| / (2 d_ij)
-  double Ub[M];
+  // f(U) c_ij with c_ij = |c_ij| n_ij, from m.c = |c| m.n and v.c = |c| v.n
+  double cv[DIM], gi[M], gj[M];
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) cv[q] = cnm * nv[q];
+  flux_n<DIM>(Ui, cv, cnm * mnL, cnm * uL, p_i, gi);
+  flux_n<DIM>(Uj, cv, cnm * mnR, cnm * uR, p_j, gj);
+  // W = 2 Ubar = U_i + U_j - (f(U_j) - f(U_i)) c_ij / d_ij, halved where it is used
+  const double r = MX ? to_f64(1.f / to_f32(d)) : rcp64(d);
+  double W[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) {
-    S.G[q * nnz + e] = cnm * fj[q];
-    S.G[q * nnz + t] = -(cnm * fi[q]);
-    Ub[q] = 0.5 * (Ui[q] + Uj[q]) - h * (fj[q] - fi[q]);
+    S.G[q * nnz + e] = gj[q];
+    S.G[q * nnz + t] = -gi[q];
+    W[q] = fma(-r, gj[q] - gi[q], Ui[q] + Uj[q]);
   }
-  double mb2 = 0.0, irb;
+  double Ub[M];
+  Ub[0] = 0.5 * W[0];
+  Ub[DIM + 1] = 0.5 * W[DIM + 1];
+  double mw2 = 0.0, irb;  // |2 m(Ubar)|^2; 0.125 mw2 = |m(Ubar)|^2 / 2
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) mb2 += Ub[1 + q] * Ub[1 + q];
+  for (int q = 0; q < DIM; ++q) mw2 += W[1 + q] * W[1 + q];
+  const double hm2 = 0.125 * mw2;
   double stb;
   if constexpr (MX) {
     // eps(Ubar) in FP64 (E - |m|^2 / (2 rho) cancels at high Mach numbers) with 1/rho(Ubar) from one
@@ -255,14 +267,14 @@ __global__ void __launch_bounds__(kThreads) k_edge(Src src) {
     const double y = to_f64(1.f / rbf);
     irb = y * fma(-Ub[0], y, 2.0);
     const float rg = powf(rbf, -D.gamma_f);
-    stb = to_f64(rg * to_f32(Ub[DIM + 1] - 0.5 * mb2 * irb));
+    stb = to_f64(rg * to_f32(fma(-hm2, irb, Ub[DIM + 1])));
     if (!finite_f32(rg)) {
       const double rgb = rho_neg_gamma(D, Ub[0], &irb);
-      stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+      stb = rgb * fma(-hm2, irb, Ub[DIM + 1]);
     }
   } else {
     const double rgb = rho_neg_gamma(D, Ub[0], &irb);  // sets irb = 1 / rho(Ubar) before its use below
-    stb = rgb * (Ub[DIM + 1] - 0.5 * mb2 * irb);
+    stb = rgb * fma(-hm2, irb, Ub[DIM + 1]);
   }
   S.barR[e] = Ub[0];
   S.barR[t] = Ub[0];
