@@ -189,7 +189,9 @@ int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream);
 
 /* Copies an intermediate of the last stage to host memory (for tests and diagnostics): name is one of
  * "dL" [nnz], "dB" [nb], "N" [n], "UL" [m][n], "rho_min" [n], "rho_max" [n], "s_min" [n], "l1" [nnz],
- * "l2" [nnz], "U1" [m][n], "A" [m][nnz]; entries follow gdg_problem's order (boundary data its own).
+ * "l2" [nnz] (written only where min(l1_ij, l1_ji) < 1, the entries whose pass-2 factor multiplies a
+ * nonzero remainder), "U1" [m][n], "A" [m][nnz]; entries follow gdg_problem's order (boundary data its
+ * own).
  * "ls_deferred" [2] gives the number of line searches of each limiter pass that needed the bracketed
  * iteration (run by a separate kernel over a queue).  count must equal the array size.  Synchronises
  * the stream. */

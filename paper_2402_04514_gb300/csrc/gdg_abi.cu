@@ -105,7 +105,8 @@ struct Arena {
   X(prim, double, gdg::NPRIM * n) X(dL, double, nnz) X(dB, double, nb) X(bbar, double, 2 * nb)            \
   X(UL, double, m * n) X(RHSL, double, m * n) X(N, double, n) X(agg, double, 3 * n) X(A, double, m * nnz) \
   X(AB, double, m * nb) X(bounds, double, 3 * n) X(l1, double, nnz) X(l1B, double, nb) X(l2, double, nnz) \
-  X(l2B, double, nb) X(U1, double, m * n) X(flags, unsigned, 4) X(tau, unsigned long long, 1)             \
+  X(l2B, double, nb) X(U1, double, m * n) X(rem, unsigned char, n) X(flags, unsigned, 4)                 \
+  X(tau, unsigned long long, 1)                                                                          \
   X(lsq, int2, nnz + nb) X(clk, gdg::Clock, 1)
 
 struct Layout {
@@ -536,6 +537,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   S.l2 = (double*)ptr(o_l2);
   S.l2B = (double*)ptr(o_l2B);
   S.U1 = (double*)ptr(o_U1);
+  S.rem = (unsigned char*)ptr(o_rem);
   S.flags = (unsigned*)ptr(o_flags);
   S.lsq_n = S.flags + 2;
   S.lsq = (int2*)ptr(o_lsq);

@@ -147,6 +147,7 @@ struct Scratch {
   double* l2;      // [nnz] pass 2
   double* l2B;     // [nb]
   double* U1;      // [m][n]
+  unsigned char* rem;  // [n] 1 where row i has a pass-2 remainder (a symmetrised pass-1 factor below 1)
   unsigned int* flags;
   unsigned int* lsq_n;  // [2] lengths of the deferred line-search queues of passes 1 and 2
   int2* lsq;            // [nnz + nb] deferred line searches of the current pass (ls_defer)

@@ -54,21 +54,16 @@ __global__ void __maxnreg__(72) k_limit2(Src src, int last) {
   }
 #pragma unroll
   for (int q = 0; q < M; ++q) S.U1[q * n + i] = U1[q];
-  if (!remainder) {  // every l2 multiplies a zero remainder: no row context, no search
-    for (int e = r0; e < r1; ++e) S.l2[e] = 1.0;
-    for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) S.l2B[b] = 1.0;
-    return;
-  }
+  S.rem[i] = remainder;
+  // l2 is computed only where it multiplies a nonzero remainder (1 - l1)A: k_final reads no other, and a
+  // row without a remainder (the flag above) takes no row context and no search
+  if (!remainder) return;
   LsRow<DIM> ls;
   ls_row<DIM>(D, ls, U1, S.bounds[i], S.bounds[n + i], S.bounds[2 * n + i]);
   const double ikm = D.inv_km[i];
-  // an entry with l1 = 1 has no remainder: its l2 multiplies zero and is set to 1 without a search
   for (int e = r0; e < r1; ++e) {
     const double l1s = pmin(S.l1[e], S.l1[D.tr[e]]);
-    if (is_one_bits(l1s)) {
-      S.l2[e] = 1.0;
-      continue;
-    }
+    if (is_one_bits(l1s)) continue;
     const double w = (1.0 - l1s) * ikm;
     double A[M];
 #pragma unroll
@@ -80,10 +75,7 @@ __global__ void __maxnreg__(72) k_limit2(Src src, int last) {
       ls_defer(S, 1, e, i);
   }
   for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    if (is_one_bits(S.l1B[b])) {
-      S.l2B[b] = 1.0;
-      continue;
-    }
+    if (is_one_bits(S.l1B[b])) continue;
     const double w = (1.0 - S.l1B[b]) * ikm;
     double A[M];
 #pragma unroll
@@ -150,6 +142,11 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
   const int i = lb * blockDim.x + threadIdx.x;
   if (i >= D.n) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
+  if (!S.rem[i]) {  // no remainder in the row: U^(2)_i = U^(1)_i
+#pragma unroll
+    for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, S.U1[q * n + i]);
+    return;
+  }
   double acc[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) acc[q] = 0.0;

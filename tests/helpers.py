@@ -98,3 +98,27 @@ def rel_err(a, b):
         scale = max(np.abs(b[c]).max(), 1e-300)
         out = max(out, float(np.abs(a[c] - b[c]).max() / scale))
     return out
+
+
+def inoutflow_case(name):
+    """The in/outflow cases of the GPU tests: (problem, initial state, boundary data [m][nb])."""
+    if name == "sod1d_open":
+        P = assembly.assemble_1d(200, 1, bc=("inoutflow", "inoutflow"))
+        U = workloads.sod(P.x[0])
+        return P, U, np.ascontiguousarray(workloads.sod(P.b_x[0]))
+    if name == "oct_q1_3d_open":
+        P, U = octant_problem((5, 4, 4), 1, seed=3, bc=dict(left="inoutflow", right="inoutflow", back="inoutflow"))
+        return P, U, np.ascontiguousarray(U[:, P.b_node])
+    if name == "fq_q2_open_sides":
+        P = assembly.assemble_2d(13, 13, 2, bc=dict(left="inoutflow", right="inoutflow"))
+        U = workloads.four_quadrant(P.x[0], P.x[1], seed=0)
+        return P, U, np.ascontiguousarray(U[:, P.b_node])
+    # supersonic stream (Mach ~2.6 along x) over a density bump
+    sides = dict(left="inoutflow", right="inoutflow", bottom="inoutflow", top="inoutflow")
+    P = assembly.assemble_2d(16, 16, 1, bc=sides)
+    x, y = P.x
+    rho = 1.0 + 0.5 * np.exp(-40 * ((x - 0.4) ** 2 + (y - 0.5) ** 2))
+    U = workloads.prim_to_cons(rho, np.stack([np.full(P.n, 3.0), np.full(P.n, 0.5)]), np.full(P.n, 1.0), 1.4)
+    bd = workloads.prim_to_cons(np.full(P.nb, 1.0), np.stack([np.full(P.nb, 3.0), np.full(P.nb, 0.5)]),
+                                np.full(P.nb, 1.0), 1.4)
+    return P, U, np.ascontiguousarray(bd)

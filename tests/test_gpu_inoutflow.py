@@ -6,12 +6,13 @@ import numpy as np
 import pytest
 
 from paper_2402_04514_gb300 import assembly, workloads
-from tests.helpers import rel_err
+from tests.helpers import inoutflow_case, rel_err
 
 pytestmark = pytest.mark.gpu
 
 STAGE_TOL = 1e-12
 LONG_TOL = 1e-10
+ILL_TOL = 3e-11  # per step on the supersonic stream: at least three times the oracle's own one-ulp move
 
 
 @pytest.fixture(scope="module")
@@ -27,27 +28,7 @@ def torch_cuda():
 
 
 def _case(name):
-    if name == "sod1d_open":
-        P = assembly.assemble_1d(200, 1, bc=("inoutflow", "inoutflow"))
-        U = workloads.sod(P.x[0])
-        return P, U, np.ascontiguousarray(workloads.sod(P.b_x[0]))
-    if name == "oct_q1_3d_open":
-        from tests.helpers import octant_problem
-        P, U = octant_problem((5, 4, 4), 1, seed=3, bc=dict(left="inoutflow", right="inoutflow", back="inoutflow"))
-        return P, U, np.ascontiguousarray(U[:, P.b_node])
-    if name == "fq_q2_open_sides":
-        P = assembly.assemble_2d(13, 13, 2, bc=dict(left="inoutflow", right="inoutflow"))
-        U = workloads.four_quadrant(P.x[0], P.x[1], seed=0)
-        return P, U, np.ascontiguousarray(U[:, P.b_node])
-    # supersonic stream (Mach ~2.6 along x) over a density bump
-    sides = dict(left="inoutflow", right="inoutflow", bottom="inoutflow", top="inoutflow")
-    P = assembly.assemble_2d(16, 16, 1, bc=sides)
-    x, y = P.x
-    rho = 1.0 + 0.5 * np.exp(-40 * ((x - 0.4) ** 2 + (y - 0.5) ** 2))
-    U = workloads.prim_to_cons(rho, np.stack([np.full(P.n, 3.0), np.full(P.n, 0.5)]), np.full(P.n, 1.0), 1.4)
-    bd = workloads.prim_to_cons(np.full(P.nb, 1.0), np.stack([np.full(P.nb, 3.0), np.full(P.nb, 0.5)]),
-                                np.full(P.nb, 1.0), 1.4)
-    return P, U, np.ascontiguousarray(bd)
+    return inoutflow_case(name)
 
 
 NAMES = ["sod1d_open", "fq_q2_open_sides", "supersonic_stream", "oct_q1_3d_open"]
@@ -77,8 +58,11 @@ def test_inoutflow_stage_parity(torch_cuda, name, order):
 def test_inoutflow_fused_steps(torch_cuda, name):
     """20 fused SSP-RK3 steps with the in/outflow data: every step agrees within 3e-12 (three stages, each
     within the 1e-12 of a stage) with the oracle's step from the same state with the device's tau, and on
-    the shock tube the 20-step trajectories agree within 1e-10.  (On the nearly uniform supersonic stream the entropy-viscosity ratio N = R/D of Sec. 5.2 is
-    ill-conditioned, so two trajectories drift apart faster; the per-step agreement is the test there.)
+    the shock tube the 20-step trajectories agree within 1e-10.  The nearly uniform supersonic stream is
+    the exception: there the entropy-viscosity ratio N = R/D of Sec. 5.2 is a ratio of quantities near
+    their rounding level, and the oracle's own step moves by up to 6.6e-12 when its input changes by one
+    ulp (test_oracle_bc.py::test_supersonic_stream_conditioning), so no implementation with another
+    rounding order can be held to 3e-12 there; its bound is ILL_TOL, three times that sensitivity or more.
     Step 16 of the open-sided Q2 case holds a line search whose psi, evaluated with fused multiply-adds,
     sits below its rounding resolution near the root: it converges only because the iteration bisects
     whenever the bracket has not halved."""
@@ -93,13 +77,14 @@ def test_inoutflow_fused_steps(torch_cuda, name):
     bdd = torch.from_numpy(bd).cuda()
     work = (torch.empty_like(Ud), torch.empty_like(Ud))
     Uo = np.ascontiguousarray(U).copy()
+    tol = ILL_TOL if name == "supersonic_stream" else 3 * STAGE_TOL
     for _ in range(20):
         before = Ud.cpu().numpy()
         S.step(Ud, work, bdata=bdd)
         tau = S.clock()[1]
         one, f = O.ssprk3_step(before, tau, lambda t: bd)
         assert f == 0
-        assert rel_err(Ud.cpu().numpy(), one) <= 3 * STAGE_TOL
+        assert rel_err(Ud.cpu().numpy(), one) <= tol
         Uo, _ = O.ssprk3_step(Uo, tau, lambda t: bd)
     if name == "sod1d_open":
         assert rel_err(Ud.cpu().numpy(), Uo) <= LONG_TOL
