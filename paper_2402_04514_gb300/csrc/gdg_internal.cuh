@@ -844,6 +844,28 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
   return deps - smin * D.gamma * rg * irho * A[0];
 }
 
+// psi(s) and d psi / d s together (the two share the state, rho^gamma and 1/rho), each computed as
+// ls_psi and ls_dpsi compute it.
+template <int DIM>
+__device__ __forceinline__ double ls_psi_dpsi(const Dev& D, const double* U0, const double* A, double s, double smin,
+                                              double* dpsi) {
+  double V[DIM + 2];
+#pragma unroll
+  for (int q = 0; q < DIM + 2; ++q) V[q] = fma(s, A[q], U0[q]);
+  double mA = 0.0, m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    mA += V[1 + k] * A[1 + k];
+    m2 += V[1 + k] * V[1 + k];
+  }
+  double irho;
+  double rg = rho_pow_gamma(D, V[0], &irho);
+  double deps = A[DIM + 1] - mA * irho + 0.5 * m2 * A[0] * irho * irho;
+  *dpsi = deps - smin * D.gamma * rg * irho * A[0];
+  if (!(V[0] > 0.0)) return -1.0;
+  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
+}
+
 // Certifies psi(s) >= 0 from psi(0) and the increment dpsi = psi(s) - psi(0) evaluated in FP32 in
 // differenced form, so that its error scales with |s A| rather than with |U0|:
 //   dpsi = s A_E - dK - dG,  dK = (rho0 (2 m0.b + |b|^2) - a |m0|^2) / (2 rho0 (rho0 + a)),
@@ -935,18 +957,24 @@ __device__ double line_search_tail(const Dev& D, const LsRow<DIM>& c, const doub
   const double smin = c.smin;
   double fa = c.psi0;
   double a = 0.0, b = l;
+  // the slope at b, kept while b stays: the tangent point, which usually becomes the next b, is evaluated
+  // with its slope; a b set by the chord or the bisection takes it afresh at the next iteration
+  double dfb = 0.0;
+  bool fresh = false;
   for (int it = 0; it < D.ls_maxit && b - a > D.ls_tol; ++it) {
     const double width = b - a;
     double ts = a + (b - a) * fa / (fa - fb);
-    double dfb = w * ls_dpsi<DIM>(D, U0, A, b * w, smin);
+    if (!fresh) dfb = w * ls_dpsi<DIM>(D, U0, A, b * w, smin);
+    fresh = true;
     double tn = dfb < 0.0 ? b - fb / dfb : b;
     if (ts > a && ts < b) {
       double fs = ls_psi<DIM>(D, U0, A, ts * w, smin);
-      if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; }
+      if (fs >= 0.0) { a = ts; fa = fs; } else { b = ts; fb = fs; fresh = false; }
     }
     if (tn > a && tn < b) {
-      double fn = ls_psi<DIM>(D, U0, A, tn * w, smin);
-      if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; }
+      double dn;
+      double fn = ls_psi_dpsi<DIM>(D, U0, A, tn * w, smin, &dn);
+      if (fn >= 0.0) { a = tn; fa = fn; } else { b = tn; fb = fn; dfb = w * dn; fresh = true; }
     }
     // Near the root psi is evaluated below its rounding resolution (a change of t by an ulp leaves
     // U0 + t P unchanged), and the chord and tangent points then creep towards one end while the other
@@ -955,7 +983,7 @@ __device__ double line_search_tail(const Dev& D, const LsRow<DIM>& c, const doub
       double tm = a + 0.5 * (b - a);
       if (!(tm > a && tm < b)) break;
       double fm = ls_psi<DIM>(D, U0, A, tm * w, smin);
-      if (fm >= 0.0) { a = tm; fa = fm; } else { b = tm; fb = fm; }
+      if (fm >= 0.0) { a = tm; fa = fm; } else { b = tm; fb = fm; fresh = false; }
     }
   }
   return a;
