@@ -421,7 +421,7 @@ def main():
             step()
         torch.cuda.synchronize()
         assert solver.status() == 0, "inadmissible state or CFL violation during warm-up"
-        schedule = solver.schedule() if args.no_autotune else solver.autotune(U, work, trials=1)  # state restored
+        schedule = solver.schedule() if args.no_autotune else solver.autotune(U, work, trials=2)  # state restored
 
         sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
         barrier()
