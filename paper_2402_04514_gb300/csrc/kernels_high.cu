@@ -91,6 +91,8 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
   double Ui[M];
   R dUi[M];
   double Ni = 0.0;
+  const bool lim = D.order != GDG_ORDER_HIGH;  // the limiter's steps 3 and 4 follow the solve
+  double lo = 0.0, hi = 0.0, sl = 0.0;         // two-hop aggregates of node i (step 3)
   if (valid) {
     load_state<DIM>(U, D.n, i, Ui);
     Ni = abs_bits(S.N[i]);
@@ -103,8 +105,14 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
         rhs[q] = S.RHSL[(size_t)q * n + i];
     }
     // min / max of non-negative values on the integer pipe; every input of the loop is read-only in this
-    // kernel, so its loads take the read-only path and may move ahead of the stores of A
+    // kernel, so its loads take the read-only path and may move ahead of the stores of A.  The same pass
+    // over I(i) gathers the two-hop aggregates of the relaxed bounds (step 3).
     const int e1 = D.sten_end[i];
+    if (lim) {
+      lo = S.agg[i];
+      hi = S.agg[n + i];
+      sl = S.agg[2 * n + i];
+    }
 #pragma unroll 2
     for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
       const int j = __ldg(D.col + e);
@@ -112,6 +120,11 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
       double Uj[M];
 #pragma unroll
       for (int q = 0; q < M; ++q) Uj[q] = __ldg(U + (size_t)q * n + j);
+      if (lim) {
+        lo = pmin(lo, __ldg(S.agg + j));
+        hi = pmax(hi, __ldg(S.agg + n + j));
+        sl = pmin(sl, __ldg(S.agg + 2 * n + j));
+      }
       if constexpr (MX) {
         // d^H - d^L from FP32 operands: every factor is symmetric in (i, j), so the same bits come out
         // of row j, and A_ji = -A_ij holds exactly
@@ -139,6 +152,11 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
       }
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
+      if (lim) {
+        lo = pmin(lo, S.bbar[b]);
+        hi = pmax(hi, S.bbar[b]);
+        sl = pmin(sl, S.bbar[(size_t)D.nb + b]);
+      }
       double nv[DIM], UB[M];
 #pragma unroll
       for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
@@ -156,6 +174,17 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
     }
 #pragma unroll
     for (int q = 0; q < M; ++q) sR[q][sh] = rhs[q];
+    if (lim) {  // relaxed local bounds, read back after the solve
+      double rmin = 0.0, rmax = INFINITY, smin = 0.0;
+      if (D.bounds_mode == 0) {
+        rmin = D.rminus[i] * lo;
+        rmax = D.rplus[i] * hi;
+        smin = D.rminus[i] * sl;
+      }
+      S.bounds[i] = rmin;
+      S.bounds[n + i] = rmax;
+      S.bounds[2 * n + i] = smin;
+    }
   }
   __syncthreads();
   if (valid) {
@@ -196,33 +225,8 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
   if (D.order == GDG_ORDER_HIGH) return;
   __syncthreads();
   if (!valid) return;
-  // relaxed local bounds
-  double lo = S.agg[i], hi = S.agg[n + i], sl = S.agg[2 * n + i];
-  for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b) {
-    lo = pmin(lo, S.bbar[b]);
-    hi = pmax(hi, S.bbar[b]);
-    sl = pmin(sl, S.bbar[(size_t)D.nb + b]);
-  }
+  const double rmin = S.bounds[i], rmax = S.bounds[n + i], smin = S.bounds[2 * n + i];
   const int se = D.sten_end[i];
-  for (int e = D.row_ptr[i]; e < se; ++e) {
-    int j = D.col[e];
-    lo = pmin(lo, S.agg[j]);
-    hi = pmax(hi, S.agg[n + j]);
-    sl = pmin(sl, S.agg[2 * n + j]);
-  }
-  double rmin, rmax, smin;
-  if (D.bounds_mode == 0) {
-    rmin = D.rminus[i] * lo;
-    rmax = D.rplus[i] * hi;
-    smin = D.rminus[i] * sl;
-  } else {
-    rmin = 0.0;
-    rmax = INFINITY;
-    smin = 0.0;
-  }
-  S.bounds[i] = rmin;
-  S.bounds[n + i] = rmax;
-  S.bounds[2 * n + i] = smin;
   // antidiffusive fluxes and pass-1 line search
   double UL[M];
 #pragma unroll
