@@ -242,6 +242,63 @@ def test_full_size_bench_configuration_sampled(torch_cuda):
         assert (np.abs(got - want) <= STAGE_TOL * scale).all(), (ex, ey)
 
 
+def test_full_size_developed_state_sampled(torch_cuda):
+    """The bench workload after 40 fused SSP-RK3 steps on the autotuned schedule (as bench.py runs it):
+    the waves from the quadrant interfaces are several elements wide and the limiter is active there.  One
+    more stage at full size; elements sampled on and next to the interfaces, and at random, are checked
+    against the oracle on a 15 x 15-element patch of the GPU's own state around each of them (a dG node
+    belongs to one element, so the patch state is the full state's element blocks)."""
+    torch = torch_cuda
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Solver
+
+    N, k = 1024, 2
+    nl = (k + 1) ** 2
+    P = assembly.assemble_2d(N, N, k)
+    Ud = _dev(torch, workloads.four_quadrant(P.x[0], P.x[1], seed=0))
+    S = Solver(P)
+    S.set_clock(0.0, float("inf"), 0.5)
+    work = (torch.empty_like(Ud), torch.empty_like(Ud))
+    for _ in range(3):
+        S.step(Ud, work)
+    S.autotune(Ud, work, trials=1)
+    for _ in range(37):
+        S.step(Ud, work)
+    assert S.status() == 0
+    U = Ud.cpu().numpy()
+    tau = S.max_dt(Ud, 0.5)
+    out = S.stage(Ud, tau).cpu().numpy()
+    assert S.status() == 0
+    l1 = S.export("l1")
+    assert (l1 < 1.0).mean() > 1e-3  # the limiter is active
+    tot0, tot1 = (P.mi * U).sum(1), (P.mi * out).sum(1)
+    for c in (0, 3):
+        assert abs(tot1[c] - tot0[c]) <= 1e-12 * abs(tot0[c])
+    rng = np.random.default_rng(11)
+    samples = [(512, 512), (511, 512), (513, 509), (510, 300), (514, 800), (200, 511), (850, 514), (509, 20)]
+    samples += [tuple(rng.integers(0, N, 2)) for _ in range(3)]
+    R = 7
+    Ue = U.reshape(4, N * N, nl)
+    limited = 0
+    for ex, ey in samples:
+        ex0, ex1 = max(0, ex - R), min(N, ex + R + 1)
+        ey0, ey1 = max(0, ey - R), min(N, ey + R + 1)
+        Pp = _patch_problem(N, k, ex0, ex1, ey0, ey1)
+        Pp.omega_measure = P.omega_measure
+        elems = (np.arange(ey0, ey1)[:, None] * N + np.arange(ex0, ex1)[None, :]).ravel()
+        Up = np.ascontiguousarray(Ue[:, elems, :].reshape(4, -1))
+        ref, _, tr = Oracle(Pp).stage(Up, tau, trace=True)
+        le = (ey - ey0) * (ex1 - ex0) + (ex - ex0)
+        ge = ey * N + ex
+        got = out[:, ge * nl:(ge + 1) * nl]
+        want = ref[:, le * nl:(le + 1) * nl]
+        scale = np.abs(U).max(1, keepdims=True)
+        assert (np.abs(got - want) <= STAGE_TOL * scale).all(), (ex, ey)
+        rows = np.repeat(np.arange(Pp.n), np.diff(Pp.row_ptr))
+        limited += int((tr["l1"][(rows // nl) == le] < 1.0).any())
+    assert limited >= 3  # some samples sit where the limiter acts
+
+
 @pytest.mark.parametrize("q", [1, 3, 5, 7, 12])
 def test_fp64_helpers_against_cuda(torch_cuda, q):
     """The Newton-Raphson reciprocal and inverse root used in the sweep: the reciprocal is within 2 ulp
