@@ -48,6 +48,10 @@ MUTANTS = {
         "double R2 = vni <= 0.0 ? pi / pow(Ui[0], g) : pd / pow(Ud[0], g);"),
     "supersonic_inflow_keeps_the_interior": ("  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ud[q];",
                                              "  if (vni < -ai) {\n    for (int q = 0; q < m; ++q) UB[q] = Ui[q];"),
+    # the limiter's direction and closed form (Sec. 5.4)
+    "limiter_kappa_dropped": ("Pv[q] = Arem[q * nnz + e] / (kappa * P->mi[i]);", "Pv[q] = Arem[q * nnz + e] / P->mi[i];"),
+    "density_bound_from_the_wrong_side": ("if (U0[0] + Pv[0] > rmax) l = (rmax - U0[0]) / Pv[0];",
+                                          "if (U0[0] + Pv[0] > rmax) l = (rmin - U0[0]) / Pv[0];"),
     # dimension handling that only a 3D mesh exercises
     "flux_pressure_only_in_the_first_two_directions": (
         "for (int k = 0; k < d; ++k) out[1 + k] = U[1 + k] * vc + p * c[k];",
@@ -69,6 +73,7 @@ FAST_PINS = [
     lambda O: pins.test_limited_state_within_local_bounds(O, 2, 0.0),
     lambda O: pins.test_sod_exact_solution(O),
     lambda O: pins.test_line_search_converges_to_the_root(O),
+    lambda O: pins.test_stage_limiter_factors_by_brute_force(O),
 ]
 
 

@@ -392,3 +392,73 @@ def test_3d_limited_stage_invariants(oracle_mod):
         assert (r > 0).all() and (eps > 0).all()
         assert (r >= tr["rho_min"] * (1 - 1e-13)).all() and (r <= tr["rho_max"] * (1 + 1e-13)).all()
         assert (r ** -1.4 * eps >= tr["s_min"] * (1 - 1e-12)).all()
+
+
+def _largest_feasible(U0, Pv, rmin, rmax, smin, g):
+    """Brute force for the pass-1 factor of Sec. 5.4: the largest l in [0, 1] with U0 + l Pv in B_i
+    (rmin <= rho <= rmax and eps - smin rho^g >= 0), by bisection on that predicate in long double (B_i is
+    convex, so its feasible l form an interval that holds 0 when U0 is in B_i; 0 when it is not)."""
+    ld = np.longdouble
+    U0 = np.asarray(U0, ld)
+    Pv = np.asarray(Pv, ld)
+    d = len(U0) - 2
+
+    def ok(t):
+        V = U0 + ld(t) * Pv
+        rho = V[0]
+        if not (rho > 0) or rho < ld(rmin) or rho > ld(rmax):
+            return False
+        eps = V[-1] - (V[1:1 + d] ** 2).sum() / (2 * rho)
+        return eps - ld(smin) * rho ** ld(g) >= 0
+
+    if not ok(0.0):
+        return 0.0
+    if ok(1.0):
+        return 1.0
+    lo, hi = ld(0.0), ld(1.0)
+    for _ in range(70):
+        mid = (lo + hi) / 2
+        if ok(mid):
+            lo = mid
+        else:
+            hi = mid
+    return float(lo)
+
+
+def test_stage_limiter_factors_by_brute_force(oracle_mod):
+    """The pass-1 limiter factors of one limited stage on a small shocked mesh (2D Q1, 6 x 6 elements,
+    four-quadrant data after two steps, slip walls), for every CSR and boundary entry, against a
+    brute-force bisection of the set B_i of Sec. 5.4 from the stage's own U^L, A_ij and bounds, with
+    P = A_ij / (kappa_i m_i): l_ij = min(l*_ij from row i, l*_ji from row j) (Lemma ConsInvariants), and
+    boundary entries unsymmetrised.  Compared through their effect on the state,
+    |l - l*| |P| <= 1e-12 |U0|: where |P| is far below |U0| the root is only defined to the rounding of
+    U0 + l P."""
+    g = 1.4
+    P, U = four_quadrant_problem(6, 1, seed=0)
+    O = oracle_mod.Oracle(P)
+    for _ in range(2):
+        U, _ = O.ssprk3_step(U, O.max_dt(U, 0.5))
+    _, flags, tr = O.stage(U, O.max_dt(U, 0.5), trace=True)
+    assert flags == 0
+    n = P.n
+    tmap, rows = transpose_map(P)
+    terms = np.diff(P.row_ptr) + np.bincount(P.b_node, minlength=n)
+    w = terms / P.mi
+
+    def raw(i, Pv):
+        U0 = tr["UL"][:, i]
+        return _largest_feasible(U0, Pv, tr["rho_min"][i], tr["rho_max"][i], tr["s_min"][i], g)
+
+    lraw = np.array([raw(i, w[i] * tr["A"][:, e]) for e, i in enumerate(rows)])
+    limited = 0
+    for e, i in enumerate(rows):
+        want = min(lraw[e], lraw[tmap[e]])
+        got = tr["l1"][e]
+        scale = max(np.abs(w[i] * tr["A"][:, e]).max(), np.abs(w[rows[tmap[e]]] * tr["A"][:, tmap[e]]).max())
+        assert abs(got - want) * scale <= 1e-12 * np.abs(tr["UL"]).max(), (e, got, want)
+        limited += want < 1.0
+    for b, i in enumerate(P.b_node):
+        Pv = w[i] * tr["AB"][:, b]
+        want, got = raw(i, Pv), tr["l1B"][b]
+        assert abs(got - want) * np.abs(Pv).max() <= 1e-12 * np.abs(tr["UL"]).max(), (b, got, want)
+    assert limited > 20  # the limiter acts on this stage
