@@ -74,6 +74,7 @@ FAST_PINS = [
     lambda O: pins.test_sod_exact_solution(O),
     lambda O: pins.test_line_search_converges_to_the_root(O),
     lambda O: pins.test_stage_limiter_factors_by_brute_force(O),
+    lambda O: pins.test_viscosity_and_time_step_of_a_uniform_flow(O),
 ]
 
 

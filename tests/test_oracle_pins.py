@@ -70,6 +70,34 @@ def test_constant_state_preserved(oracle_mod):
             assert rel_err(U1, U) < 1e-14
 
 
+def test_viscosity_and_time_step_of_a_uniform_flow(oracle_mod):
+    """For one state everywhere the projected Riemann problem along n has no waves but the state's own, so
+    its largest wave speed is |v.n| + a, and the bound of Sec. 3.1 must reach it exactly: every stencil
+    entry of the traced d^L equals |c_ij| (|v.n_ij| + a), by hand from the assembled c_ij; d_ii is minus the
+    row sum (eq:dij_low_order_supplement; periodic mesh, no boundary terms), and the time step of Sec. 3.3 is
+    Cr min_i m_i / (2 |d_ii|)."""
+    g = 1.4
+    rho, v, p = 1.3, np.array([0.4, -0.7]), 2.1
+    a = math.sqrt(g * p / rho)
+    for k in (1, 2):
+        P, _ = periodic_vortex_problem(4, k)
+        U = workloads.prim_to_cons(np.full(P.n, rho), np.stack([np.full(P.n, v[0]), np.full(P.n, v[1])]),
+                                   np.full(P.n, p), g)
+        O = oracle_mod.Oracle(P, params=dict(order=oracle_mod.LOW))
+        tau = O.max_dt(U, 0.5)
+        _, flags, tr = O.stage(U, tau, trace=True)
+        assert flags == 0
+        c = P.cij
+        cn = np.sqrt((c * c).sum(0))
+        st = cn > 0
+        want = np.zeros_like(cn)
+        want[st] = cn[st] * (np.abs(v @ (c[:, st] / cn[st])) + a)
+        assert np.allclose(tr["dL"], want, rtol=1e-13, atol=0.0)
+        rows = np.repeat(np.arange(P.n), np.diff(P.row_ptr))
+        assert np.allclose(tr["dii"], -np.bincount(rows, weights=want, minlength=P.n), rtol=1e-13, atol=0.0)
+        assert abs(tau - 0.5 * (P.mi / (2.0 * np.bincount(rows, weights=want, minlength=P.n))).min()) <= 1e-13 * tau
+
+
 def _fq(order, k=2, ne=4, seed=3, passes=2, bounds_mode=0, **extra):
     from oracle import oracle as om
     P, U = four_quadrant_problem(ne, k, seed=seed)
