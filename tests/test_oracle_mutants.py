@@ -39,6 +39,7 @@ MUTANTS = {
     "ev_uses_only_own_residual": ("fmin(P->c_ev * fmax(fabs(N[i]), fabs(N[j])), 1.0);",
                                   "fmin(P->c_ev * fabs(N[i]), 1.0);"),
     "entropy_gradient_sign": ("grad[d + 1] = pref * ((g - 1.0) / pi);", "grad[d + 1] = -pref * ((g - 1.0) / pi);"),
+    "entropy_flux_difference_reversed": ("psum += dot(Uj + 1, c, d) * (fj - fi);", "psum += dot(Uj + 1, c, d) * (fi - fj);"),
     "bounds_skip_bar_states": ("lo = fmin(lo, fmin(Uk[0], Ubk[0]));", "lo = fmin(lo, Uk[0]);"),
     # in/outflow boundary state (Sec. 4.1)
     "inoutflow_incoming_riemann_invariant_from_interior": ("double R1 = vnd - 2.0 * ad / (g - 1.0);",
@@ -75,6 +76,7 @@ FAST_PINS = [
     lambda O: pins.test_line_search_converges_to_the_root(O),
     lambda O: pins.test_stage_limiter_factors_by_brute_force(O),
     lambda O: pins.test_viscosity_and_time_step_of_a_uniform_flow(O),
+    lambda O: pins.test_entropy_indicator_vanishes_in_smooth_flow(O),
 ]
 
 

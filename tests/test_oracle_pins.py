@@ -98,6 +98,22 @@ def test_viscosity_and_time_step_of_a_uniform_flow(oracle_mod):
         assert abs(tau - 0.5 * (P.mi / (2.0 * np.bincount(rows, weights=want, minlength=P.n))).min()) <= 1e-13 * tau
 
 
+def test_entropy_indicator_vanishes_in_smooth_flow(oracle_mod):
+    """The entropy-viscosity indicator N_i = R_i / D_i of Sec. 5.2 measures the entropy residual, which is
+    a truncation error where the flow is smooth: on the isentropic vortex its mean |N| falls by about 2^k
+    per halving of h (about 1.6-1.9x for Q1, 3.1-4.5x for Q2 seen), so that the high-order viscosity
+    vanishes there.  A term of R or D dropped or of the wrong sign leaves N of order one."""
+    for k, rate in ((1, 1.4), (2, 2.5)):
+        means = []
+        for ne in (16, 32, 64):
+            P, U = periodic_vortex_problem(ne, k)
+            O = oracle_mod.Oracle(P)
+            _, flags, tr = O.stage(U, O.max_dt(U, 0.5), trace=True)
+            assert flags == 0
+            means.append(np.abs(tr["N"]).mean())
+        assert means[0] / means[1] > rate and means[1] / means[2] > rate, (k, means)
+
+
 def _fq(order, k=2, ne=4, seed=3, passes=2, bounds_mode=0, **extra):
     from oracle import oracle as om
     P, U = four_quadrant_problem(ne, k, seed=seed)
