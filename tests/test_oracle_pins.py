@@ -304,6 +304,16 @@ def test_isentropic_vortex_against_paper_tables(oracle_mod):
     assert 0.5 < f[1] / fo[1][0] < 1.0  # same order of magnitude; see the design doc on the wave-speed bound
 
 
+def test_vortex_convergence_rate_limited_q1(oracle_mod):
+    """Convergence of the limited scheme on the isentropic vortex (Sec. 6.2, test case (i)): from 2304 to
+    9216 Q1 DoFs (h halved) the L1 error falls by the factor of the paper's table (3.10, Appendix A,
+    Table ErrorIsentropicConvex) within 20%: second order, with the limiter active at the vortex core."""
+    tab = load_vortex_tables()
+    want = tab["limited"][1][0] / tab["limited"][1][1]
+    got = _vortex_error(oracle_mod, 24, 1, oracle_mod.LIMITED) / _vortex_error(oracle_mod, 48, 1, oracle_mod.LIMITED)
+    assert abs(got / want - 1.0) < 0.2, (got, want)
+
+
 def test_vortex_is_a_steady_solution_in_its_frame():
     """The generator's vortex satisfies radial equilibrium dp/dr = rho v_theta^2 / r (the fix of the
     printed formula) and p = rho^gamma (isentropic)."""
