@@ -123,8 +123,3 @@ def measured_traffic(path: str, kernel: str, n_nodes: int, precision: str = "fp6
         if len(f) in (5, 6) and f[0] == kernel and f[4] == digest and (f[5] if len(f) == 6 else "fp64") == precision:
             return (float(f[2]) + float(f[3])) * n_nodes / float(f[1])
     return None
-    digest = library_source_digest()
-    for f in lines:
-        if len(f) == 5 and f[0] == kernel and f[4] == digest:
-            return (float(f[2]) + float(f[3])) * n_nodes / float(f[1])
-    return None
