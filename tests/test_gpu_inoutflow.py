@@ -5,7 +5,6 @@ octant problem with three open sides."""
 import numpy as np
 import pytest
 
-from paper_2402_04514_gb300 import assembly, workloads
 from tests.helpers import inoutflow_case, rel_err
 
 pytestmark = pytest.mark.gpu
