@@ -107,6 +107,33 @@ def test_batch_equals_each_member_alone(torch_cuda, degree):
         assert S.status() == 0
 
 
+@pytest.mark.parametrize("degree", [1, 2])
+def test_batch_of_3d_members(torch_cuda, degree):
+    """Hexahedral members of ragged sizes (eight-octant data, slip walls), one reaching its end time inside
+    the run: the same bits and clocks as alone."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import Solver
+    from tests.helpers import octant_problem
+
+    members = []
+    for shape, seed, f in (((5, 4, 3), 1, np.inf), ((2, 2, 2), 2, np.inf), ((6, 3, 4), 3, 1.5)):
+        P, U = octant_problem(shape, degree, seed=seed)
+        S = Solver(P)
+        U = np.ascontiguousarray(U)
+        t_end = np.inf if not np.isfinite(f) else f * S.max_dt(torch.from_numpy(U).cuda(), 0.5)
+        members.append((S, U, t_end))
+    steps = 4
+    alone = _run_alone(torch, members, steps)
+    got = _run_batch(torch, members, steps, [2, 0, 1])
+    for i, (U_a, clk_a) in enumerate(alone):
+        U_b, clk_b = got[i]
+        assert np.array_equal(U_a, U_b), i
+        assert clk_a == clk_b, (i, clk_a, clk_b)
+    assert alone[2][1][2] < steps  # the third member stopped at its end time
+    for S, _, _ in members:
+        assert S.status() == 0
+
+
 def test_batch_with_dirichlet_members(torch_cuda):
     """Members with Dirichlet boundary data (time-independent here) next to slip-wall members."""
     torch = torch_cuda
