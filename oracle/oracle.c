@@ -13,9 +13,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXM 5
 #define MAXNL 32 /* nodes per element (Q2 in 3D has 27); the Python wrapper rejects more */
+
+/* The row loops carry ORC_PARALLEL_* markers.  They are empty in the default build, the one the tests pin.
+ * Built with -fopenmp (the multi-core timing build of the CPU baseline) they share the rows of a loop
+ * among threads; every row writes only its own entries, so both builds give bit-identical results. */
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PARALLEL_FOR ORC_PRAGMA(omp parallel for schedule(dynamic, 1024))
+#define ORC_PARALLEL_PRIVATE(...) ORC_PRAGMA(omp parallel for schedule(dynamic, 1024) private(__VA_ARGS__))
+#else
+#define ORC_PARALLEL_FOR
+#define ORC_PARALLEL_PRIVATE(...)
+#endif
 
 static double dot(const double* a, const double* b, int d) {
   double s = 0.0;
@@ -193,6 +208,7 @@ static void low_order_viscosities(const orc_problem* P, const double* U, const d
   int d = P->dim, m = d + 2;
   long n = P->n;
   double Ui[MAXM], Uj[MAXM], Ub[MAXM], c[3], nrm[3];
+  ORC_PARALLEL_PRIVATE(Ui, Uj, Ub, c, nrm)
   for (long i = 0; i < n; ++i) {
     gather(U, n, i, m, Ui);
     dii[i] = 0.0;
@@ -306,6 +322,14 @@ static double line_search(const double* U0, const double* Pv, double rmin, doubl
   return a;
 }
 
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 double orc_line_search(const double* U0, const double* Pv, double rmin, double rmax, double smin, int d,
                        double g, double tol, int maxit) {
   return line_search(U0, Pv, rmin, rmax, smin, d, g, tol, maxit);
@@ -377,6 +401,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
   /* ---- low-order update: Sec. 4.2, eq. (cijdijschememodified), i.e. Sec. 3.1, eq. (cijdijscheme)
    * with one boundary term per boundary part ---- */
   ALLOC(UL, m * n);
+  ORC_PARALLEL_PRIVATE(Ui, Uj, Ub, c, nrm, fv)
   for (long i = 0; i < n; ++i) {
     double acc[MAXM] = {0};
     gather(Uin, n, i, m, Ui);
@@ -399,6 +424,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
 
   /* bar states for the trace and the local bounds */
   ALLOC(ubar, m * nnz); ALLOC(ubarB, m * nb);
+  ORC_PARALLEL_PRIVATE(Ui, Uj, c, nrm)
   for (long i = 0; i < n; ++i) {
     gather(Uin, n, i, m, Ui);
     for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) {
@@ -435,6 +461,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
      * evaluated as sum_j (f_k(U_j) - f_k(U_i)) c_ij - f_k(U_i) sum_k c_i^{d,k}, equal by the partition
      * of unity (Lemma LemPart): a node whose stencil holds a single state then gets R_i = D_i = 0
      * exactly instead of a ratio of rounding errors. */
+    ORC_PARALLEL_PRIVATE(Ui, Uj, c, nrm, fv)
     for (long i = 0; i < n; ++i) {
       gather(Uin, n, i, m, Ui);
       double pi = pressure(Ui, d, g);
@@ -473,6 +500,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
 
     /* ---- high-order viscosity: Sec. 5, eq. (HighOrderViscosity), d^H = max(d^min, d^ev), with
      * Sec. 5.1, eq. (ViscMin), and d^ev of Sec. 5.2 ---- */
+    ORC_PARALLEL_FOR
     for (long i = 0; i < n; ++i) {
       for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) {
         long j = P->col_idx[e];
@@ -497,6 +525,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
 
     /* ---- high-order update, Sec. 5, eq. (HighScheme): sum_j m_ij (U_j^H - U_j)/tau + RHS_i^H = 0 ---- */
     ALLOC(rhs, m * n);
+    ORC_PARALLEL_PRIVATE(Ui, Uj, Ub, c, nrm, fv)
     for (long i = 0; i < n; ++i) {
       gather(Uin, n, i, m, Ui);
       double acc[MAXM] = {0};
@@ -516,6 +545,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
       for (int q = 0; q < m; ++q) rhs[q * n + i] = acc[q];
     }
     double Bblk[MAXNL * MAXM];
+    ORC_PARALLEL_PRIVATE(Bblk)
     for (long K = 0; K < n / nl; ++K) {
       for (int a = 0; a < nl; ++a)
         for (int q = 0; q < m; ++q) Bblk[a * m + q] = -tau * rhs[q * n + K * nl + a];
@@ -536,6 +566,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
      * h_i = (m_i / |Omega|)^{1/d} ----
      * Reading: the outer minimum runs over I(i) and i itself, the inner one over I(j) and j itself;
      * only node i's own boundary bar states enter. */
+    ORC_PARALLEL_PRIVATE(Uj, Ub, c, nrm)
     for (long i = 0; i < n; ++i) {
       double lo = INFINITY, hi = -INFINITY, sl = INFINITY;
       for (long t = bptr[i]; t < bptr[i + 1]; ++t) {
@@ -576,6 +607,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
      * eq. (skewSymmetric) and eq. (HighSchemeAlgebraic):
      *   A_ij = tau (d_ij^H - d_ij^L)(U_j - U_i) - (m_ij - delta_ij m_i)(dU_j^H - dU_i^H),
      *   A_i^{d,k} = tau (d^{d,H} - d^{d,L})(U^{d,k} - U_i). ---- */
+    ORC_PARALLEL_FOR
     for (long i = 0; i < n; ++i) {
       long K = i / nl;
       for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e) {
@@ -607,6 +639,7 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
     for (int pass = 0; pass < P->limiter_passes; ++pass) {
       double* lsym = pass == 0 ? l1 : l2;
       double* lsymB = pass == 0 ? l1B : l2B;
+      ORC_PARALLEL_FOR
       for (long i = 0; i < n; ++i) {
         long nterms = (P->row_ptr[i + 1] - P->row_ptr[i]) + (bptr[i + 1] - bptr[i]);
         double kappa = 1.0 / (double)nterms;
@@ -622,10 +655,12 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
           lrawB[b] = line_search(U0, Pv, rmin[i], rmax[i], smin[i], d, g, P->ls_tol, P->ls_maxit);
         }
       }
+      ORC_PARALLEL_FOR
       for (long i = 0; i < n; ++i)
         for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e)
           lsym[e] = fmin(lraw[e], lraw[transpose_entry(P, i, P->col_idx[e])]);
       memcpy(lsymB, lrawB, sizeof(double) * nb);
+      ORC_PARALLEL_FOR
       for (long i = 0; i < n; ++i) {
         double acc[MAXM] = {0};
         for (long e = P->row_ptr[i]; e < P->row_ptr[i + 1]; ++e)

@@ -65,6 +65,8 @@ typedef struct {
   double* U1;    /* [m][n] state after pass 1 */
 } orc_trace;
 
+/* Threads a stage's row loops use: 1 in the default build, OpenMP's thread count in the -fopenmp build. */
+int orc_threads(void);
 /* Upper bound on the maximum wave speed of the 1D Riemann problem (U_L, U_R) along unit n. */
 double orc_lambda_max(const double* UL, const double* UR, const double* nrm, int dim, double gamma);
 /* The line search of the limiter (Sec. 5.4): the largest l in [0, 1] with U0 + l Pv inside the bounds

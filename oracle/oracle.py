@@ -15,23 +15,27 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
+LIB_OMP = os.path.join(BUILD, "liboracle_omp.so")  # the same source with its row loops shared by OpenMP
 
 LOW, HIGH, LIMITED = 0, 1, 2
 F_INADMISSIBLE, F_CFL = 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (-O2, no FP contraction, so the C arithmetic is evaluated as written)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c with gcc (-O2, no FP contraction, so the C arithmetic is evaluated as written).
+    openmp=True builds the multi-core variant used only to time the CPU baseline: the same loops with their
+    rows shared among threads, bit-identical results."""
     src = os.path.join(HERE, "oracle.c")
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+    lib_path = LIB_OMP if openmp else LIB
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
-        return LIB
+        return lib_path
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", src, "-o", tmp,
-                           "-lm"])
-    os.replace(tmp, LIB)
-    return LIB
+    tmp = lib_path + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", *(["-fopenmp"] if openmp else []),
+                           "-fPIC", "-shared", src, "-o", tmp, "-lm"])
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class _Problem(C.Structure):
@@ -55,13 +59,14 @@ class _Trace(C.Structure):
     _fields_ = [(f, C.c_void_p) for f in _TRACE_FIELDS]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(openmp: bool = False):
+    L = _libs.get(openmp)
+    if L is None:
+        L = C.CDLL(build(openmp=openmp))
+        L.orc_threads.restype = C.c_int
         L.orc_inoutflow_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         L.orc_line_search.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
                                       C.c_double, C.c_double, C.c_int]
@@ -74,8 +79,13 @@ def lib():
         L.orc_stage.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                 C.c_void_p, C.c_void_p, C.POINTER(_Trace)]
         L.orc_stage.restype = C.c_int
-        _lib = L
-    return _lib
+        _libs[openmp] = L
+    return L
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads the stage's row loops use in that build (1 without OpenMP)."""
+    return lib(openmp).orc_threads()
 
 
 def default_params(degree: int) -> dict:
@@ -98,6 +108,7 @@ class Oracle:
     problem: object
     gamma: float = 1.4
     params: dict = None
+    openmp: bool = False  # the multi-core timing build (same results)
 
     def __post_init__(self):
         P = self.problem
@@ -138,7 +149,7 @@ class Oracle:
         U = np.ascontiguousarray(U, np.float64)
         bd = self._bdata(bdata)
         tau = C.c_double()
-        lib().orc_max_dt(C.byref(self._c), _p(U), _p(bd), cfl, C.byref(tau))
+        lib(self.openmp).orc_max_dt(C.byref(self._c), _p(U), _p(bd), cfl, C.byref(tau))
         return tau.value
 
     def stage(self, U_in, tau, U_base=None, alpha=0.0, bdata=None, trace=False):
@@ -156,7 +167,7 @@ class Oracle:
                           rho_max=(n,), s_min=(n,), l1=(nnz,), l1B=(nb,), l2=(nnz,), l2B=(nb,), U1=(m, n))
             arrays = {f: np.zeros(shapes[f]) for f in _TRACE_FIELDS}
             tr = _Trace(*[_p(arrays[f]) for f in _TRACE_FIELDS])
-        flags = lib().orc_stage(C.byref(self._c), _p(U_in), _p(ub), alpha, tau, _p(bd), _p(out),
+        flags = lib(self.openmp).orc_stage(C.byref(self._c), _p(U_in), _p(ub), alpha, tau, _p(bd), _p(out),
                                 C.byref(tr) if tr is not None else None)
         if trace:
             return out, flags, arrays

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2402_04514_gb300 import assembly, workloads
-from tests.helpers import four_quadrant_problem, periodic_vortex_problem, rel_err
+from tests.helpers import four_quadrant_problem, octant_problem, periodic_vortex_problem, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,7 @@ def torch_cuda():
 
 CASES = {
     "sod1d_q1": lambda: (assembly.assemble_1d(200, 1), None),
+    "oct_q1_3d": lambda: octant_problem((7, 6, 5), 1, seed=1),
     "vortex_q1_periodic": lambda: periodic_vortex_problem(17, 1),
     "fq_q2_slip": lambda: four_quadrant_problem(13, 2, seed=0),
     "fq_q1_slip": lambda: four_quadrant_problem(19, 1, seed=4),
@@ -139,9 +140,8 @@ def test_stage_in_place_on_its_base(torch_cuda):
 def test_ssprk54_step_matches_oracle(torch_cuda, name):
     """gdg_ssprk54_step against the oracle's SSPRK(5,4) step (oracle/ssprk.py) taken with the dt the device
     chose: dt = cfl * C * the forward-Euler bound (C = 1.508) to 1e-12, the state within 1e-12 relative
-    after one step; after 30 steps within 1e-10 on the cases of the 100-step SSPRK3 test (on strongly
-    shocked Q2 data a limiter decision can flip on a last-bit difference and the two sides then differ by
-    ~1e-11 to 1e-10 for some steps, as with SSPRK3)."""
+    after one step; after 30 steps within 1e-10 on the cases of the 100-step SSPRK3 test (the 100-step
+    runs of both integrators on Q2, Q3 and 3D meshes follow below)."""
     torch = torch_cuda
     from oracle import ssprk
 
@@ -171,6 +171,39 @@ def test_ssprk54_step_matches_oracle(torch_cuda, name):
             assert rel_err(Ud.cpu().numpy(), Uo) <= STAGE_TOL
     got = Ud.cpu().numpy()
     assert rel_err(got, Uo) <= (LONG_TOL if long_run else STAGE_TOL)
+    rho = got[0]
+    eps = got[-1] - 0.5 * (got[1:-1] ** 2).sum(0) / rho
+    assert (rho > 0).all() and (eps > 0).all()
+    assert S.status() == 0
+
+
+@pytest.mark.parametrize("integrator", ["ssprk3", "ssprk54"])
+@pytest.mark.parametrize("name", ["fq_q2_slip", "fq_q3_slip", "oct_q1_3d"])
+def test_hundred_steps_q2_q3_3d(torch_cuda, name, integrator):
+    """100 fused steps of the limited scheme on shocked data with Q2 (the degree of the 1024^2 bench
+    workload, here 13^2 elements), Q3 (7^2) and 3D hexahedral Q1 (7 x 6 x 5), with either integrator; the
+    oracle steps with the dt the device chose.  The whole trajectory stays within 1e-10 of the oracle's
+    (per component, relative to max |U|); every state admissible; no flag raised."""
+    torch = torch_cuda
+    P, U, S, O, Ud, work = _setup(torch, name)
+    if integrator == "ssprk54":
+        work = (work[0], work[1], torch.empty_like(Ud))
+    Uo = U.copy()
+    worst = 0.0
+    for it in range(100):
+        S.step(Ud, work)
+        _, dt, steps = S.clock()
+        assert steps == it + 1
+        if integrator == "ssprk3":
+            Uo, flags = O.ssprk3_step(Uo, dt)
+        else:
+            Uo, flags = O.ssprk54_step(Uo, dt)
+        assert flags == 0
+        if it % 10 == 9:
+            worst = max(worst, rel_err(Ud.cpu().numpy(), Uo))
+    got = Ud.cpu().numpy()
+    worst = max(worst, rel_err(got, Uo))
+    assert worst <= LONG_TOL, worst
     rho = got[0]
     eps = got[-1] - 0.5 * (got[1:-1] ** 2).sum(0) / rho
     assert (rho > 0).all() and (eps > 0).all()

@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes: each mutant below is a copy of oracle.c with one planted error (a
 dropped term, a flipped sign, a swapped operand or index), compiled on the CPU; the pins of
-test_oracle_pins.py must reject every mutant.  The real oracle is untouched."""
+test_oracle_pins.py, test_oracle_hand.py and test_oracle_bc.py must reject every mutant.  The real oracle is untouched."""
 import os
 import subprocess
 import tempfile
@@ -9,6 +9,7 @@ import pytest
 
 from oracle import oracle as om
 from tests import test_oracle_bc as bc
+from tests import test_oracle_hand as hand
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(om.__file__), "oracle.c")
@@ -53,6 +54,20 @@ MUTANTS = {
     "limiter_kappa_dropped": ("Pv[q] = Arem[q * nnz + e] / (kappa * P->mi[i]);", "Pv[q] = Arem[q * nnz + e] / P->mi[i];"),
     "density_bound_from_the_wrong_side": ("if (U0[0] + Pv[0] > rmax) l = (rmax - U0[0]) / Pv[0];",
                                           "if (U0[0] + Pv[0] > rmax) l = (rmin - U0[0]) / Pv[0];"),
+    # the relaxed local bounds (Sec. 5.4, eq. (eq:local_bounds), (ViscMinConst2))
+    "bounds_upper_relaxation_doubled": ("double rm = 1.0 - P->c_r * hh, rp = 1.0 + P->c_r * hh;",
+                                        "double rm = 1.0 - P->c_r * hh, rp = 1.0 + 2.0 * P->c_r * hh;"),
+    "bounds_one_hop_only": ("for (long ek = P->row_ptr[j]; ek < P->row_ptr[j + 1]; ++ek) {",
+                            "for (long ek = P->row_ptr[j]; ek < P->row_ptr[j + 1] && j == i; ++ek) {"),
+    "bounds_mesh_size_without_the_dimension_root": ("double hh = pow(pow(P->mi[i] / P->omega, 1.0 / d), P->p_r);",
+                                                    "double hh = pow(P->mi[i] / P->omega, P->p_r);"),
+    # the minimal and boundary high-order viscosities (Sec. 5.1, eq. (ViscMin); the boundary reading)
+    "minimal_viscosity_power_dropped": ("dmin = P->c_k * pow(hij, P->p_k) * dL[e];", "dmin = P->c_k * dL[e];"),
+    "minimal_viscosity_mesh_size_of_the_row_node": (
+        "double hij = pow(0.5 * (P->mi[i] + P->mi[j]) / P->omega, 1.0 / d);",
+        "double hij = pow(P->mi[i] / P->omega, 1.0 / d);"),
+    "boundary_high_order_viscosity_is_the_low_order_one": (
+        "dBH[b] = fmax(P->c_k * pow(hi, P->p_k), fmin(P->c_ev * fabs(N[i]), 1.0)) * dB[b];", "dBH[b] = dB[b];"),
     # dimension handling that only a 3D mesh exercises
     "flux_pressure_only_in_the_first_two_directions": (
         "for (int k = 0; k < d; ++k) out[1 + k] = U[1 + k] * vc + p * c[k];",
@@ -77,6 +92,8 @@ FAST_PINS = [
     lambda O: pins.test_stage_limiter_factors_by_brute_force(O),
     lambda O: pins.test_viscosity_and_time_step_of_a_uniform_flow(O),
     lambda O: pins.test_entropy_indicator_vanishes_in_smooth_flow(O),
+    lambda O: [hand.test_relaxed_local_bounds_by_hand(O, c) for c in range(len(hand.CASES))],
+    lambda O: [hand.test_high_order_viscosity_by_hand(O, c) for c in range(len(hand.CASES))],
 ]
 
 
@@ -110,8 +127,8 @@ def test_pins_reject_mutant(name, monkeypatch):
         subprocess.check_call(["cp", os.path.join(os.path.dirname(SRC), "oracle.h"), d])
         so = os.path.join(d, "liboracle_mutant.so")
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", c, "-o", so, "-lm"])
-        monkeypatch.setattr(om, "_lib", None)
-        monkeypatch.setattr(om, "build", lambda force=False: so)
+        monkeypatch.setattr(om, "_libs", {})
+        monkeypatch.setattr(om, "build", lambda force=False, openmp=False: so)
         caught = []
         for pin in FAST_PINS + BC_PINS + DIM3_PINS + [_vortex_q1_limited]:
             try:
