@@ -11,7 +11,11 @@ L2, so no flush is needed between steps.
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own instance (replicas: the path has no
 exchange step); value = all ranks' DoF-stage updates / max over ranks of the timed region.
---impl reference times the FP64 CPU oracle on the host cores (rank 0 only) on a bounded sample of the
+At N = 1 the line also carries samples of the batched workload (the first 128 of its 512 seeded Q1
+instances: batched solves/s against one at a time) and of the served workload (48 Poisson-arrival Q1/Q2
+requests with meshes up to 256^2 and end times capped at 0.01: solves/s and p50/p99 time-to-solution
+against one at a time); --workload batched_q1_riemann / served_stream run either at any size.
+--impl reference times the FP64 CPU oracle on all host cores (rank 0 only) on a bounded sample of the
 same workload (the same four-quadrant data on a 128 x 128 Q2 mesh).
 """
 from __future__ import annotations
@@ -35,6 +39,9 @@ WORKLOADS = {
 }
 SAMPLE_N = 128  # oracle sample: same data on a 128 x 128 mesh
 SOLVE_STEPS = 50  # a batched solve: 50 SSP-RK3 steps of one instance
+# samples of the batched and served workloads that the default run reports beside the main line
+COMBINED_BATCH_INSTANCES = 128
+COMBINED_SERVED = dict(requests=48, rate=20.0, n_max=256, t_cap=0.01)
 
 
 def make_problem(spec):
@@ -104,13 +111,15 @@ def whole_job_rate(world, units_per_rank, ms_max):
     return world * units_per_rank / (ms_max / 1e3)
 
 
-def oracle_sample_rate(steps, warmup=0, log=None):
-    """DoF-stage updates/s of the CPU oracle (single thread) on the 128^2 sample; returns (value, seconds)."""
-    from oracle.oracle import Oracle
+def oracle_sample_rate(steps, warmup=0, openmp=False):
+    """DoF-stage updates/s of the CPU oracle on the 128^2 sample: the pinned single-thread build, or with
+    openmp=True the same code with its row loops shared among all host cores (bit-identical results).
+    Returns (value, seconds, nodes, threads)."""
+    from oracle import oracle as om
 
     spec = dict(WORKLOADS["q2_1024_four_quadrant"], N=SAMPLE_N)
     P, U = make_problem(spec)
-    O = Oracle(P)
+    O = om.Oracle(P, openmp=openmp)
     for _ in range(warmup):
         tau = O.max_dt(U, 0.5)
         U, _ = O.ssprk3_step(U, tau)
@@ -119,21 +128,36 @@ def oracle_sample_rate(steps, warmup=0, log=None):
         tau = O.max_dt(U, 0.5)
         U, _ = O.ssprk3_step(U, tau)
     dt = time.perf_counter() - t0
-    return P.n * 3 * steps / dt, dt, P.n
+    return P.n * 3 * steps / dt, dt, P.n, om.threads(openmp)
+
+
+def oracle_full_size_rate(P, U, steps):
+    """The all-core oracle on the full bench mesh itself for a few SSP-RK3 steps (the time step from the
+    oracle's own max_dt): its DoF-stage rate, which extrapolates per stage to any number of steps.
+    Returns (value, seconds, threads)."""
+    from oracle import oracle as om
+
+    O = om.Oracle(P, openmp=True)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, _ = O.ssprk3_step(U, O.max_dt(U, 0.5))
+    dt = time.perf_counter() - t0
+    return P.n * 3 * steps / dt, dt, om.threads(True)
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    value, secs, n_s = oracle_sample_rate(args.steps, args.warmup)
+    value, secs, n_s, threads = oracle_sample_rate(args.steps, args.warmup, openmp=True)
     sample = (f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.steps} SSP-RK3 steps after "
-              f"{args.warmup} warm-up steps, single thread, {secs:.1f} s")
+              f"{args.warmup} warm-up steps, {threads} threads (the oracle's row loops shared by OpenMP), "
+              f"{secs:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(args, None),
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -155,19 +179,20 @@ def c4_instances(count, seed=1):
         yield N, P, workloads.two_state_riemann(P.x[0], P.x[1], rng)
 
 
-def run_batched(args):
+def measure_batched(instances, steps, warmup, autotune=True):
     """Batched solves: one gdg_batch_step advances every instance by one SSP-RK3 step in shared launches;
     against the same instances stepped one at a time (gdg_ssprk3_step per instance, in turn, on one
     stream).  A solve is SOLVE_STEPS steps of one instance; solves/s = instances x timed steps /
-    SOLVE_STEPS / time."""
+    SOLVE_STEPS / time.  `instances` takes the first instances of the seeded 512-instance stream."""
     import torch
 
     from paper_2402_04514_gb300.gdg import Batch, Solver
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     solvers, states, works, sizes = [], [], [], []
     t0 = time.perf_counter()
-    for N, P, U in c4_instances(args.instances):
+    stream_ = c4_instances(512)
+    for _ in range(instances):
+        N, P, U = next(stream_)
         S = Solver(P)
         S.set_clock(0.0, float("inf"), 0.5)
         Ud = torch.from_numpy(U).cuda()
@@ -180,11 +205,11 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     dofs = sum(sizes)
 
-    def timed(fn, steps):
+    def timed(fn, k):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(k):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -194,40 +219,56 @@ def run_batched(args):
         for S, U, w in zip(solvers, states, works):
             S.step(U, w)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         B.step()
         one_at_a_time()
-    schedule = B.schedule() if args.no_autotune else B.autotune(trials=1)  # states restored
+    schedule = B.autotune(trials=1) if autotune else B.schedule()  # states restored
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    t_batch = timed(B.step, args.steps)
-    t_single = timed(one_at_a_time, args.steps)
+    t_batch = timed(B.step, steps)
+    t_single = timed(one_at_a_time, steps)
     clocks = sampler.stop()
     flags = max(S.status() for S in solvers)
+    B.close()
+    for S in solvers:
+        S.close()
     inst = len(solvers)
-    rate = inst * args.steps / SOLVE_STEPS / t_batch
-    line = {"metric": "batched solves/s", "value": rate, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched_q1_riemann", "instances": inst, "mesh": "N x N Q1 quads, N log-uniform "
-                       "in [32, 512]", "dofs_total": dofs, "solve": f"{SOLVE_STEPS} SSP-RK3 steps",
-                       "scheme": "convex-limited, 2 limiter passes", "cfl": 0.5, "seed": 1,
-                       "setup_s": round(setup_s, 1), "schedule": schedule},
-            "dof_stage_per_s": dofs * 3 * args.steps / t_batch,
-            "one_at_a_time": {"value": inst * args.steps / SOLVE_STEPS / t_single, "unit": "solves/s",
-                              "ms_per_step": 1e3 * t_single / args.steps,
-                              "dof_stage_per_s": dofs * 3 * args.steps / t_single},
-            "speedup_vs_one_at_a_time": t_single / t_batch, "gpu_launches": 26 * args.steps,
+    return {"value": inst * steps / SOLVE_STEPS / t_batch, "unit": "solves/s", "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * t_batch / steps,
+            "config": {"workload": "batched_q1_riemann", "instances": inst,
+                       "sample": ("all 512 instances" if inst == 512 else
+                                  f"the first {inst} of the 512 instances of the seeded stream"),
+                       "mesh": "N x N Q1 quads, N log-uniform in [32, 512]", "dofs_total": dofs,
+                       "solve": f"{SOLVE_STEPS} SSP-RK3 steps", "scheme": "convex-limited, 2 limiter passes",
+                       "cfl": 0.5, "seed": 1, "setup_s": round(setup_s, 1), "schedule": schedule},
+            "dof_stage_per_s": dofs * 3 * steps / t_batch,
+            "one_at_a_time": {"value": inst * steps / SOLVE_STEPS / t_single, "unit": "solves/s",
+                              "ms_per_step": 1e3 * t_single / steps,
+                              "dof_stage_per_s": dofs * 3 * steps / t_single},
+            "speedup_vs_one_at_a_time": t_single / t_batch, "gpu_launches": 26 * steps,
             "clocks": clocks, "status_flags": flags}
+
+
+def run_batched(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = measure_batched(args.instances, args.steps, args.warmup, autotune=not args.no_autotune)
+    line = {"metric": "batched solves/s", "value": r["value"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": r["config"],
+            **{k: r[k] for k in ("dof_stage_per_s", "one_at_a_time", "speedup_vs_one_at_a_time", "gpu_launches",
+                                 "clocks", "status_flags")}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def served_requests(count, rate, seed=2, n_max=64):
+def served_requests(count, rate, seed=2, n_max=64, t_cap=None):
     """The served stream: `count` requests with Poisson arrivals at `rate` per second, all from
     default_rng(seed): Q1 or Q2 (even odds), N x N quads of [0,1]^2 with N log-uniform in [16, n_max], slip
     walls, two-state Riemann data (as the batched workload) or the isentropic vortex of Sec. 6.2 scaled to the
-    unit square (even odds), end time uniform in [0.1, 1].  Yields (arrival_s, problem, U0, t_end)."""
+    unit square (even odds), end time uniform in [0.1, 1] (capped at t_cap when given, so that a stream with
+    large meshes ends in minutes).  Yields (arrival_s, problem, U0, t_end)."""
     import numpy as np
 
     from paper_2402_04514_gb300 import assembly, workloads
@@ -243,10 +284,11 @@ def served_requests(count, rate, seed=2, n_max=64):
             U = workloads.two_state_riemann(P.x[0], P.x[1], rng)
         else:
             U = workloads.vortex(10.0 * P.x[0] - 5.0, 10.0 * P.x[1] - 5.0, 0.0, gamma=1.4)
-        yield t, P, np.ascontiguousarray(U), float(rng.uniform(0.1, 1.0))
+        t_end = float(rng.uniform(0.1, 1.0))
+        yield t, P, np.ascontiguousarray(U), (t_end if t_cap is None else min(t_end, t_cap))
 
 
-def run_served(args):
+def measure_served(requests, rate, n_max, t_cap=None, skip_one_at_a_time=False):
     """Served stream: requests submitted at their arrival times to the continuous-batching server
     (gdg_server), against the same stream solved one request at a time (each with gdg_ssprk3_step to its
     end time, in arrival order).  Reports solves/s over the makespan and p50/p99 time-to-solution."""
@@ -257,8 +299,7 @@ def run_served(args):
 
     from paper_2402_04514_gb300.gdg import Server, Solver
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    reqs = list(served_requests(args.requests, args.rate, n_max=args.n_max))
+    reqs = list(served_requests(requests, rate, n_max=n_max, t_cap=t_cap))
     dofs = sum(P.n for _, P, _, _ in reqs)
 
     def pct(v, q):
@@ -292,7 +333,7 @@ def run_served(args):
     # one at a time, in arrival order, each request as soon as it has arrived and the previous one is done
     t1 = time.perf_counter()
     tts1 = []
-    for ta, P, U, te in ([] if args.skip_one_at_a_time else reqs):
+    for ta, P, U, te in ([] if skip_one_at_a_time else reqs):
         now = time.perf_counter() - t1
         if now < ta:
             time.sleep(ta - now)
@@ -310,20 +351,30 @@ def run_served(args):
         S.close()
     span1 = time.perf_counter() - t1 - reqs[0][0]
     clocks = sampler.stop()
-    one = None if args.skip_one_at_a_time else {
+    one = None if skip_one_at_a_time else {
         "value": len(reqs) / span1, "unit": "solves/s", "tts_p50_s": pct(tts1, 50), "tts_p99_s": pct(tts1, 99),
         "makespan_s": span1}
-    line = {"metric": "served solves/s", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
-            "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "served_stream", "requests": len(reqs), "rate_per_s": args.rate,
-                       "mesh": f"N x N Q1/Q2 quads, N log-uniform in [16, {args.n_max}]",
-                       "t_end": "uniform in [0.1, 1]", "data": "Riemann or scaled vortex", "seed": 2,
-                       "dofs_total": dofs, "budget": "80% of free HBM"},
+    return {"value": len(reqs) / span, "unit": "solves/s", "steps": steps,
+            "config": {"workload": "served_stream", "requests": len(reqs), "rate_per_s": rate,
+                       "mesh": f"N x N Q1/Q2 quads, N log-uniform in [16, {n_max}]",
+                       "t_end": "uniform in [0.1, 1]" + ("" if t_cap is None else f", capped at {t_cap}"),
+                       "data": "Riemann or scaled vortex", "seed": 2, "dofs_total": dofs,
+                       "budget": "80% of free HBM"},
             "tts_p50_s": pct(tts, 50), "tts_p99_s": pct(tts, 99), "makespan_s": span,
             "one_at_a_time": one, "speedup_vs_one_at_a_time": None if one is None else span1 / span,
-            "clocks": clocks, "status_flags": flags,
-            "status": status}
+            "clocks": clocks, "status_flags": flags, "status": status}
+
+
+def run_served(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = measure_served(args.requests, args.rate, args.n_max, args.t_cap, args.skip_one_at_a_time)
+    line = {"metric": "served solves/s", "value": r["value"], "unit": "solves/s", "n_gpus": 1, "steps": r["steps"],
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": r["config"],
+            **{k: r[k] for k in ("tts_p50_s", "tts_p99_s", "makespan_s", "one_at_a_time", "speedup_vs_one_at_a_time",
+                                 "clocks", "status_flags", "status")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -347,7 +398,12 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--n-max", type=int, default=48, help="served workload: largest N")
+    ap.add_argument("--t-cap", type=float, default=None, help="served workload: cap on the end times")
     ap.add_argument("--skip-one-at-a-time", action="store_true", help="served workload: no one-at-a-time run")
+    ap.add_argument("--no-batched", action="store_true", help="main line: skip the batched sample")
+    ap.add_argument("--no-served", action="store_true", help="main line: skip the served sample")
+    ap.add_argument("--cpu-c3-steps", type=int, default=3,
+                    help="main line: SSP-RK3 steps of the all-core oracle on the full mesh (0: none)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--instances", type=int, default=512, help="batched workload: number of instances")
     ap.add_argument("--no-e2e", action="store_true")
@@ -509,12 +565,29 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return 0
+    # the batched and served workloads, measured on samples sized to end in about a minute each (their own
+    # --workload runs take any size)
+    batched = served = None
+    if world == 1 and not args.no_batched:
+        batched = measure_batched(COMBINED_BATCH_INSTANCES, steps=3, warmup=1)
+    if world == 1 and not args.no_served:
+        served = measure_served(**COMBINED_SERVED)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, secs, n_s = oracle_sample_rate(args.cpu_baseline_steps)
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.cpu_baseline_steps} "
-                         f"SSP-RK3 steps, single thread, {secs:.1f} s"}
+        v1, secs1, n_s, _ = oracle_sample_rate(args.cpu_baseline_steps)
+        v, secs, _, threads = oracle_sample_rate(args.cpu_baseline_steps, openmp=True)
+        sample = f"Q2 {SAMPLE_N}x{SAMPLE_N} four-quadrant (seed 0, {n_s} DoFs), {args.cpu_baseline_steps} SSP-RK3 steps"
+        cpu = {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"{sample}, {threads} threads (the oracle's row loops shared by OpenMP), {secs:.1f} s",
+               "single_thread": {"value": v1, "unit": METRIC, "cores": 1,
+                                 "sample": f"{sample}, single thread, {secs1:.1f} s"}}
+        if args.cpu_c3_steps > 0:
+            v3, secs3, threads3 = oracle_full_size_rate(P, np.ascontiguousarray(U0), args.cpu_c3_steps)
+            cpu["full_size_extrapolated"] = {
+                "value": v3, "unit": METRIC, "cores": threads3,
+                "sample": (f"the full {args.workload} mesh ({n} DoFs), {args.cpu_c3_steps} SSP-RK3 steps "
+                           f"({3 * args.cpu_c3_steps} stages) from the initial data, {threads3} threads, "
+                           f"{secs3:.1f} s; the per-stage rate extrapolates to the workload's 200 steps")}
     line = {"metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed" if main_mixed else "f64",
@@ -523,6 +596,10 @@ def main():
             "roofline": res["roofline"], "roofline_hbm" if not main_mixed else "roofline_alu": res["other"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["launches"] * world,
             "clocks": res["clocks"], "kernels": res["kernels"], "status_flags": res["flags"]}
+    if batched is not None:
+        line["batched"] = batched
+    if served is not None:
+        line["served"] = served
     if mixed_res is not None:
         # the mixed-precision path (GDG_PRECISION_MIXED) on the same workload, reported on its own: its
         # results differ from the FP64 path's by up to ~1e-5 of max |U| per stage

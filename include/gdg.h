@@ -253,8 +253,15 @@ int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
  *   row_ptr [n+1] and col_idx [nnz] (int32 CSR, as in gdg_problem), cij [dim][nnz], mi [n];
  *   boundary entries ordered by node: those of node i are b_ptr[i] .. b_ptr[i+1]-1 (int32 [n+1]), with
  *   b_c [dim][nb] and b_type [nb] in that order, and bdata [m][nb] (the data of the Dirichlet and
- *   in/outflow entries in the same order; may be NULL when every entry is a slip wall: an entry that needs
- *   data and has none makes the result NaN).
+ *   in/outflow entries in the same order; may be NULL when every entry is a slip wall).
+ * The arrays are trusted, not checked: they must satisfy the rules gdg_setup checks on the host (row_ptr
+ * non-decreasing from 0 to nnz, 0 <= col_idx < n with no diagonal entry, b_ptr non-decreasing from 0 to
+ * nb, m_i > 0, c_ij = -c_ji, U admissible).  Reading them on the device to check would cost the caller a
+ * synchronisation; an index out of range is an out-of-bounds read.
+ * NaN: a node whose sum is NaN (an inadmissible state, or a Dirichlet / in-flow entry without data) makes
+ * tau NaN.  gdg_max_dt instead refuses a call without the data (GDG_EINVAL) and drops an inadmissible
+ * node from its minimum (fmin ignores NaN), reporting the state through gdg_status, which this entry,
+ * having no handle, cannot do.
  * Output: *tau_out, a device double, written on stream (asynchronous; the call does not synchronise).
  *
  * Scratch: a fixed array of GDG_NOALLOC_MAX_NODES / 256 doubles (128 KB) in the library's own device
@@ -263,7 +270,9 @@ int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
  * array, so calls whose kernels overlap on the GPU (on different streams, or from several threads)
  * race and must be serialised by the caller.  The array needs no clearing: each call writes every
  * slot it reads.  The first call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ * address (cudaGetSymbolAddress) and caches it with the id of the current context; make that first call
+ * before any stream capture.  After a device reset (a new primary context) the next call looks the
+ * address up again, so it too must come before any capture.
  * Errors: GDG_EINVAL (NULL pointer, cfl <= 0, gamma <= 1), GDG_ENOTSUP (dim, sizes), GDG_ECUDA. */
 #define GDG_NOALLOC_MAX_NODES 4194304
 typedef struct {

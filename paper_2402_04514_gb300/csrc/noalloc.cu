@@ -1,6 +1,8 @@
 // gdg_max_dt_noalloc: the time step of the handle-based gdg_max_dt, for callers that must not
 // allocate device memory.  The per-block partial minima live in a fixed file-scope device array
 // instead of handle scratch; the per-node primitives are recomputed on the fly from U.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -17,9 +19,41 @@ static_assert(GDG_NOALLOC_MAX_NODES % kThreads == 0, "node limit must be a multi
 // 128 KB until the process exits.
 static __device__ __align__(256) double g_noalloc_partial[kMaxBlocks];
 
-// Address of g_noalloc_partial on each device, filled by the first call made with that device current.
+// Address of g_noalloc_partial on each device, filled by the first call made with that device current,
+// with the id of the context it was looked up in: after a device reset the runtime creates a new context
+// and loads the module again, so a cached address is used only while the current context has that id.
 std::mutex g_setup_mutex;
 double* g_partial_ptr[64] = {nullptr};
+unsigned long long g_partial_ctx[64] = {0};
+
+// The driver's context calls, reached through the runtime (the library links only cudart).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the current context (0 when it cannot be read: then every call looks the address up again).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 struct NodePrim {
   double irho, p, ip, a, pme;
@@ -167,19 +201,21 @@ __global__ void k_noalloc_final(const double* __restrict__ partial, int count, d
   }
 }
 
-// Looks up (once per device, under a lock) the device address of g_noalloc_partial.
+// Looks up (once per device and context, under a lock) the device address of g_noalloc_partial.
 int partial_buffer(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GDG_ECUDA;
   if (dev < 0 || dev >= 64) return GDG_ENOTSUP;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partial_ptr[dev]) {
+  unsigned long long ctx = current_context_id();
+  if (!g_partial_ptr[dev] || ctx == 0 || ctx != g_partial_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess || !p) {
       cudaGetLastError();
       return GDG_ECUDA;
     }
     g_partial_ptr[dev] = static_cast<double*>(p);
+    g_partial_ctx[dev] = ctx ? ctx : current_context_id();  // the lookup creates the context if it had none
   }
   *out = g_partial_ptr[dev];
   return GDG_OK;

@@ -112,3 +112,31 @@ def test_oversized_request_is_refused_and_footprint_is_exact(torch_cuda):
     with pytest.raises(GdgError):
         srv.submit(P, U, 0.01)
     srv.close()
+
+
+def test_served_requests_against_the_oracle(torch_cuda):
+    """Requests served together (two Q2 and one Q1 two-state Riemann problems, submitted at once so that
+    the Q2 ones share a batch) against the oracle directly: the oracle steps each request
+    with its own time step of Sec. 3.3 (Cr = 0.5, the last step clipped to the end time) and the served
+    result equals its trajectory within 1e-10 relative per component, with the same number of steps."""
+    torch = torch_cuda
+    from oracle.oracle import Oracle
+    from paper_2402_04514_gb300.gdg import Server
+    from tests.helpers import rel_err
+
+    reqs = [(_request(7, 2, 21), 0.02), (_request(11, 1, 22), 0.03), (_request(5, 2, 23), 0.015)]
+    srv = Server()
+    ids = [srv.submit(P, U, t_end) for (P, U), t_end in reqs]
+    results = [srv.wait(r, timeout=300.0) for r in ids]
+    srv.close()
+    for ((P, U), t_end), (got, info) in zip(reqs, results):
+        O = Oracle(P)
+        V, t, steps = U.copy(), 0.0, 0
+        while t < t_end:
+            tau = min(O.max_dt(V, 0.5), t_end - t)
+            V, flags = O.ssprk3_step(V, tau)
+            assert flags == 0
+            t = t + tau if t + tau < t_end else t_end
+            steps += 1
+        assert info["status"] == 0 and info["flags"] == 0 and info["steps"] == steps
+        assert rel_err(got, V) <= 1e-10
