@@ -11,8 +11,8 @@ L2, so no flush is needed between steps.
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own instance (replicas: the path has no
 exchange step); value = all ranks' DoF-stage updates / max over ranks of the timed region.
-At N = 1 the line also carries samples of the batched workload (the first 128 of its 512 seeded Q1
-instances: batched solves/s against one at a time) and of the served workload (48 Poisson-arrival Q1/Q2
+At N = 1 the line also carries the batched workload (its 512 seeded Q1 instances: batched solves/s
+against one at a time) and a sample of the served workload (48 Poisson-arrival Q1/Q2
 requests with meshes up to 256^2 and end times capped at 0.01: solves/s and p50/p99 time-to-solution
 against one at a time); --workload batched_q1_riemann / served_stream run either at any size.
 --impl reference times the FP64 CPU oracle on all host cores (rank 0 only) on a bounded sample of the
@@ -40,7 +40,7 @@ WORKLOADS = {
 SAMPLE_N = 128  # oracle sample: same data on a 128 x 128 mesh
 SOLVE_STEPS = 50  # a batched solve: 50 SSP-RK3 steps of one instance
 # samples of the batched and served workloads that the default run reports beside the main line
-COMBINED_BATCH_INSTANCES = 128
+COMBINED_BATCH_INSTANCES = 512
 COMBINED_SERVED = dict(requests=48, rate=20.0, n_max=256, t_cap=0.01)
 
 

@@ -291,11 +291,13 @@ int gdg_max_dt_noalloc(const gdg_dev_mesh* mesh, const double* U, const double* 
                        double* tau_out, void* stream);
 
 /* Launch schedule: threads per block of the one-thread-per-row (per-edge) kernels (128, 256 or 512),
- * the largest element block of the element sweep (whole elements, 1..288 nodes) and the queue slots per
- * thread of the deferred line-search grid (1..1024).  Defaults: 256 threads, 160 nodes, 4 slots.
- * gdg_autotune picks them for one handle by timing: it saves U and the clock, runs 3 + 5 + 3 candidate
- * schedules of (trials + 1) gdg_ssprk3_step each from that saved state (coordinate descent: row-kernel
- * block sizes, then the element block, then the queue grid; each kernel keeps its fastest candidate),
+ * the node cap of the element sweep's blocks (1..288: a block holds the largest power of two of
+ * elements, at most 32, whose nodes fit the cap, one element at least) and the queue slots per thread of
+ * the deferred line-search grid (1..1024), and the row order of the kernels with per-entry loops.
+ * Defaults: 256 threads, 288 nodes, 4 slots, slice order.  gdg_autotune picks them for one handle by
+ * timing: it saves U and the clock, runs 3 + 2 + 4 + 3 candidate schedules of (trials + 1)
+ * gdg_ssprk3_step each from that saved state (coordinate descent: row-kernel block sizes, their row
+ * order, then the element block, then the queue grid; each kernel keeps its fastest candidate),
  * and restores U, the clock and the status flags.  It allocates one temporary state copy and
  * synchronises the stream.  Arguments as gdg_ssprk3_step.  The schedule changes speed only: results are
  * bit-identical under every schedule.  gdg_get_schedule / gdg_set_schedule read or install one (e.g. a
@@ -305,6 +307,9 @@ typedef struct {
   int32_t prim_threads, edge_threads, tau_threads, low_threads, limit2_threads, final_threads, maxdt_threads;
   int32_t high_block_cap;
   int32_t lsfix_slots;
+  int32_t row_slices;  // bits 1 << GDG_K_{MAXDT,LOW,LIMIT2,FINAL,TAU}: that kernel's threads take their rows in
+                       // the entry storage's slice order (a warp takes one local index of 32 consecutive
+                       // elements) instead of node order; default: all five
 } gdg_schedule;
 int gdg_autotune(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, int32_t trials,
                  void* stream);

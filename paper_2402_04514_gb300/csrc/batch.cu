@@ -44,12 +44,16 @@ cudaError_t launch_many(const gdg_batch* b, int kern, int stage, int arg, cudaSt
   const long long blocks = b->blocks[kern];
   switch (kern) {
     case gdg::KN_HIGH:
-      return gdg::launch_high_file_many(b->dim, b->mixed, m, blocks,
-                                        gdg::high_nodes_per_block(b->n_loc, b->sched.high_cap), s);
+      return gdg::launch_high_file_many(b->dim, b->mixed, m, b->n_loc, blocks,
+                                        gdg::high_elems_per_block(b->n_loc, b->sched.high_cap), s);
     case gdg::KN_LIMIT2:
     case gdg::KN_FINAL:
-    case gdg::KN_LSFIX: return gdg::launch_limit_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], arg, s);
-    default: return gdg::launch_low_file_many(kern, b->dim, b->mixed, m, blocks, b->sched.bt[kern], arg, s);
+    case gdg::KN_LSFIX:
+      return gdg::launch_limit_file_many(kern, b->dim, m, blocks, b->sched.bt[kern], (b->sched.slices >> kern) & 1,
+                                         arg, s);
+    default:
+      return gdg::launch_low_file_many(kern, b->dim, b->mixed, m, blocks, b->sched.bt[kern],
+                                       (b->sched.slices >> kern) & 1, arg, s);
   }
 }
 

@@ -95,9 +95,10 @@ struct Arena {
 };
 
 // The device arena of a handle: every array with its element type and count (m = dim + 2 components,
-// ne canonical stencil edges, nel elements of nl nodes).  gdg_setup allocates it; gdg_footprint sizes it.
+// nnz the length of the sliced-ELL per-entry arrays, ne canonical stencil edges, nel the elements rounded
+// up to whole ELL groups, of nl nodes).  gdg_setup allocates it; gdg_footprint sizes it.
 #define GDG_ARENA(X)                                                                                       \
-  X(rowptr, int, n + 1) X(sten, int, n) X(col, int, nnz) X(tr, int, nnz) X(cnorm, double, nnz) X(cn, double, dim * nnz)   \
+  X(rbeg, int, n) X(rend, int, n) X(sten, int, n) X(col, int, nnz) X(tr, int, nnz) X(cnorm, double, nnz) X(cn, double, dim * nnz)   \
   X(mij, double, nnz) X(mu, double, nnz) X(mi, double, n) X(imi, double, n) X(ikm, double, n)             \
   X(rm, double, n) X(rp, double, n) X(muB, double, n) X(bptr, int, n + 1) X(bnorm, double, nb)           \
   X(bn, double, dim * nb) X(btype, int, nb) X(borig, int, nb) X(minv, double, nel * nl * nl)             \
@@ -115,6 +116,34 @@ struct Layout {
 #undef GDG_F
   size_t total;
 };
+
+// Sliced-ELL layout of the per-entry arrays (kEll in gdg_internal.cuh): the start of every slice (group g of
+// kEll consecutive elements, local index l) from the row lengths, each slice padded to its longest row,
+// and the total length.
+struct EllLayout {
+  std::vector<int64_t> sbase;  // [groups * nl + 1]
+  int64_t total = 0;
+};
+template <class Len>
+EllLayout ell_layout(int64_t n, int nl, Len len) {
+  const int64_t nel = n / nl, ngrp = (nel + gdg::kEll - 1) / gdg::kEll;
+  EllLayout L;
+  L.sbase.assign((size_t)(ngrp * nl + 1), 0);
+  for (int64_t g = 0; g < ngrp; ++g)
+    for (int l = 0; l < nl; ++l) {
+      int64_t w = 0;
+      for (int e = 0; e < gdg::kEll; ++e) {
+        const int64_t E = g * gdg::kEll + e;
+        if (E < nel) w = std::max<int64_t>(w, len(E * nl + l));
+      }
+      const int64_t sl = g * nl + l;
+      L.sbase[sl + 1] = L.sbase[sl] + gdg::kEll * w;
+    }
+  L.total = L.sbase[ngrp * nl];
+  return L;
+}
+
+int64_t padded_elements(int64_t nel) { return (nel + gdg::kEll - 1) / gdg::kEll * gdg::kEll; }
 
 Layout make_layout(int dim, int64_t n, int64_t nnz, int64_t nb, int nl, int64_t ne, int64_t nel) {
   const int64_t m = dim + 2;
@@ -135,9 +164,9 @@ struct ParamArrays {
 };
 
 int param_arrays(const gdg_handle* h, const gdg_params& p, ParamArrays& A) {
-  const int64_t n = h->n, nnz = h->nnz;
+  const int64_t n = h->n;
   const double dinv = 1.0 / h->dim;
-  A.mu.assign(nnz, 0.0);
+  A.mu.assign(h->nnz_ell, 0.0);
   A.rm.resize(n);
   A.rp.resize(n);
   A.muB.resize(n);
@@ -152,14 +181,14 @@ int param_arrays(const gdg_handle* h, const gdg_params& p, ParamArrays& A) {
       if (!h->coloc[e]) continue;
       int j = h->col[e];
       double hij = std::pow(0.5 * (h->mi[i] + h->mi[j]) / h->omega, dinv);
-      A.mu[e] = p.c_k * std::pow(hij, p.p_k);
+      A.mu[h->epos[e]] = p.c_k * std::pow(hij, p.p_k);
     }
   }
   return GDG_OK;
 }
 
 int upload_param_arrays(gdg_handle* h, const ParamArrays& A) {
-  const int64_t n = h->n, nnz = h->nnz;
+  const int64_t n = h->n, nnz = h->nnz_ell;
   cudaError_t e;
   if ((nnz > 0 && (e = cudaMemcpy(h->d_mu, A.mu.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (n > 0 && (e = cudaMemcpy(h->d_rminus, A.rm.data(), sizeof(double) * n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
@@ -416,16 +445,60 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     double terms = (h->row_ptr[i + 1] - h->row_ptr[i]) + (b_ptr[i + 1] - b_ptr[i]);
     inv_km[i] = terms > 0 ? terms / h->mi[i] : 0.0;
   }
-  // canonical stencil edges (i < j, c_ij != 0) in entry order
-  std::vector<int> edge_e, edge_i;
-  edge_e.reserve(nnz / 2 + 1);
-  edge_i.reserve(nnz / 2 + 1);
+  // ---- sliced-ELL positions of the entries (gdg_internal.cuh, kEll) ----
+  const EllLayout EL = ell_layout(n, nl, [&](int64_t i) { return (int64_t)(h->row_ptr[i + 1] - h->row_ptr[i]); });
+  if (EL.total >= (int64_t(1) << 31)) return fail(GDG_ENOTSUP);
+  const int64_t NE = EL.total;
+  h->nnz_ell = NE;
+  h->epos.resize(nnz);
+  std::vector<int> rbeg(n), rend(n), sten_ell(n);
+  parallel_for(n, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      const int64_t E = i / nl, l = i % nl;
+      const int64_t p0 = EL.sbase[(size_t)((E / gdg::kEll) * nl + l)] + E % gdg::kEll;
+      rbeg[i] = (int)p0;
+      rend[i] = (int)(p0 + gdg::kEll * (int64_t)(h->row_ptr[i + 1] - h->row_ptr[i]));
+      sten_ell[i] = (int)(p0 + gdg::kEll * (int64_t)(sten_end[i] - h->row_ptr[i]));
+      for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q)
+        h->epos[q] = (int)(p0 + gdg::kEll * (int64_t)(q - h->row_ptr[i]));
+    }
+  });
+  // the per-entry arrays in ELL order; padding slots stay zero and no kernel reads them
+  std::vector<int> col_e((size_t)NE, 0), tr_e((size_t)NE, 0);
+  std::vector<double> cnorm_e((size_t)NE, 0.0), cn_e((size_t)dim * NE, 0.0), mij_e((size_t)NE, 0.0);
+  parallel_for(nnz, [&](int64_t b, int64_t e) {
+    for (int64_t q = b; q < e; ++q) {
+      const int64_t pq = h->epos[q];
+      col_e[pq] = h->col[q];
+      tr_e[pq] = h->epos[h->tr[q]];
+      cnorm_e[pq] = cnorm[q];
+      mij_e[pq] = mij[q];
+      for (int k = 0; k < dim; ++k) cn_e[(size_t)k * NE + pq] = cn[(size_t)k * nnz + q];
+    }
+  });
+  // M_K^{-1} grouped like the entries: (K, a, b) at ((K / kEll * nl + a) * nl + b) * kEll + K % kEll
+  const int64_t nel_pad = padded_elements(nel);
+  std::vector<double> minv_g((size_t)nel_pad * nl * nl, 0.0);
+  parallel_for(nel, [&](int64_t b, int64_t e) {
+    for (int64_t K = b; K < e; ++K)
+      for (int a = 0; a < nl; ++a)
+        for (int c = 0; c < nl; ++c)
+          minv_g[(((size_t)(K / gdg::kEll) * nl + a) * nl + c) * gdg::kEll + K % gdg::kEll] =
+              MKinv[((size_t)K * nl + a) * nl + c];
+  });
+  // canonical stencil edges (i < j, c_ij != 0) in ELL order: consecutive threads of the edge sweep take
+  // the same entry of the rows of consecutive elements, so their per-entry writes are contiguous
+  std::vector<std::pair<int, int>> edges;
+  edges.reserve(nnz / 2 + 1);
   for (int64_t i = 0; i < n; ++i)
     for (int q = h->row_ptr[i]; q < h->row_ptr[i + 1]; ++q)
-      if (cnorm[q] > 0.0 && h->col[q] > i) {
-        edge_e.push_back(q);
-        edge_i.push_back((int)i);
-      }
+      if (cnorm[q] > 0.0 && h->col[q] > i) edges.emplace_back(h->epos[q], (int)i);
+  std::sort(edges.begin(), edges.end());
+  std::vector<int> edge_e(edges.size()), edge_i(edges.size());
+  for (size_t k = 0; k < edges.size(); ++k) {
+    edge_e[k] = edges[k].first;
+    edge_i[k] = edges[k].second;
+  }
   const int64_t ne = (int64_t)edge_e.size();
   std::vector<double> bnorm(nb), bn((size_t)dim * nb);
   std::vector<int> btype(nb);
@@ -442,7 +515,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
   if (int rc = param_arrays(h, h->params, pa); rc != GDG_OK) return fail(rc);
 
   // ---- device arena ----
-  const Layout Lo = make_layout(dim, n, nnz, nb, nl, ne, nel);
+  const Layout Lo = make_layout(dim, n, NE, nb, nl, ne, nel_pad);
 #define GDG_F(name, T, cnt) const size_t o_##name = Lo.o_##name;
   GDG_ARENA(GDG_F)
 #undef GDG_F
@@ -461,13 +534,14 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
     if (bytes == 0) return cudaSuccess;
     return cudaMemcpy(ptr(o), src, bytes, cudaMemcpyHostToDevice);
   };
-  if ((ce = up(o_rowptr, h->row_ptr.data(), sizeof(int) * (n + 1))) != cudaSuccess ||
-      (ce = up(o_sten, sten_end.data(), sizeof(int) * n)) != cudaSuccess ||
-      (ce = up(o_col, h->col.data(), sizeof(int) * nnz)) != cudaSuccess ||
-      (ce = up(o_tr, h->tr.data(), sizeof(int) * nnz)) != cudaSuccess ||
-      (ce = up(o_cnorm, cnorm.data(), sizeof(double) * nnz)) != cudaSuccess ||
-      (ce = up(o_cn, cn.data(), sizeof(double) * dim * nnz)) != cudaSuccess ||
-      (ce = up(o_mij, mij.data(), sizeof(double) * nnz)) != cudaSuccess ||
+  if ((ce = up(o_rbeg, rbeg.data(), sizeof(int) * n)) != cudaSuccess ||
+      (ce = up(o_rend, rend.data(), sizeof(int) * n)) != cudaSuccess ||
+      (ce = up(o_sten, sten_ell.data(), sizeof(int) * n)) != cudaSuccess ||
+      (ce = up(o_col, col_e.data(), sizeof(int) * NE)) != cudaSuccess ||
+      (ce = up(o_tr, tr_e.data(), sizeof(int) * NE)) != cudaSuccess ||
+      (ce = up(o_cnorm, cnorm_e.data(), sizeof(double) * NE)) != cudaSuccess ||
+      (ce = up(o_cn, cn_e.data(), sizeof(double) * dim * NE)) != cudaSuccess ||
+      (ce = up(o_mij, mij_e.data(), sizeof(double) * NE)) != cudaSuccess ||
       (ce = up(o_mi, h->mi.data(), sizeof(double) * n)) != cudaSuccess ||
       (ce = up(o_imi, inv_mi.data(), sizeof(double) * n)) != cudaSuccess ||
       (ce = up(o_ikm, inv_km.data(), sizeof(double) * n)) != cudaSuccess ||
@@ -476,7 +550,7 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
       (ce = up(o_bn, bn.data(), sizeof(double) * dim * nb)) != cudaSuccess ||
       (ce = up(o_btype, btype.data(), sizeof(int) * nb)) != cudaSuccess ||
       (ce = up(o_borig, border.data(), sizeof(int) * nb)) != cudaSuccess ||
-      (ce = up(o_minv, MKinv.data(), sizeof(double) * MKinv.size())) != cudaSuccess ||
+      (ce = up(o_minv, minv_g.data(), sizeof(double) * minv_g.size())) != cudaSuccess ||
       (ce = up(o_ee, edge_e.data(), sizeof(int) * ne)) != cudaSuccess ||
       (ce = up(o_ei, edge_i.data(), sizeof(int) * ne)) != cudaSuccess ||
       (ce = cudaMemset(ptr(o_flags), 0, 16)) != cudaSuccess)
@@ -484,11 +558,13 @@ int gdg_setup(const gdg_problem* P, gdg_handle** out) {
 
   Dev& D = h->D;
   D.n = (int)n;
-  D.nnz = (int)nnz;
+  D.nnz = (int)NE;
   D.nb = (int)nb;
   D.n_loc = nl;
+  D.nel = (int)nel;
   gdg::set_nl_division(D, nl);
-  D.row_ptr = (const int*)ptr(o_rowptr);
+  D.rbeg = (const int*)ptr(o_rbeg);
+  D.rend = (const int*)ptr(o_rend);
   D.sten_end = (const int*)ptr(o_sten);
   D.col = (const int*)ptr(o_col);
   D.tr = (const int*)ptr(o_tr);
@@ -569,7 +645,9 @@ int gdg_footprint(const gdg_problem* P, int64_t* bytes) {
       for (int k = 0; k < P->dim; ++k) nz = nz || P->cij[(size_t)k * P->nnz + q] != 0.0;
       if (nz && P->col_idx[q] > i) ++ne;
     }
-  *bytes = (int64_t)make_layout(P->dim, P->n, P->nnz, P->nb, P->n_loc, ne, P->n / P->n_loc).total;
+  if (P->n % P->n_loc != 0) return GDG_EINVAL;
+  const EllLayout EL = ell_layout(P->n, P->n_loc, [&](int64_t i) { return P->row_ptr[i + 1] - P->row_ptr[i]; });
+  *bytes = (int64_t)make_layout(P->dim, P->n, EL.total, P->nb, P->n_loc, ne, padded_elements(P->n / P->n_loc)).total;
   return GDG_OK;
 }
 
@@ -836,7 +914,7 @@ int gdg_status(gdg_handle* h, int32_t* flags, int32_t clear, void* stream) {
 
 int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count, void* stream) {
   if (!h || !name || !dst) return GDG_EINVAL;
-  const int64_t n = h->n, nnz = h->nnz, nb = h->nb, m = h->dim + 2;
+  const int64_t n = h->n, nnz = h->nnz, nb = h->nb, m = h->dim + 2, NE = h->nnz_ell;
   const double* src = nullptr;
   int64_t want = -1;
   int kind = 0;  // 0 plain copy, 1 symmetrised per-entry limiter, 2 boundary order
@@ -865,16 +943,19 @@ int gdg_debug_export(gdg_handle* h, const char* name, double* dst, int64_t count
     dst[1] = q[1];
     return GDG_OK;
   }
-  std::vector<double> tmp(want);
-  if (want > 0 && (e = cudaMemcpy(tmp.data(), src, sizeof(double) * want, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  // per-entry arrays live in sliced-ELL order on the device (their length NE per component)
+  const int64_t dev_count = (per_entry || kind == 1) ? want / std::max<int64_t>(nnz, 1) * NE : want;
+  std::vector<double> tmp(dev_count);
+  if (dev_count > 0 &&
+      (e = cudaMemcpy(tmp.data(), src, sizeof(double) * dev_count, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e);
   if (kind == 0 && per_entry) {  // device entry order back to the caller's
-    for (int64_t r = 0; r < want / nnz; ++r)
-      for (int64_t q = 0; q < nnz; ++q) dst[r * nnz + h->eorig[q]] = tmp[r * nnz + q];
+    for (int64_t r = 0; r < want / std::max<int64_t>(nnz, 1); ++r)
+      for (int64_t q = 0; q < nnz; ++q) dst[r * nnz + h->eorig[q]] = tmp[r * NE + h->epos[q]];
   } else if (kind == 0) {
     std::memcpy(dst, tmp.data(), sizeof(double) * want);
   } else if (kind == 1) {
-    for (int64_t q = 0; q < want; ++q) dst[h->eorig[q]] = std::min(tmp[q], tmp[h->tr[q]]);
+    for (int64_t q = 0; q < want; ++q) dst[h->eorig[q]] = std::min(tmp[h->epos[q]], tmp[h->epos[h->tr[q]]]);
   } else {
     for (int64_t t = 0; t < want; ++t) dst[h->borig[t]] = tmp[t];
   }

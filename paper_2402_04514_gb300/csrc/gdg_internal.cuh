@@ -26,16 +26,26 @@ __host__ __device__ inline RootQ root_q(int q) {
   return r;
 }
 
-// Everything a kernel needs, passed by value.  Per-entry and per-node arrays are device pointers in
-// CSR order (rows element-contiguous; within a row the stencil entries c_ij != 0 come first, then the
-// m_ij-only entries); boundary entries are sorted by node (b_ptr indexes them).
+// Per-entry arrays are stored as sliced ELL.  The elements are taken in groups of kEll consecutive
+// elements; slice (g, l) holds the rows of local index l of the group's elements, entry k of the row of
+// the group's e-th element at slice_base(g, l) + kEll * k + e, and every slice is padded to its longest
+// row.  A warp that takes one local index of kEll consecutive elements (the element sweep's thread map)
+// then reads entry k of its 32 rows as one contiguous 256-byte segment.  Within a row the stencil entries
+// c_ij != 0 come first, then the m_ij-only entries.  Padding slots are never read.
+constexpr int kEll = 32;
+
+// Everything a kernel needs, passed by value.  Per-entry arrays are device pointers in the sliced-ELL
+// order above (row i's entries at rbeg[i], rbeg[i] + kEll, ... below rend[i]); per-node arrays in node
+// order (rows element-contiguous); boundary entries are sorted by node (b_ptr indexes them).
 struct Dev {
-  int n, nnz, nb, n_loc;
+  int n, nnz, nb, n_loc;      // nnz: the length of the per-entry arrays, padding included
+  int nel;                    // elements (n / n_loc)
   unsigned long long nl_mul;  // floor(x / n_loc) = (x * nl_mul) >> nl_shift for 0 <= x < 2^31 (div_nl)
   int nl_shift;
-  // CSR
-  const int* row_ptr;   // [n+1]
-  const int* sten_end;  // [n] end of row i's stencil entries: I(i) is row_ptr[i] .. sten_end[i] - 1
+  // rows
+  const int* rbeg;      // [n] position of row i's first entry
+  const int* rend;      // [n] end of row i: rbeg[i] + kEll * (row length)
+  const int* sten_end;  // [n] end of row i's stencil entries: I(i) is rbeg[i], rbeg[i] + kEll, ... below it
   const int* col;       // [nnz]
   const int* tr;        // [nnz] position of the transposed entry (j, i)
   const double* cnorm;  // [nnz] |c_ij| (0 when c_ij = 0)
@@ -92,6 +102,15 @@ inline void set_nl_division(Dev& D, int nl) {
 }
 __device__ __forceinline__ int div_nl(const Dev& D, int x) {
   return (int)(((unsigned long long)(unsigned)x * D.nl_mul) >> D.nl_shift);
+}
+
+// The row of slot t of a one-thread-per-row kernel (row_slots below), -1 past the mesh.
+__device__ __forceinline__ int row_node(const Dev& D, int t, int sliced) {
+  if (!sliced) return t < D.n ? t : -1;
+  const int sl = t / kEll;
+  const int g = div_nl(D, sl);
+  const int E = g * kEll + (t & (kEll - 1));
+  return E < D.nel ? E * D.n_loc + (sl - g * D.n_loc) : -1;
 }
 
 // Equation-of-state constants of Dev for gamma (host side; gdg_setup and the wave-speed check).
@@ -273,36 +292,51 @@ enum Kern { KN_PRIM = 0, KN_MAXDT, KN_EDGE, KN_LOW, KN_HIGH, KN_LIMIT2, KN_FINAL
             KN_COUNT };
 constexpr int kRowMaxThreads = 512;  // one-thread-per-row / per-edge kernels: 128, 256 or 512 threads
 constexpr int kHighMaxBlock = 288;   // element sweep: whole elements, at most this many nodes per block
-constexpr int kHighDefaultCap = 160;  // the element block of an untuned schedule
+constexpr int kHighDefaultCap = 288;  // the element block of an untuned schedule
 constexpr int kLsfixThreads = 128;
 
 // The launch schedule: threads per block of each one-thread-per-row kernel (KN_EDGE: per edge), the
 // largest element block of the element sweep (whole elements, <= kHighMaxBlock nodes), and how many
 // queue slots per thread the deferred line-search grid is sized for.  The defaults are what an untuned
 // handle or batch runs; gdg_autotune / gdg_batch_autotune pick others by timing.
+// slices: the row kernels (bit KN_*) whose threads take their rows in ELL slice order (row_node).
 struct Sched {
   int bt[KN_COUNT];
   int high_cap;
   int lsfix_slots;
+  int slices;
 };
+constexpr int kSliceable = (1 << KN_MAXDT) | (1 << KN_LOW) | (1 << KN_LIMIT2) | (1 << KN_FINAL) | (1 << KN_TAU);
 inline Sched default_sched() {
   Sched sc;
   for (int k = 0; k < KN_COUNT; ++k) sc.bt[k] = 256;
   sc.high_cap = kHighDefaultCap;
   sc.lsfix_slots = 4;
+  sc.slices = kSliceable;
   return sc;
 }
-__host__ __device__ inline int high_nodes_per_block(int n_loc, int cap) { return n_loc > 0 ? (cap / n_loc) * n_loc : 0; }
-__host__ __device__ inline int high_threads(int npb) {
-  const int t = (npb + 31) / 32 * 32;
-  return t > kHighMaxBlock ? kHighMaxBlock : t;
+
+// Row slots of a one-thread-per-row kernel: in node order slot t is row t; in ELL slice order slot t is
+// lane t % kEll of slice t / kEll = g n_loc + l, the row of local index l of element g kEll + t % kEll, so
+// that a warp's per-entry loads are contiguous (the nodes' own arrays are then read n_loc apart).
+__host__ __device__ inline long long row_slots(const Dev& D, bool sliced) {
+  return sliced ? (long long)((D.nel + kEll - 1) / kEll) * kEll * D.n_loc : (long long)D.n;
 }
+// Elements per block of the element sweep: the largest power of two <= kEll whose nodes fit the cap (so
+// that a block is an aligned part of one ELL group), at least one.
+__host__ __device__ inline int high_elems_per_block(int n_loc, int cap) {
+  if (n_loc <= 0) return 0;
+  int eb = kEll;
+  while (eb > 1 && eb * n_loc > cap) eb >>= 1;
+  return eb;
+}
+__host__ __device__ inline int high_threads(int n_loc, int eb) { return (eb * n_loc + 31) / 32 * 32; }
 inline long long kernel_blocks(int k, const Dev& D, const Sched& sc) {
   switch (k) {
     case KN_EDGE: return ((long long)D.ne + sc.bt[k] - 1) / sc.bt[k];
-    case KN_HIGH: {
-      const int npb = high_nodes_per_block(D.n_loc, sc.high_cap);
-      return npb > 0 ? ((long long)D.n + npb - 1) / npb : 0;
+    case KN_HIGH: {  // the groups of kEll elements, each in kEll / eb blocks
+      const int eb = high_elems_per_block(D.n_loc, sc.high_cap);
+      return eb > 0 ? ((long long)D.nel + kEll - 1) / kEll * (kEll / eb) : 0;
     }
     case KN_LSFIX: {
       // The queue length is only known on the device.  The grid covers the entries at lsfix_slots per
@@ -311,25 +345,26 @@ inline long long kernel_blocks(int k, const Dev& D, const Sched& sc) {
       const long long per_block = (long long)kLsfixThreads * sc.lsfix_slots;
       return D.n == 0 ? 0 : ((long long)D.nnz + D.nb + per_block - 1) / per_block;
     }
-    default: return ((long long)D.n + sc.bt[k] - 1) / sc.bt[k];
+    default: return (row_slots(D, (sc.slices >> k) & 1) + sc.bt[k] - 1) / sc.bt[k];
   }
 }
 
 // Kernel launchers of each file, dim in 1..3: one instance (context by value) or a batch (Many; blocks =
 // the batch's total for that kernel).  arg: write_out for KN_LOW (the stage ends after U^L), last for
 // KN_LIMIT2 (one limiter pass only), the pass (0 or 1) for KN_LSFIX.  threads: the block size of a
-// one-thread-per-row kernel; npb: nodes per element block of KN_HIGH; mixed: the precision of every
-// member (single instances take it from their context).
-cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+// one-thread-per-row kernel; sliced: its rows in ELL slice order; eb: elements per block of KN_HIGH;
+// mixed: the precision of every member (single instances take it from their context).
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
                             cudaStream_t s);
-cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads, int arg,
-                                 cudaStream_t s);
-cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s);
-cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, long long blocks, int npb, cudaStream_t s);
-cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads,
+                                 int sliced, int arg, cudaStream_t s);
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int eb, cudaStream_t s);
+cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, int n_loc, long long blocks, int eb,
+                                  cudaStream_t s);
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
                               cudaStream_t s);
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
-                                   cudaStream_t s);
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int sliced,
+                                   int arg, cudaStream_t s);
 // End of a fused step: advances the clock(s) by the step's dt (kernels_limit.cu).
 cudaError_t launch_clock_one(Clock* clk, double dt_factor, cudaStream_t s);
 cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);
@@ -338,12 +373,12 @@ cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);
 inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sched& sc, cudaStream_t s) {
   const long long blocks = kernel_blocks(kern, c.D, sc);
   switch (kern) {
-    case KN_HIGH: return launch_high_file(dim, c, blocks, high_nodes_per_block(c.D.n_loc, sc.high_cap), s);
+    case KN_HIGH: return launch_high_file(dim, c, blocks, high_elems_per_block(c.D.n_loc, sc.high_cap), s);
     case KN_LIMIT2:
     case KN_FINAL:
     case KN_AXPY:
-    case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
-    default: return launch_low_file(kern, dim, c, blocks, sc.bt[kern], arg, s);
+    case KN_LSFIX: return launch_limit_file(kern, dim, c, blocks, sc.bt[kern], (sc.slices >> kern) & 1, arg, s);
+    default: return launch_low_file(kern, dim, c, blocks, sc.bt[kern], (sc.slices >> kern) & 1, arg, s);
   }
 }
 

@@ -19,7 +19,9 @@ struct gdg_handle {
   gdg::Scratch S{};
   // host copies needed after setup
   std::vector<int> row_ptr, col, tr, borig, bnode_sorted;
-  std::vector<int> eorig;  // caller's index of each device entry (rows are stencil-first on the device)
+  std::vector<int> eorig;  // caller's index of each CSR entry q (rows are stencil-first on the device)
+  std::vector<int> epos;   // position of CSR entry q in the device's sliced-ELL arrays
+  int64_t nnz_ell = 0;     // length of the device's per-entry arrays (padding included)
   std::vector<uint8_t> coloc;
   std::vector<double> mi;
   // device pointers of the parameter-dependent arrays
@@ -93,9 +95,10 @@ inline gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Uba
 // descent over three groups of knobs, each candidate timed over `trials` fused steps from the same saved
 // state (restore() puts state and clocks back before every candidate and at the end):
 //   1. threads per block of the one-thread-per-row/edge kernels, 128, 256 or 512, chosen per kernel
-//      (all row kernels take the candidate together; each keeps its own fastest);
-//   2. the element sweep's block cap (whole elements of n_loc nodes), among the caps that give
-//      different blocks;
+//      (all row kernels take the candidate together; each keeps its own fastest); then the row order
+//      (node order or ELL slice order) of the kernels with per-entry loops, each keeping the faster;
+//   2. the element sweep's block: 32, 16, 8 or 4 elements of one ELL group (the cap eb * n_loc), those
+//      that fit kHighMaxBlock nodes;
 //   3. the queue slots per thread of the deferred line-search grid, 1, 4 or 16.
 // apply(sc) installs a schedule, step() runs one fused step with kernel timing on, kernel_ms(ms) returns
 // the mean ms per launch of each GDG_K_* kernel since the last call.
@@ -131,13 +134,32 @@ int autotune_schedule(gdg::Sched& sched, int n_loc, int trials, Apply apply, Ste
         sc.bt[row_kern[r][0]] = bt;
       }
   }
-  // 2. element sweep block cap
+  // 1b. row order of the kernels with per-entry loops: node order or ELL slice order, each kernel keeps
+  //     the faster (k_maxdt is not part of a fused step and keeps its order)
+  {
+    static const int order_kern[][2] = {{gdg::KN_TAU, GDG_K_TAU}, {gdg::KN_LOW, GDG_K_LOW},
+                                        {gdg::KN_LIMIT2, GDG_K_LIMIT2}, {gdg::KN_FINAL, GDG_K_FINAL}};
+    double t_on[4], t_off[4];
+    gdg::Sched cand = sc;
+    for (auto& ok : order_kern) cand.slices |= 1 << ok[0];
+    if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
+    for (int r = 0; r < 4; ++r) t_on[r] = ms[order_kern[r][1]];
+    for (auto& ok : order_kern) cand.slices &= ~(1 << ok[0]);
+    if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
+    for (int r = 0; r < 4; ++r) {
+      t_off[r] = ms[order_kern[r][1]];
+      if (t_off[r] > 0.0 && t_off[r] < t_on[r])
+        sc.slices &= ~(1 << order_kern[r][0]);
+      else
+        sc.slices |= 1 << order_kern[r][0];
+    }
+  }
+  // 2. element sweep block: eb = 32, 16, 8, 4 elements (parts of one ELL group), the cap eb * n_loc
   double best = 1e300;
-  int last_npb = -1, best_cap = sc.high_cap;
-  for (int cap : {64, 96, 128, 160, gdg::kHighMaxBlock}) {
-    const int npb = gdg::high_nodes_per_block(n_loc, cap);
-    if (npb < 1 || npb == last_npb) continue;
-    last_npb = npb;
+  int best_cap = sc.high_cap;
+  for (int eb = gdg::kEll; eb >= 4; eb >>= 1) {
+    const int cap = eb * n_loc;
+    if (cap > gdg::kHighMaxBlock) continue;
     gdg::Sched cand = sc;
     cand.high_cap = cap;
     if (int rc = trial(cand, ms); rc != GDG_OK) return rc;
@@ -177,6 +199,11 @@ inline void sched_to_public(const gdg::Sched& sc, gdg_schedule* out) {
   out->maxdt_threads = sc.bt[gdg::KN_MAXDT];
   out->high_block_cap = sc.high_cap;
   out->lsfix_slots = sc.lsfix_slots;
+  static const int map[][2] = {{gdg::KN_MAXDT, GDG_K_MAXDT}, {gdg::KN_LOW, GDG_K_LOW}, {gdg::KN_LIMIT2, GDG_K_LIMIT2},
+                               {gdg::KN_FINAL, GDG_K_FINAL}, {gdg::KN_TAU, GDG_K_TAU}};
+  out->row_slices = 0;
+  for (auto& mp : map)
+    if ((sc.slices >> mp[0]) & 1) out->row_slices |= 1 << mp[1];
 }
 
 inline bool sched_from_public(const gdg_schedule* in, gdg::Sched* sc) {
@@ -186,6 +213,9 @@ inline bool sched_from_public(const gdg_schedule* in, gdg::Sched* sc) {
     if (v != 128 && v != 256 && v != 512) return false;
   if (in->high_block_cap < 1 || in->high_block_cap > gdg::kHighMaxBlock) return false;
   if (in->lsfix_slots < 1 || in->lsfix_slots > 1024) return false;
+  const int public_sliceable = (1 << GDG_K_MAXDT) | (1 << GDG_K_LOW) | (1 << GDG_K_LIMIT2) | (1 << GDG_K_FINAL) |
+                               (1 << GDG_K_TAU);
+  if (in->row_slices & ~public_sliceable) return false;
   *sc = gdg::default_sched();
   sc->bt[gdg::KN_PRIM] = in->prim_threads;
   sc->bt[gdg::KN_EDGE] = in->edge_threads;
@@ -196,5 +226,10 @@ inline bool sched_from_public(const gdg_schedule* in, gdg::Sched* sc) {
   sc->bt[gdg::KN_MAXDT] = in->maxdt_threads;
   sc->high_cap = in->high_block_cap;
   sc->lsfix_slots = in->lsfix_slots;
+  static const int map[][2] = {{gdg::KN_MAXDT, GDG_K_MAXDT}, {gdg::KN_LOW, GDG_K_LOW}, {gdg::KN_LIMIT2, GDG_K_LIMIT2},
+                               {gdg::KN_FINAL, GDG_K_FINAL}, {gdg::KN_TAU, GDG_K_TAU}};
+  sc->slices = 0;
+  for (auto& mp : map)
+    if ((in->row_slices >> mp[1]) & 1) sc->slices |= 1 << mp[0];
   return true;
 }

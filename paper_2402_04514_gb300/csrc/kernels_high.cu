@@ -12,40 +12,27 @@ namespace {
 constexpr int kMaxBlock = kHighMaxBlock;
 constexpr int kMaxLocal = 32;  // n_loc limit of gdg_setup
 
-// Thread-to-node map of an element block.  Lanes that take the same trip counts through the row loops
-// should share a warp, so the block's nodes are dealt out by local index: the epb = npb / n_loc elements
-// of the block take consecutive threads for one local index, and the local indices come in order of
-// decreasing row length (taken from the block's first element; rows of equal length keep their order).
-// When every local index has the same row length the identity map is kept, so that the per-node loads
-// of an element stay contiguous.  Returns the position of thread t's node within the block (the element
-// is slot / n_loc, the local index slot % n_loc); threads past npb keep t.  *pad is set to 1 when the
-// shared arrays should space elements n_loc + 1 apart: under the dealt-out map the lanes of a warp read
-// one node of each of several elements, and an even n_loc would put them in the same shared bank.
-__device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t, int* s_order, int* s_uneven,
-                                            int* pad) {
-  const int nl = D.n_loc;
-  if (t == 0) *s_uneven = 0;
-  __syncthreads();
-  if (t < nl) {
-    const long long first = (long long)lb * npb;  // the block's first element always exists
-    auto len = [&](int l) {
-      const long long v = first + l;
-      return v < D.n ? D.row_ptr[v + 1] - D.row_ptr[v] : 0;
-    };
-    const int mine = len(t);
-    int rank = 0;
-    for (int o = 0; o < nl; ++o) {
-      const int lo = len(o);
-      rank += (lo > mine) || (lo == mine && o < t);
-      if (lo != mine) *s_uneven = 1;
-    }
-    s_order[rank] = t;
-  }
-  __syncthreads();
-  *pad = *s_uneven && !(nl & 1);
-  if (!*s_uneven || t >= npb) return t;
-  const int epb = npb / nl;
-  return (t % epb) * nl + s_order[t / epb];
+// Thread-to-node map of an element block.  A block holds eb elements (a power of two <= kEll) of one
+// ELL group of kEll consecutive elements: block lb of an instance takes group g = lb / (kEll / eb) and its
+// elements e0 .. e0 + eb - 1 with e0 = (lb % (kEll / eb)) eb.  Thread t takes local index t / eb of
+// element e0 + t % eb, so the lanes of a warp hold one local index of consecutive elements: rows of one
+// shape (equal trip counts through the row loops) whose entries lie side by side in the ELL slices.
+struct ElemSlot {
+  int i;      // the node, valid only if ok
+  int el, l;  // the element's place in the block and the node's local index
+  bool ok;
+};
+__device__ __forceinline__ ElemSlot element_slot(const Dev& D, int lb, int eb) {
+  const int per_group = kEll / eb;
+  const int g = lb / per_group;
+  const int t = threadIdx.x;
+  ElemSlot r;
+  r.l = t / eb;
+  r.el = t - r.l * eb;
+  const int E = g * kEll + (lb - g * per_group) * eb + r.el;
+  r.ok = r.l < D.n_loc && E < D.nel;
+  r.i = E * D.n_loc + r.l;
+  return r;
 }
 
 // Per node i of the block:
@@ -64,15 +51,13 @@ __device__ __forceinline__ int element_slot(const Dev& D, int lb, int npb, int t
 // The mixed path (MX) runs steps 1, 2 and the A_ij of step 4 in FP32 (the differences U_j - U_i in FP64
 // first); the bounds and the line search stay FP64.
 template <int DIM, bool MX, class Src>
-__device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) {
+__device__ __forceinline__ void high_sweep(const Src& src, int eb) {
   constexpr int M = DIM + 2;
-  constexpr int kShared = kMaxBlock + kMaxBlock / 2;  // room for one pad slot per element of 2+ nodes
-  using R = std::conditional_t<MX, float, double>;    // arithmetic of steps 1, 2 and the A_ij of step 4
+  constexpr int kShared = kMaxBlock + kEll;        // room for one pad slot per element
+  using R = std::conditional_t<MX, float, double>;  // arithmetic of steps 1, 2 and the A_ij of step 4
   __shared__ R sR[M][kShared];
   __shared__ R sdU[M][kShared];
   __shared__ Ctx sctx;
-  __shared__ int s_order[kMaxLocal];
-  __shared__ int s_uneven;
   int lb;
   const Ctx& c = src.get(&sctx, &lb);
   if (finished(c)) return;
@@ -80,11 +65,14 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
   const Scratch& S = c.S;
   const double* U = c.U;
   const double* bdata = c.bdata;
-  int pad;
-  const int slot = element_slot(D, lb, nodes_per_block, threadIdx.x, s_order, &s_uneven, &pad);
-  const int i = lb * nodes_per_block + slot;
-  const bool valid = slot < nodes_per_block && i < D.n;
-  const int sh = slot + pad * (slot / D.n_loc);  // slot in the shared arrays
+  const ElemSlot es = element_slot(D, lb, eb);
+  const int i = es.i;
+  const bool valid = es.ok;
+  // the shared arrays space elements n_loc + 1 apart for even n_loc: the lanes of a warp read one node of
+  // each of consecutive elements, and an even stride would put pairs of them in the same bank
+  const int stride_sh = D.n_loc + !(D.n_loc & 1);
+  const int t0 = es.el * stride_sh;  // the element's first slot in the shared arrays
+  const int sh = t0 + es.l;
   const size_t n = D.n;
   const double tau = stage_tau(c);
   const R tau_r = MX ? R(to_f32(tau)) : R(tau);
@@ -114,7 +102,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
       sl = S.agg[2 * n + i];
     }
 #pragma unroll 2
-    for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
+    for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
       const int j = __ldg(D.col + e);
       const double dl64 = __ldg(S.dL + e), mu = __ldg(D.mu + e), Nj = abs_bits(__ldg(S.N + j));
       double Uj[M];
@@ -190,18 +178,18 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
   if (valid) {
     const int nl = D.n_loc;
     const int ei = div_nl(D, i);
-    const int il = i - ei * nl;
-    const int t0 = sh - il;  // first node of the element in the shared arrays
-    const double* Minv = D.MKinv + ((size_t)ei * nl + il) * nl;
+    // row il of the element's M_K^{-1}, stored grouped like the entries: (E, a, b) at
+    // ((E / kEll * n_loc + a) * n_loc + b) * kEll + E % kEll
+    const double* Minv = D.MKinv + ((size_t)(ei / kEll) * nl + es.l) * nl * kEll + (ei % kEll);
     R acc[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) acc[q] = R(0);
     for (int l = 0; l < nl; ++l) {
       R w;
       if constexpr (MX)
-        w = to_f32(Minv[l]);
+        w = to_f32(Minv[(size_t)l * kEll]);
       else
-        w = Minv[l];
+        w = Minv[(size_t)l * kEll];
 #pragma unroll
       for (int q = 0; q < M; ++q) acc[q] += w * sR[q][t0 + l];
     }
@@ -237,8 +225,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
   const float ikmf = d2f_fast(ikm);
   const int nl = D.n_loc;
   const int elem = div_nl(D, i);
-  const int t0 = sh - (i - elem * nl);
-  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+  for (int e = D.rbeg[i], e1 = D.rend[i]; e < e1; e += kEll) {
     int j = D.col[e];
     double A[M];
     const bool stencil = e < se;
@@ -295,47 +282,52 @@ __device__ __forceinline__ void high_sweep(const Src& src, int nodes_per_block) 
 // the FP64 pipe and memory latency, runs fastest at 72 registers (three 288-thread blocks per SM, a few
 // spills); the mixed path, whose FP32 work needs more live values, at 96.
 template <int DIM, class Src>
-__global__ void __maxnreg__(72) k_high(Src src, int nodes_per_block) {
-  high_sweep<DIM, false, Src>(src, nodes_per_block);
+__global__ void __maxnreg__(72) k_high(Src src, int eb) {
+  high_sweep<DIM, false, Src>(src, eb);
 }
 template <int DIM, class Src>
-__global__ void __maxnreg__(96) k_high_mixed(Src src, int nodes_per_block) {
-  high_sweep<DIM, true, Src>(src, nodes_per_block);
+__global__ void __maxnreg__(96) k_high_mixed(Src src, int eb) {
+  high_sweep<DIM, true, Src>(src, eb);
 }
 
+// eb: elements per block, a power of two <= kEll with eb * n_loc <= kMaxBlock (one element may exceed
+// no block: n_loc <= kMaxLocal); n_loc is the one of the instance (a batch shares it).
 template <int DIM, bool MX, class Src>
-cudaError_t high_launch(const Src& src, long long blocks, int npb, cudaStream_t s) {
+cudaError_t high_launch(const Src& src, long long blocks, int n_loc, int eb, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  if (npb < 1 || npb > kMaxBlock) return cudaErrorInvalidValue;
+  if (eb < 1 || eb > kEll || (eb & (eb - 1)) || n_loc < 1 || n_loc > kMaxLocal || eb * n_loc > kMaxBlock)
+    return cudaErrorInvalidValue;
+  const int threads = high_threads(n_loc, eb);
   if constexpr (MX)
-    k_high_mixed<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
+    k_high_mixed<DIM, Src><<<(unsigned)blocks, threads, 0, s>>>(src, eb);
   else
-    k_high<DIM, Src><<<(unsigned)blocks, high_threads(npb), 0, s>>>(src, npb);
+    k_high<DIM, Src><<<(unsigned)blocks, threads, 0, s>>>(src, eb);
   return cudaGetLastError();
 }
 
 template <class Src>
-cudaError_t high_dispatch(int dim, bool mx, const Src& src, long long blocks, int npb, cudaStream_t s) {
+cudaError_t high_dispatch(int dim, bool mx, const Src& src, long long blocks, int n_loc, int eb, cudaStream_t s) {
   switch (dim * 2 + (mx ? 1 : 0)) {
-    case 2: return high_launch<1, false, Src>(src, blocks, npb, s);
-    case 3: return high_launch<1, true, Src>(src, blocks, npb, s);
-    case 4: return high_launch<2, false, Src>(src, blocks, npb, s);
-    case 5: return high_launch<2, true, Src>(src, blocks, npb, s);
-    case 6: return high_launch<3, false, Src>(src, blocks, npb, s);
-    case 7: return high_launch<3, true, Src>(src, blocks, npb, s);
+    case 2: return high_launch<1, false, Src>(src, blocks, n_loc, eb, s);
+    case 3: return high_launch<1, true, Src>(src, blocks, n_loc, eb, s);
+    case 4: return high_launch<2, false, Src>(src, blocks, n_loc, eb, s);
+    case 5: return high_launch<2, true, Src>(src, blocks, n_loc, eb, s);
+    case 6: return high_launch<3, false, Src>(src, blocks, n_loc, eb, s);
+    case 7: return high_launch<3, true, Src>(src, blocks, n_loc, eb, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-// npb: nodes per block, whole elements (all instances of a batch share n_loc, hence the block shape).
-cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int npb, cudaStream_t s) {
-  return high_dispatch(dim, c.D.mixed != 0, One{c}, blocks, npb, s);
+// eb: elements per block (all instances of a batch share n_loc, hence the block shape).
+cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int eb, cudaStream_t s) {
+  return high_dispatch(dim, c.D.mixed != 0, One{c}, blocks, c.D.n_loc, eb, s);
 }
 
-cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, long long blocks, int npb, cudaStream_t s) {
-  return high_dispatch(dim, mixed, m, blocks, npb, s);
+cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, int n_loc, long long blocks, int eb,
+                                  cudaStream_t s) {
+  return high_dispatch(dim, mixed, m, blocks, n_loc, eb, s);
 }
 
 }  // namespace gdg

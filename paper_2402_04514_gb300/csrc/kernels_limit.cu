@@ -15,7 +15,7 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // sums, which every row runs, need far fewer, and the searches of the rare rows with a remainder would
 // otherwise set the kernel's occupancy.
 template <int DIM, class Src>
-__global__ void __maxnreg__(72) k_limit2(Src src, int last) {
+__global__ void __maxnreg__(72) k_limit2(Src src, int sliced, int last) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -23,15 +23,15 @@ __global__ void __maxnreg__(72) k_limit2(Src src, int last) {
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
-  const int i = lb * blockDim.x + threadIdx.x;
-  if (i >= D.n) return;
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  if (i < 0) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   double acc[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
-  const int r0 = D.row_ptr[i], r1 = D.row_ptr[i + 1];
+  const int r0 = D.rbeg[i], r1 = D.rend[i];
   bool remainder = false;  // some entry has l1 < 1, so that pass 2 has a remainder to limit
-  for (int e = r0; e < r1; ++e) {
+  for (int e = r0; e < r1; e += kEll) {
     double l = pmin(S.l1[e], S.l1[D.tr[e]]);  // limiter coefficients are in [0, 1]: integer min
     remainder |= !is_one_bits(l);
 #pragma unroll
@@ -61,7 +61,7 @@ __global__ void __maxnreg__(72) k_limit2(Src src, int last) {
   LsRow<DIM> ls;
   ls_row<DIM>(D, ls, U1, S.bounds[i], S.bounds[n + i], S.bounds[2 * n + i]);
   const double ikm = D.inv_km[i];
-  for (int e = r0; e < r1; ++e) {
+  for (int e = r0; e < r1; e += kEll) {
     const double l1s = pmin(S.l1[e], S.l1[D.tr[e]]);
     if (is_one_bits(l1s)) continue;
     const double w = (1.0 - l1s) * ikm;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
 // Sweep D: U^(2)_i = U^(1)_i + (sum_j l2_ij (1 - l1_ij) A_ij + sum_k l2_i^k (1 - l1_i^k) A_i^k) / m_i,
 // symmetrised as in sweep C, and U_out = alpha U_base + (1 - alpha) U^(2).
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kThreads) k_final(Src src) {
+__global__ void __launch_bounds__(kThreads) k_final(Src src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
-  const int i = lb * blockDim.x + threadIdx.x;
-  if (i >= D.n) return;
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  if (i < 0) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   if (!S.rem[i]) {  // no remainder in the row: U^(2)_i = U^(1)_i
 #pragma unroll
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src) {
 #pragma unroll
   for (int q = 0; q < M; ++q) acc[q] = 0.0;
   // an entry with l1 = 1 has no remainder (its weight is 0): skipped, with the loads of its A
-  for (int e = D.row_ptr[i]; e < D.row_ptr[i + 1]; ++e) {
+  for (int e = D.rbeg[i], e1 = D.rend[i]; e < e1; e += kEll) {
     int t = D.tr[e];
     const double l1s = pmin(S.l1[e], S.l1[t]);
     if (is_one_bits(l1s)) continue;
@@ -218,13 +218,14 @@ __global__ void __launch_bounds__(kThreads) k_axpy(Src src) {
 }
 
 template <int DIM, class Src>
-cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads, int arg, cudaStream_t s) {
+cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads, int sliced, int arg,
+                         cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
-    case KN_LIMIT2: k_limit2<DIM, Src><<<g, threads, 0, s>>>(src, arg); break;
-    case KN_FINAL: k_final<DIM, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_LIMIT2: k_limit2<DIM, Src><<<g, threads, 0, s>>>(src, sliced, arg); break;
+    case KN_FINAL: k_final<DIM, Src><<<g, threads, 0, s>>>(src, sliced); break;
     case KN_AXPY: k_axpy<DIM, Src><<<g, threads, 0, s>>>(src); break;
     case KN_LSFIX: k_lsfix<DIM, Src><<<g, kLsfixThreads, 0, s>>>(src, arg); break;
     default: return cudaErrorInvalidValue;
@@ -234,23 +235,23 @@ cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads
 
 }  // namespace
 
-cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
                               cudaStream_t s) {
   const One src{c};
   switch (dim) {
-    case 1: return limit_launch<1, One>(kern, src, blocks, threads, arg, s);
-    case 2: return limit_launch<2, One>(kern, src, blocks, threads, arg, s);
-    case 3: return limit_launch<3, One>(kern, src, blocks, threads, arg, s);
+    case 1: return limit_launch<1, One>(kern, src, blocks, threads, sliced, arg, s);
+    case 2: return limit_launch<2, One>(kern, src, blocks, threads, sliced, arg, s);
+    case 3: return limit_launch<3, One>(kern, src, blocks, threads, sliced, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int arg,
-                                   cudaStream_t s) {
+cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int sliced,
+                                   int arg, cudaStream_t s) {
   switch (dim) {
-    case 1: return limit_launch<1, Many>(kern, m, blocks, threads, arg, s);
-    case 2: return limit_launch<2, Many>(kern, m, blocks, threads, arg, s);
-    case 3: return limit_launch<3, Many>(kern, m, blocks, threads, arg, s);
+    case 1: return limit_launch<1, Many>(kern, m, blocks, threads, sliced, arg, s);
+    case 2: return limit_launch<2, Many>(kern, m, blocks, threads, sliced, arg, s);
+    case 3: return limit_launch<3, Many>(kern, m, blocks, threads, sliced, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }

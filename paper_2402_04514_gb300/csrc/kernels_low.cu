@@ -116,7 +116,7 @@ __device__ __forceinline__ void block_min_to(double val, unsigned long long* dst
 // eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|), with d_ij^L evaluated here
 // (gdg_max_dt, before any stage).
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
+__global__ void __launch_bounds__(kThreads) k_maxdt(Src src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
   const Dev& D = c.D;
   const Scratch& S = c.S;
   const double* U = c.U;
-  const int i = lb * blockDim.x + threadIdx.x;
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
   double val = INFINITY;
-  if (i < D.n) {
+  if (i >= 0) {
     size_t n = D.n;
     double Ui[M];
     load_state<DIM>(U, D.n, i, Ui);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
            pme_i = P[PR_PME * n + i];
     double dsum = 0.0;
     const int e1 = D.sten_end[i];
-    for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
+    for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
       double cnm = D.cnorm[e];
       int j = D.col[e];
       double nv[DIM], uL = 0.0, uR = 0.0;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src) {
 // 48 registers: the row sum, which every row runs, is latency-bound and wants many warps; the boundary
 // viscosities of the few boundary rows would otherwise take 117 and spill at the cap.
 template <int DIM, bool MX, class Src>
-__global__ void __maxnreg__(48) k_tau(Src src) {
+__global__ void __maxnreg__(48) k_tau(Src src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -172,13 +172,13 @@ __global__ void __maxnreg__(48) k_tau(Src src) {
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
-  const int i = lb * blockDim.x + threadIdx.x;
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
   double val = INFINITY;
-  if (i < D.n) {
+  if (i >= 0) {
     double dsum = 0.0;
-    const int e0 = D.row_ptr[i], e1 = D.sten_end[i];
+    const int e0 = D.rbeg[i], e1 = D.sten_end[i];
 #pragma unroll 4
-    for (int e = e0; e < e1; ++e) dsum += __ldg(S.dL + e);  // loads issued ahead of the in-order sum
+    for (int e = e0; e < e1; e += kEll) dsum += __ldg(S.dL + e);  // loads issued ahead of the in-order sum
     const int b0 = D.b_ptr[i], b1 = D.b_ptr[i + 1];
     if (b0 < b1) {
       const size_t n = D.n;
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
 // The mixed path (MX) computes the indicator in FP32 (its sums from FP64 flux differences) and the
 // boundary wave-speed bounds with lambda_pair<true>; the low-order update stays FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
+__global__ void __launch_bounds__(kThreads) k_low(Src src, int sliced, int write_out) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   const Dev& D = c.D;
   const Scratch& S = c.S;
   const double* U = c.U;
-  const int i = lb * blockDim.x + threadIdx.x;
-  if (i >= D.n) return;
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  if (i < 0) return;
   const double tau = stage_tau(c);
   size_t n = D.n;
   const double* P = S.prim;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
   double lo = Ui[0], hi = Ui[0], sl = st_i;
   const size_t nnz = D.nnz;
   const int e1 = D.sten_end[i];
-  for (int e = D.row_ptr[i]; e < e1; ++e) {  // I(i)
+  for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
     const int j = D.col[e], t = D.tr[e];
     const double d = S.dL[e];
     dsum += d;
@@ -467,31 +467,31 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int write_out) {
 }
 
 template <int DIM, bool MX, class Src>
-cudaError_t low_launch(int kern, const Src& src, long long blocks, int threads, int arg, cudaStream_t s) {
+cudaError_t low_launch(int kern, const Src& src, long long blocks, int threads, int sliced, int arg, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
     case KN_PRIM: k_prim<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_MAXDT: k_maxdt<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_TAU: k_tau<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
+    case KN_MAXDT: k_maxdt<DIM, MX, Src><<<g, threads, 0, s>>>(src, sliced); break;
+    case KN_TAU: k_tau<DIM, MX, Src><<<g, threads, 0, s>>>(src, sliced); break;
     case KN_EDGE: k_edge<DIM, MX, Src><<<g, threads, 0, s>>>(src); break;
-    case KN_LOW: k_low<DIM, MX, Src><<<g, threads, 0, s>>>(src, arg); break;
+    case KN_LOW: k_low<DIM, MX, Src><<<g, threads, 0, s>>>(src, sliced, arg); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <class Src>
-cudaError_t low_dispatch(int kern, int dim, bool mx, const Src& src, long long blocks, int threads, int arg,
-                         cudaStream_t s) {
+cudaError_t low_dispatch(int kern, int dim, bool mx, const Src& src, long long blocks, int threads, int sliced,
+                         int arg, cudaStream_t s) {
   switch (dim * 2 + (mx ? 1 : 0)) {
-    case 2: return low_launch<1, false, Src>(kern, src, blocks, threads, arg, s);
-    case 3: return low_launch<1, true, Src>(kern, src, blocks, threads, arg, s);
-    case 4: return low_launch<2, false, Src>(kern, src, blocks, threads, arg, s);
-    case 5: return low_launch<2, true, Src>(kern, src, blocks, threads, arg, s);
-    case 6: return low_launch<3, false, Src>(kern, src, blocks, threads, arg, s);
-    case 7: return low_launch<3, true, Src>(kern, src, blocks, threads, arg, s);
+    case 2: return low_launch<1, false, Src>(kern, src, blocks, threads, sliced, arg, s);
+    case 3: return low_launch<1, true, Src>(kern, src, blocks, threads, sliced, arg, s);
+    case 4: return low_launch<2, false, Src>(kern, src, blocks, threads, sliced, arg, s);
+    case 5: return low_launch<2, true, Src>(kern, src, blocks, threads, sliced, arg, s);
+    case 6: return low_launch<3, false, Src>(kern, src, blocks, threads, sliced, arg, s);
+    case 7: return low_launch<3, true, Src>(kern, src, blocks, threads, sliced, arg, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -500,14 +500,14 @@ cudaError_t low_dispatch(int kern, int dim, bool mx, const Src& src, long long b
 
 // Launchers of this file's kernels, dispatched on the dimension and the precision (called by
 // launch_kernel*).
-cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int arg,
+cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
                             cudaStream_t s) {
-  return low_dispatch(kern, dim, c.D.mixed != 0, One{c}, blocks, threads, arg, s);
+  return low_dispatch(kern, dim, c.D.mixed != 0, One{c}, blocks, threads, sliced, arg, s);
 }
 
-cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads, int arg,
-                                 cudaStream_t s) {
-  return low_dispatch(kern, dim, mixed, m, blocks, threads, arg, s);
+cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, long long blocks, int threads,
+                                 int sliced, int arg, cudaStream_t s) {
+  return low_dispatch(kern, dim, mixed, m, blocks, threads, sliced, arg, s);
 }
 
 }  // namespace gdg

@@ -58,11 +58,12 @@ class _Info(C.Structure):
 
 class Schedule(C.Structure):
     """gdg_schedule: launch shapes (threads per block of the row kernels, element block cap, deferred
-    line-search slots per thread)."""
+    line-search slots per thread, row order of the kernels with per-entry loops)."""
 
     _fields_ = [("prim_threads", C.c_int32), ("edge_threads", C.c_int32), ("tau_threads", C.c_int32),
                 ("low_threads", C.c_int32), ("limit2_threads", C.c_int32), ("final_threads", C.c_int32),
-                ("maxdt_threads", C.c_int32), ("high_block_cap", C.c_int32), ("lsfix_slots", C.c_int32)]
+                ("maxdt_threads", C.c_int32), ("high_block_cap", C.c_int32), ("lsfix_slots", C.c_int32),
+                ("row_slices", C.c_int32)]
 
 
 class RequestInfo(C.Structure):

@@ -15,6 +15,8 @@ SCHEDULES = [
          final_threads=128, high_block_cap=96, lsfix_slots=16),
     dict(high_block_cap=37, lsfix_slots=3),  # a cap that is not a multiple of 32 (ragged blocks)
     dict(high_block_cap=288),  # the largest element block (32 Q2 elements)
+    dict(row_slices=0),  # every row kernel in node order
+    dict(row_slices=(1 << 2) | (1 << 5), high_block_cap=1),  # k_low and k_final sliced; one element per block
 ]
 
 
@@ -72,7 +74,8 @@ def test_autotune_restores_state_and_clock(torch_cuda):
     assert np.array_equal(Ud.cpu().numpy(), before) and S.clock() == clk and S.status() == 0
     for f in ("prim_threads", "edge_threads", "tau_threads", "low_threads", "limit2_threads", "final_threads"):
         assert sc[f] in (128, 256, 512)
-    assert sc["high_block_cap"] in (64, 96, 128, 160, 288) and sc["lsfix_slots"] in (1, 4, 16)
+    assert sc["high_block_cap"] in (36, 72, 144, 288) and sc["lsfix_slots"] in (1, 4, 16)  # 4..32 Q2 elements
+    assert sc["row_slices"] & ~((1 << 1) | (1 << 2) | (1 << 4) | (1 << 5) | (1 << 8)) == 0
     # the tuned schedule continues the same trajectory as the default one
     S.step(Ud, work)
     S2 = Solver(P)
@@ -113,6 +116,7 @@ def test_invalid_schedules_are_refused(torch_cuda):
 
     P, _ = _instance(5, 1, 1)
     S = Solver(P)
-    for bad in (dict(low_threads=96), dict(high_block_cap=0), dict(high_block_cap=289), dict(lsfix_slots=0)):
+    for bad in (dict(low_threads=96), dict(high_block_cap=0), dict(high_block_cap=289), dict(lsfix_slots=0),
+                dict(row_slices=1 << 3)):
         with pytest.raises(GdgError):
             S.set_schedule(**bad)
