@@ -82,46 +82,25 @@ def run_oracle(ne, strategy, M, openmp=True):
     return consolidated_l1(P, U, exact(P.x[0], P.x[1], tF, M))
 
 
-def run_gpu(ne, strategy, M, torch, exact_fn=None, far_fn=None):
-    """The same run on the GPU through gdg_stage: each forward-Euler stage runs in the library with its
-    boundary data at the stage time; the Shu-Osher combinations of SSPRK(5,4) are formed from the
-    stages' outputs (gdg_stage's U_out = alpha U_base + (1 - alpha) FE(U_in) covers every stage but the
-    last, whose base is a combination of u2 and FE(u3) = (u4 - alpha40 u0) / alpha43).  Returns the L1
-    error at t_F."""
-    from oracle import ssprk
+def run_gpu(ne, strategy, M, torch):
+    """The same run on the GPU (tests/gpu_rk.py: every forward-Euler stage in the library with its data at
+    the stage's time).  Returns the L1 error at t_F."""
     from paper_2402_04514_gb300.gdg import Solver
+    from tests.gpu_rk import ssprk54_solve
 
-    exact_fn = exact_fn or exact
-    far_fn = far_fn or far_field
-    A, B = ssprk.SSPRK54_ALPHA, ssprk.SSPRK54_BETA
-    _, _, c = ssprk.butcher(A, B)
-    C = ssprk.ssp_coefficient(A, B)
     P = problem(ne, strategy)
-    S = Solver(P, gamma=GAMMA)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    U = dev(exact_fn(P.x[0], P.x[1], 0.0, M))
-    ff = dev(far_fn(P, M))
-    t, tF = 0.0, 6.0 / M
+    tF = 6.0 / M
+    ff = far_field(P, M)
 
-    def bd(time, Ustart):
+    def bdata(t, U_start):
         if strategy in ("a", "b"):
-            return dev(exact_fn(P.b_x[0], P.b_x[1], time, M))
+            return exact(P.b_x[0], P.b_x[1], t, M)
         if strategy == "c":
             return ff
-        return Ustart[:, torch.from_numpy(P.b_node.astype(np.int64)).cuda()].contiguous()
+        return U_start[:, torch.from_numpy(P.b_node.astype(np.int64)).cuda()].contiguous()
 
-    while t < tF - 1e-12:
-        dt = min(CFL * C * S.max_dt(U, 1.0, bdata=bd(t, U)), tF - t)
-        tau = lambda i, j: B[i][j] / A[i][j] * dt
-        u1 = S.stage(U, tau(0, 0), bdata=bd(t + c[0] * dt, U))
-        u2 = S.stage(u1, tau(1, 1), U_base=U, alpha=A[1][0], bdata=bd(t + c[1] * dt, U))
-        u3 = S.stage(u2, tau(2, 2), U_base=U, alpha=A[2][0], bdata=bd(t + c[2] * dt, U))
-        u4 = S.stage(u3, tau(3, 3), U_base=U, alpha=A[3][0], bdata=bd(t + c[3] * dt, U))
-        base = (A[4][2] * u2 + (A[4][3] / A[3][3]) * (u4 - A[3][0] * U)) / (1.0 - A[4][4])
-        U = S.stage(u4, tau(4, 4), U_base=base, alpha=1.0 - A[4][4], bdata=bd(t + c[4] * dt, U))
-        t += dt
-    assert S.status() == 0
-    return consolidated_l1(P, U.cpu().numpy(), exact_fn(P.x[0], P.x[1], tF, M))
+    U = ssprk54_solve(Solver(P, gamma=GAMMA), exact(P.x[0], P.x[1], 0.0, M), bdata, tF, torch, CFL)
+    return consolidated_l1(P, U, exact(P.x[0], P.x[1], tF, M))
 
 
 if __name__ == "__main__":
