@@ -145,6 +145,46 @@ def oracle_full_size_rate(P, U, steps):
     return P.n * 3 * steps / dt, dt, om.threads(True)
 
 
+def measure_developed(N=256, t_dev=0.05, steps=20):
+    """How representative steps from the initial data are: the same four-quadrant Q2 problem on N^2 quads,
+    stepped to t_dev (the waves then cross a good part of the domain), against its first steps.  Returns
+    ms per SSP-RK3 step at the start and at t_dev (autotuned once at the start, as the main line)."""
+    import torch
+
+    from paper_2402_04514_gb300.gdg import Solver
+
+    P, U0 = make_problem(dict(N=N, k=2, seed=0))
+    S = Solver(P)
+    S.set_clock(0.0, float("inf"), 0.5)
+    U = torch.from_numpy(U0).cuda()
+    work = (torch.empty_like(U), torch.empty_like(U))
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        S.step(U, work)
+    S.autotune(U, work, trials=1)
+
+    def timed():
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            S.step(U, work)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    early = timed()
+    taken = 3 + steps
+    while S.clock()[0] < t_dev:
+        for _ in range(50):
+            S.step(U, work)
+        taken += 50
+    late = timed()
+    return {"workload": f"Q2 {N}x{N} four-quadrant (seed 0), the same sweep and schedule", "ms_per_step_initial": early,
+            "ms_per_step_developed": late, "t_developed": S.clock()[0], "steps_taken": taken + steps,
+            "ratio": late / early, "status_flags": S.status()}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -227,6 +267,11 @@ def measure_batched(instances, steps, warmup, autotune=True):
     sampler.start()
     t_batch = timed(B.step, steps)
     t_single = timed(one_at_a_time, steps)
+    # the same batch as one cooperative launch per stage (gdg_batch_set_persistent)
+    B.set_persistent(True)
+    B.step()
+    t_persist = timed(B.step, steps)
+    B.set_persistent(False)
     clocks = sampler.stop()
     flags = max(S.status() for S in solvers)
     B.close()
@@ -245,6 +290,9 @@ def measure_batched(instances, steps, warmup, autotune=True):
             "one_at_a_time": {"value": inst * steps / SOLVE_STEPS / t_single, "unit": "solves/s",
                               "ms_per_step": 1e3 * t_single / steps,
                               "dof_stage_per_s": dofs * 3 * steps / t_single},
+            "persistent": {"value": inst * steps / SOLVE_STEPS / t_persist, "unit": "solves/s",
+                           "ms_per_step": 1e3 * t_persist / steps, "gpu_launches": 3 * steps,
+                           "launch": "one cooperative launch per SSP-RK3 stage over all instances"},
             "speedup_vs_one_at_a_time": t_single / t_batch, "gpu_launches": 26 * steps,
             "clocks": clocks, "status_flags": flags}
 
@@ -257,8 +305,8 @@ def run_batched(args):
     line = {"metric": "batched solves/s", "value": r["value"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": r["config"],
-            **{k: r[k] for k in ("dof_stage_per_s", "one_at_a_time", "speedup_vs_one_at_a_time", "gpu_launches",
-                                 "clocks", "status_flags")}}
+            **{k: r[k] for k in ("dof_stage_per_s", "one_at_a_time", "persistent", "speedup_vs_one_at_a_time",
+                                 "gpu_launches", "clocks", "status_flags")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -401,6 +449,8 @@ def main():
     ap.add_argument("--t-cap", type=float, default=None, help="served workload: cap on the end times")
     ap.add_argument("--skip-one-at-a-time", action="store_true", help="served workload: no one-at-a-time run")
     ap.add_argument("--no-batched", action="store_true", help="main line: skip the batched sample")
+    ap.add_argument("--no-developed", action="store_true",
+                    help="main line: skip the step cost of a developed flow (Q2 256^2 at t = 0.05)")
     ap.add_argument("--no-served", action="store_true", help="main line: skip the served sample")
     ap.add_argument("--cpu-c3-steps", type=int, default=3,
                     help="main line: SSP-RK3 steps of the all-core oracle on the full mesh (0: none)")
@@ -567,7 +617,9 @@ def main():
         return 0
     # the batched and served workloads, measured on samples sized to end in about a minute each (their own
     # --workload runs take any size)
-    batched = served = None
+    batched = served = developed = None
+    if world == 1 and not args.no_developed:
+        developed = measure_developed()
     if world == 1 and not args.no_batched:
         batched = measure_batched(COMBINED_BATCH_INSTANCES, steps=3, warmup=1)
     if world == 1 and not args.no_served:
@@ -596,6 +648,8 @@ def main():
             "roofline": res["roofline"], "roofline_hbm" if not main_mixed else "roofline_alu": res["other"],
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["launches"] * world,
             "clocks": res["clocks"], "kernels": res["kernels"], "status_flags": res["flags"]}
+    if developed is not None:
+        line["developed_flow"] = developed
     if batched is not None:
         line["batched"] = batched
     if served is not None:

@@ -339,6 +339,14 @@ typedef struct gdg_batch gdg_batch;
 int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U, double* const* T1,
                      double* const* T2, const double* const* bdata, gdg_batch** out);
 int gdg_batch_step(gdg_batch* b, void* stream);
+/* gdg_batch_set_persistent: on = 1 runs each later gdg_batch_step as one cooperative launch per stage
+ * (3 launches per step instead of 26), whose phases (the kernels of the stage, Sec. 6.1, for every
+ * member) are separated by grid-wide barriers at the sweep's grid-wide dependencies, with one block per
+ * co-resident slot of the GPU (cudaLaunchCooperativeKernel); on = 0 returns to one launch per kernel.
+ * The results are the same bits either way.  Persistent steps are not captured into the batch's graph
+ * and record no kernel times (gdg_batch_profile).  Errors: GDG_EINVAL; at step time GDG_ENOTSUP where
+ * the device has no cooperative launch. */
+int gdg_batch_set_persistent(gdg_batch* b, int32_t on);
 int gdg_batch_profile(gdg_batch* b, int32_t enable);
 int gdg_batch_profile_read(gdg_batch* b, double* total_ms, int64_t* launches);
 /* gdg_batch_autotune: as gdg_autotune for the whole batch (every member's state and clock saved and

@@ -19,6 +19,12 @@ struct gdg_batch {
   gdg::Ctx* ctx[3] = {nullptr, nullptr, nullptr};  // [count] contexts of the three stages
   int* start[gdg::KN_COUNT] = {};      // [count + 1] block offsets of each kernel
   long long blocks[gdg::KN_COUNT] = {};
+  // persistent mode (gdg_batch_set_persistent): one cooperative launch per stage of pblock threads, the
+  // element sweep in blocks of peb elements; pstart [KN_COUNT][count + 1] the virtual block offsets
+  bool persistent = false;
+  int pblock = 0, peb = 0;
+  int* pstart = nullptr;
+  long long pblocks[gdg::KN_COUNT] = {};
   // kernel timing, as gdg_profile
   struct Rec {
     int kernel;
@@ -57,21 +63,37 @@ cudaError_t launch_many(const gdg_batch* b, int kern, int stage, int arg, cudaSt
   }
 }
 
-// Block offsets of every kernel under the batch's schedule, uploaded into the batch's table (synchronous).
-int upload_offsets(gdg_batch* b) {
-  std::vector<int> start((size_t)gdg::KN_COUNT * (b->count + 1));
+// Block offsets of every kernel under a schedule into a host table, and the totals.
+int offsets(const gdg_batch* b, const gdg::Sched& sc, std::vector<int>& start, long long* blocks) {
+  start.assign((size_t)gdg::KN_COUNT * (b->count + 1), 0);
   for (int kern = 0; kern < gdg::KN_COUNT; ++kern) {
     long long acc = 0;
     int* st = &start[(size_t)kern * (b->count + 1)];
     for (int k = 0; k < b->count; ++k) {
       st[k] = (int)acc;
-      acc += gdg::kernel_blocks(kern, b->hs[k]->D, b->sched);
+      acc += gdg::kernel_blocks(kern, b->hs[k]->D, sc);
     }
     st[b->count] = (int)acc;
     if (acc > 0x7fffffffLL) return GDG_ENOTSUP;  // more blocks than a grid holds
-    b->blocks[kern] = acc;
+    blocks[kern] = acc;
   }
-  if (cudaMemcpy(b->start[0], start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+  return GDG_OK;
+}
+
+// Block offsets of every kernel under the batch's schedule, and those of the persistent mode (every
+// phase in blocks of pblock threads, the element sweep in the largest block of whole ELL-group parts that
+// fits them), uploaded into the batch's tables (synchronous).
+int upload_offsets(gdg_batch* b) {
+  std::vector<int> start, pstart;
+  if (int rc = offsets(b, b->sched, start, b->blocks); rc != GDG_OK) return rc;
+  b->peb = gdg::high_elems_per_block(b->n_loc, gdg::kHighMaxBlock);
+  b->pblock = gdg::high_threads(b->n_loc, b->peb);
+  gdg::Sched ps = b->sched;
+  for (int k = 0; k < gdg::KN_COUNT; ++k) ps.bt[k] = b->pblock;
+  ps.high_cap = b->peb * b->n_loc;
+  if (int rc = offsets(b, ps, pstart, b->pblocks); rc != GDG_OK) return rc;
+  if (cudaMemcpy(b->start[0], start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->pstart, pstart.data(), sizeof(int) * pstart.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_fail_b(cudaErrorUnknown);
   if (b->exec) {  // the captured step has the old shapes
     cudaGraphExecDestroy(b->exec);
@@ -135,6 +157,29 @@ int step_launches(gdg_batch* b, cudaStream_t s) {
   return e == cudaSuccess ? GDG_OK : cuda_fail_b(e);
 }
 
+// One fused SSP-RK3 step of every member in persistent mode: one cooperative launch per stage (the last
+// one also advances the clocks).
+int persistent_step(gdg_batch* b, cudaStream_t s) {
+  const bool low_only = b->order == GDG_ORDER_LOW || (b->order == GDG_ORDER_LIMITED && b->passes == 0);
+  for (int stage = 0; stage < 3; ++stage) {
+    gdg::PersistArgs a{};
+    a.ctx = b->ctx[stage];
+    a.start = b->pstart;
+    a.ninst = b->count;
+    a.stage = stage;
+    a.eb = b->peb;
+    a.low_only = low_only ? 1 : 0;
+    a.order = b->order;
+    a.passes = b->passes;
+    a.slices = b->sched.slices;
+    for (int k = 0; k < gdg::KN_COUNT; ++k) a.nblk[k] = (int)b->pblocks[k];
+    int grid = 0;
+    cudaError_t e = gdg::launch_stage_persistent(b->dim, b->mixed, a, b->pblock, &grid, s);
+    if (e != cudaSuccess) return e == cudaErrorNotSupported ? GDG_ENOTSUP : cuda_fail_b(e);
+  }
+  return GDG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -181,7 +226,7 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
   }
   const size_t ctx_bytes = sizeof(gdg::Ctx) * ctx.size();
   const size_t start_bytes = sizeof(int) * (size_t)gdg::KN_COUNT * (count + 1);
-  cudaError_t e = cudaMalloc(&b->mem, ctx_bytes + start_bytes);
+  cudaError_t e = cudaMalloc(&b->mem, ctx_bytes + 2 * start_bytes);
   if (e != cudaSuccess) {
     b->mem = nullptr;
     cudaGetLastError();
@@ -196,6 +241,7 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
   for (int st = 0; st < 3; ++st) b->ctx[st] = (gdg::Ctx*)base + (size_t)st * count;
   for (int kern = 0; kern < gdg::KN_COUNT; ++kern)
     b->start[kern] = (int*)(base + ctx_bytes) + (size_t)kern * (count + 1);
+  b->pstart = (int*)(base + ctx_bytes + start_bytes);
   if (int rc = upload_offsets(b); rc != GDG_OK) {
     release(b);
     return rc;
@@ -207,6 +253,7 @@ int gdg_batch_create(gdg_handle* const* handles, int32_t count, double* const* U
 int gdg_batch_step(gdg_batch* b, void* stream) {
   if (!b) return GDG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->persistent) return persistent_step(b, s);
   // Every step launches the same kernels with the same arguments (the members' time steps live on the
   // device), so the step is captured once as a CUDA graph and replayed: one launch instead of ~26.  Not
   // on the legacy default stream (which cannot be captured) nor while profiling.
@@ -340,6 +387,12 @@ int gdg_batch_autotune(gdg_batch* b, int32_t trials, void* stream) {
   const int rc2 = put_back(clk0);
   cudaFree(save);
   return rc != GDG_OK ? rc : rc2;
+}
+
+int gdg_batch_set_persistent(gdg_batch* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return GDG_EINVAL;
+  b->persistent = on != 0;
+  return GDG_OK;
 }
 
 int gdg_batch_get_schedule(gdg_batch* b, gdg_schedule* out) {

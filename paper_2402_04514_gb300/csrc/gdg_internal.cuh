@@ -365,6 +365,20 @@ cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks,
                               cudaStream_t s);
 cudaError_t launch_limit_file_many(int kern, int dim, const Many& m, long long blocks, int threads, int sliced,
                                    int arg, cudaStream_t s);
+// A batch in persistent mode (persistent.cu): one cooperative launch per stage runs every kernel of the
+// stage for every member as phases separated by grid-wide barriers.  The arguments: the stage's contexts,
+// the virtual block offsets of every phase ([KN_COUNT][ninst + 1], kernel_blocks of each member for the
+// persistent block size) and their totals, and the step's structure.  grid returns the co-resident
+// grid the launch used.
+struct PersistArgs {
+  const Ctx* ctx;
+  const int* start;
+  int ninst, stage, eb, low_only, order, passes, slices;
+  int nblk[KN_COUNT];
+};
+cudaError_t launch_stage_persistent(int dim, bool mixed, const PersistArgs& a, int block, int* grid,
+                                    cudaStream_t s);
+
 // End of a fused step: advances the clock(s) by the step's dt (kernels_limit.cu).
 cudaError_t launch_clock_one(Clock* clk, double dt_factor, cudaStream_t s);
 cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s);

@@ -320,6 +320,7 @@ cudaError_t high_dispatch(int dim, bool mx, const Src& src, long long blocks, in
 
 }  // namespace
 
+#ifndef GDG_BODIES_ONLY  // (a file that includes this one for its kernel bodies defines it)
 // eb: elements per block (all instances of a batch share n_loc, hence the block shape).
 cudaError_t launch_high_file(int dim, const Ctx& c, long long blocks, int eb, cudaStream_t s) {
   return high_dispatch(dim, c.D.mixed != 0, One{c}, blocks, c.D.n_loc, eb, s);
@@ -329,5 +330,7 @@ cudaError_t launch_high_file_many(int dim, bool mixed, const Many& m, int n_loc,
                                   cudaStream_t s) {
   return high_dispatch(dim, mixed, m, blocks, n_loc, eb, s);
 }
+
+#endif  // GDG_BODIES_ONLY
 
 }  // namespace gdg

@@ -6,7 +6,7 @@ namespace gdg {
 
 namespace {
 
-constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches 128, 256 or 512
+constexpr int kLimThreads = kRowMaxThreads;  // launch bound; the schedule launches 128, 256 or 512
 
 // Sweep C: l_ij = min(l_ij^(i), l_ji^(j)) (Lemma ConsInvariants needs l_ij = l_ji);
 // U^(1)_i = U^L_i + (sum_j l_ij A_ij + sum_k l_i^k A_i^k) / m_i; then the second pass limits the
@@ -15,7 +15,7 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // sums, which every row runs, need far fewer, and the searches of the rare rows with a remainder would
 // otherwise set the kernel's occupancy.
 template <int DIM, class Src>
-__global__ void __maxnreg__(72) k_limit2(Src src, int sliced, int last) {
+__device__ __forceinline__ void limit2_body(const Src& src, int sliced, int last) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -88,12 +88,17 @@ __global__ void __maxnreg__(72) k_limit2(Src src, int sliced, int last) {
   }
 }
 
+template <int DIM, class Src>
+__global__ void __maxnreg__(72) k_limit2(Src src, int sliced, int last) {
+  limit2_body<DIM, Src>(src, sliced, last);
+}
+
 // The deferred line searches of one limiter pass (pass 0: from U^L with P = A / (kappa_i m_i), written to
 // l1; pass 1: from U^(1) with P = (1 - l1_ij) A / (kappa_i m_i), written to l2).  One thread per queued
 // entry, grid-stride over the queue: every lane runs a bracketed iteration.  The row context, l_rho and
 // psi(l_rho) are recomputed from the same stored values by the same code as in the queuing kernel.
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
+__device__ __forceinline__ void lsfix_body(const Src& src, int pass) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb, blocks_per_inst;
@@ -128,10 +133,15 @@ __global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
   }
 }
 
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
+  lsfix_body<DIM, Src>(src, pass);
+}
+
 // Sweep D: U^(2)_i = U^(1)_i + (sum_j l2_ij (1 - l1_ij) A_ij + sum_k l2_i^k (1 - l1_i^k) A_i^k) / m_i,
 // symmetrised as in sweep C, and U_out = alpha U_base + (1 - alpha) U^(2).
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kThreads) k_final(Src src, int sliced) {
+__device__ __forceinline__ void final_body(const Src& src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -170,6 +180,11 @@ __global__ void __launch_bounds__(kThreads) k_final(Src src, int sliced) {
   for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, S.U1[q * n + i] + acc[q] * inv_mi);
 }
 
+template <int DIM, class Src>
+__global__ void __launch_bounds__(kLimThreads) k_final(Src src, int sliced) {
+  final_body<DIM, Src>(src, sliced);
+}
+
 // End of a fused step for one instance's clock: t += dt of the step (the dt every kernel of the step
 // used), the step is counted, and the bound is reset for the next step.  Steps taken after t reached
 // t_end are no-ops and are not counted.
@@ -200,7 +215,7 @@ __global__ void k_clock_many(const Ctx* ctx, int ninst) {
 // U_out = alpha U_base + (1 - alpha) U_in at every node and component (alpha = 0: a copy): the linear
 // stage combinations of a Runge-Kutta step that involve no forward-Euler evaluation.
 template <int DIM, class Src>
-__global__ void __launch_bounds__(kThreads) k_axpy(Src src) {
+__device__ __forceinline__ void axpy_body(const Src& src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -218,10 +233,15 @@ __global__ void __launch_bounds__(kThreads) k_axpy(Src src) {
 }
 
 template <int DIM, class Src>
+__global__ void __launch_bounds__(kLimThreads) k_axpy(Src src) {
+  axpy_body<DIM, Src>(src);
+}
+
+template <int DIM, class Src>
 cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads, int sliced, int arg,
                          cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
-  if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
+  if (threads < 32 || threads > kLimThreads || threads % 32) return cudaErrorInvalidValue;
   const unsigned g = (unsigned)blocks;
   switch (kern) {
     case KN_LIMIT2: k_limit2<DIM, Src><<<g, threads, 0, s>>>(src, sliced, arg); break;
@@ -235,6 +255,7 @@ cudaError_t limit_launch(int kern, const Src& src, long long blocks, int threads
 
 }  // namespace
 
+#ifndef GDG_BODIES_ONLY  // (a file that includes this one for its kernel bodies defines it)
 cudaError_t launch_limit_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
                               cudaStream_t s) {
   const One src{c};
@@ -266,5 +287,7 @@ cudaError_t launch_clock_many(const Ctx* ctx, int ninst, cudaStream_t s) {
   k_clock_many<<<(ninst + 127) / 128, 128, 0, s>>>(ctx, ninst);
   return cudaGetLastError();
 }
+
+#endif  // GDG_BODIES_ONLY
 
 }  // namespace gdg

@@ -17,7 +17,7 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // also empties the stage's deferred line-search queues.  The mixed path (MX) keeps 1/rho and p in FP64
 // (the fluxes use them) and computes the rest in FP32.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_prim(Src src) {
+__device__ __forceinline__ void prim_body(const Src& src) {
   __shared__ Ctx sctx;
   int lb;
   const Ctx& c = src.get(&sctx, &lb);
@@ -73,6 +73,11 @@ __global__ void __launch_bounds__(kThreads) k_prim(Src src) {
   P[PR_ST * n + i] = st;
 }
 
+template <int DIM, bool MX, class Src>
+__global__ void __launch_bounds__(kThreads) k_prim(Src src) {
+  prim_body<DIM, MX, Src>(src);
+}
+
 // d_i^{d,k} = |c_i^{d,k}| lambda_max^+(U_i, U^{d,k}, n_i^k) of boundary entry b (Sec. 4.2,
 // eq. (eq:dij_low_order_modified); interior state on the left), from node i's primitives.
 template <int DIM, bool MX>
@@ -116,7 +121,7 @@ __device__ __forceinline__ void block_min_to(double val, unsigned long long* dst
 // eq. (eq:dij_low_order_supplement), then min over nodes of m_i / (2 |d_ii|), with d_ij^L evaluated here
 // (gdg_max_dt, before any stage).
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_maxdt(Src src, int sliced) {
+__device__ __forceinline__ void maxdt_body(const Src& src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -159,12 +164,17 @@ __global__ void __launch_bounds__(kThreads) k_maxdt(Src src, int sliced) {
   block_min_to(val, S.tau_bits);
 }
 
+template <int DIM, bool MX, class Src>
+__global__ void __launch_bounds__(kThreads) k_maxdt(Src src, int sliced) {
+  maxdt_body<DIM, MX, Src>(src, sliced);
+}
+
 // The same bound inside the fused SSP-RK3 step, after the edge sweep of the step's first stage: the row
 // sums of the stored d_ij^L plus the boundary viscosities, reduced into the instance's clock.  Capped at
 // 48 registers: the row sum, which every row runs, is latency-bound and wants many warps; the boundary
 // viscosities of the few boundary rows would otherwise take 117 and spill at the cap.
 template <int DIM, bool MX, class Src>
-__global__ void __maxnreg__(48) k_tau(Src src, int sliced) {
+__device__ __forceinline__ void tau_body(const Src& src, int sliced) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -194,6 +204,11 @@ __global__ void __maxnreg__(48) k_tau(Src src, int sliced) {
   block_min_to(val, &c.clk->tau_bits);
 }
 
+template <int DIM, bool MX, class Src>
+__global__ void __maxnreg__(48) k_tau(Src src, int sliced) {
+  tau_body<DIM, MX, Src>(src, sliced);
+}
+
 // Edge sweep, one thread per undirected stencil edge {i, j} (i < j): the quantities of a pair that are
 // symmetric in i and j are computed once and written to both entries (i, j) and (j, i):
 //  - d_ij^L = d_ji^L = |c_ij| lambda_max^+(U_i, U_j, n_ij) (Sec. 3.1, eq. (eq:dij_low_order); the bound
@@ -204,7 +219,7 @@ __global__ void __maxnreg__(48) k_tau(Src src, int sliced) {
 // The mixed path (MX) takes lambda from lambda_pair<true> and the entropy power of the bar state in FP32;
 // the fluxes, G and the bar state itself stay FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
+__device__ __forceinline__ void edge_body(const Src& src) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -282,6 +297,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
   S.barS[t] = stb;
 }
 
+template <int DIM, bool MX, class Src>
+__global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
+  edge_body<DIM, MX, Src>(src);
+}
+
 // Sweep A, one thread per row i, after the edge sweep:
 //  - the row sums of d_ij^L and f(U_j) c_ij from the edge sweep; boundary states and viscosities (Sec. 4.1;
 //    Sec. 4.2, eq. (eq:dij_low_order_modified));
@@ -294,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
 // The mixed path (MX) computes the indicator in FP32 (its sums from FP64 flux differences) and the
 // boundary wave-speed bounds with lambda_pair<true>; the low-order update stays FP64.
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads) k_low(Src src, int sliced, int write_out) {
+__device__ __forceinline__ void low_body(const Src& src, int sliced, int write_out) {
   constexpr int M = DIM + 2;
   __shared__ Ctx sctx;
   int lb;
@@ -467,6 +487,11 @@ __global__ void __launch_bounds__(kThreads) k_low(Src src, int sliced, int write
 }
 
 template <int DIM, bool MX, class Src>
+__global__ void __launch_bounds__(kThreads) k_low(Src src, int sliced, int write_out) {
+  low_body<DIM, MX, Src>(src, sliced, write_out);
+}
+
+template <int DIM, bool MX, class Src>
 cudaError_t low_launch(int kern, const Src& src, long long blocks, int threads, int sliced, int arg, cudaStream_t s) {
   if (blocks <= 0) return cudaSuccess;
   if (threads < 32 || threads > kThreads || threads % 32) return cudaErrorInvalidValue;
@@ -498,6 +523,7 @@ cudaError_t low_dispatch(int kern, int dim, bool mx, const Src& src, long long b
 
 }  // namespace
 
+#ifndef GDG_BODIES_ONLY  // (a file that includes this one for its kernel bodies defines it)
 // Launchers of this file's kernels, dispatched on the dimension and the precision (called by
 // launch_kernel*).
 cudaError_t launch_low_file(int kern, int dim, const Ctx& c, long long blocks, int threads, int sliced, int arg,
@@ -509,5 +535,7 @@ cudaError_t launch_low_file_many(int kern, int dim, bool mixed, const Many& m, l
                                  int sliced, int arg, cudaStream_t s) {
   return low_dispatch(kern, dim, mixed, m, blocks, threads, sliced, arg, s);
 }
+
+#endif  // GDG_BODIES_ONLY
 
 }  // namespace gdg

@@ -106,6 +106,7 @@ def load(build_if_missing: bool = False):
     L.gdg_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(vp)]
     L.gdg_batch_step.argtypes = [vp, vp]
+    L.gdg_batch_set_persistent.argtypes = [vp, i32]
     L.gdg_batch_profile.argtypes = [vp, i32]
     L.gdg_batch_profile_read.argtypes = [vp, vp, vp]
     L.gdg_batch_destroy.argtypes = [vp]
@@ -138,7 +139,7 @@ def load(build_if_missing: bool = False):
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_ssprk54_step",
               "gdg_clock_set",
-              "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_profile", "gdg_batch_profile_read",
+              "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_set_persistent", "gdg_batch_profile", "gdg_batch_profile_read",
               "gdg_footprint", "gdg_server_create", "gdg_server_submit", "gdg_server_wait", "gdg_server_stats",
               "gdg_autotune", "gdg_get_schedule", "gdg_set_schedule", "gdg_batch_autotune", "gdg_batch_get_schedule",
               "gdg_batch_set_schedule",
@@ -440,6 +441,10 @@ class Batch:
 
     def step(self, stream=None):
         _check(load().gdg_batch_step(self._b, _stream(stream)), "gdg_batch_step")
+
+    def set_persistent(self, on: bool):
+        """gdg_batch_set_persistent: one cooperative launch per stage instead of one launch per kernel."""
+        _check(load().gdg_batch_set_persistent(self._b, 1 if on else 0), "gdg_batch_set_persistent")
 
     def profile(self, enable: bool):
         _check(load().gdg_batch_profile(self._b, 1 if enable else 0), "gdg_batch_profile")

@@ -56,7 +56,7 @@ def _run_alone(torch, members, steps):
     return res
 
 
-def _run_batch(torch, members, steps, order=None, stream=None):
+def _run_batch(torch, members, steps, order=None, stream=None, persistent=False):
     from paper_2402_04514_gb300.gdg import Batch
 
     order = order or list(range(len(members)))
@@ -68,6 +68,8 @@ def _run_batch(torch, members, steps, order=None, stream=None):
         states.append(Ud)
         works.append((torch.empty_like(Ud), torch.empty_like(Ud)))
     B = Batch([m[0] for m in sel], states, works)
+    if persistent:
+        B.set_persistent(True)
     torch.cuda.synchronize()
     for _ in range(steps):
         B.step(stream=stream)  # on a stream of its own the step is captured once and replayed as a graph
@@ -107,6 +109,27 @@ def test_batch_equals_each_member_alone(torch_cuda, degree):
         assert S.status() == 0
 
 
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_persistent_batch_equals_each_member_alone(torch_cuda, degree):
+    """The persistent mode (one cooperative launch per stage, grid-wide barriers between the phases):
+    members of ragged sizes, two of them reaching their end time inside the run, give the same bits and
+    clocks as alone, in two batch orders and on a stream of its own."""
+    torch = torch_cuda
+    specs = [(13, degree, 1, np.inf), (3, degree, 2, np.inf), (21, degree, 3, 2.5), (8, degree, 4, np.inf),
+             (17, degree, 5, 1.5), (4, degree, 6, np.inf)]
+    members = _members(torch, specs)
+    steps = 5
+    alone = _run_alone(torch, members, steps)
+    for order, stream in ((None, None), ([4, 0, 5, 2, 1, 3], torch.cuda.Stream())):
+        got = _run_batch(torch, members, steps, order, stream, persistent=True)
+        for i, (U_a, clk_a) in enumerate(alone):
+            U_b, clk_b = got[i]
+            assert np.array_equal(U_a, U_b), i
+            assert clk_a == clk_b, (i, clk_a, clk_b)
+    for S, _, _ in members:
+        assert S.status() == 0
+
+
 @pytest.mark.parametrize("degree", [1, 2])
 def test_batch_of_3d_members(torch_cuda, degree):
     """Hexahedral members of ragged sizes (eight-octant data, slip walls), one reaching its end time inside
@@ -124,11 +147,12 @@ def test_batch_of_3d_members(torch_cuda, degree):
         members.append((S, U, t_end))
     steps = 4
     alone = _run_alone(torch, members, steps)
-    got = _run_batch(torch, members, steps, [2, 0, 1])
-    for i, (U_a, clk_a) in enumerate(alone):
-        U_b, clk_b = got[i]
-        assert np.array_equal(U_a, U_b), i
-        assert clk_a == clk_b, (i, clk_a, clk_b)
+    for persistent in (False, True):
+        got = _run_batch(torch, members, steps, [2, 0, 1], persistent=persistent)
+        for i, (U_a, clk_a) in enumerate(alone):
+            U_b, clk_b = got[i]
+            assert np.array_equal(U_a, U_b), (i, persistent)
+            assert clk_a == clk_b, (i, clk_a, clk_b)
     assert alone[2][1][2] < steps  # the third member stopped at its end time
     for S, _, _ in members:
         assert S.status() == 0
