@@ -185,6 +185,56 @@ def measure_developed(N=256, t_dev=0.05, steps=20):
             "ratio": late / early, "status_flags": S.status()}
 
 
+def run_vortex_sweep(args):
+    """The isentropic-vortex throughput sweep (Q1 on periodic [-5,5]^2 meshes of 64^2 .. 512^2 quads, gamma
+    = 1.4): per N, the GPU's DoF-stage updates/s over fused SSP-RK3 steps (after warm-up and autotuning)
+    and the FP64 oracle's on the same mesh and data, single-threaded and on all host cores, over a bounded
+    number of steps.  Prints one JSON line."""
+    import torch
+
+    from oracle import oracle as om
+    from paper_2402_04514_gb300.gdg import Solver
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rows = []
+    for N in (64, 128, 256, 512):
+        P, U0 = make_problem(dict(N=N, k=1, vortex=True))
+        S = Solver(P)
+        S.set_clock(0.0, float("inf"), 0.5)
+        U = torch.from_numpy(U0).cuda()
+        work = (torch.empty_like(U), torch.empty_like(U))
+        for _ in range(args.warmup):
+            S.step(U, work)
+        S.autotune(U, work, trials=1)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            S.step(U, work)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gpu = P.n * 3 * args.steps / (e0.elapsed_time(e1) / 1e3)
+        row = {"N": N, "dofs": int(P.n), "gpu": gpu, "gpu_ms_per_step": e0.elapsed_time(e1) / args.steps,
+               "status_flags": S.status()}
+        S.close()
+        for openmp in (False, True):
+            O = om.Oracle(P, openmp=openmp)
+            steps = max(1, int(2e6 / P.n)) if not openmp else max(2, int(5e6 / P.n))
+            V = U0.copy()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                V, _ = O.ssprk3_step(V, O.max_dt(V, 0.5))
+            dt = time.perf_counter() - t0
+            row["oracle_all_cores" if openmp else "oracle_1_thread"] = P.n * 3 * steps / dt
+            row["oracle_steps_all_cores" if openmp else "oracle_steps_1_thread"] = steps
+        row["oracle_threads"] = om.threads(True)
+        rows.append(row)
+    print(json.dumps({"metric": METRIC, "unit": METRIC, "workload": "q1_vortex_periodic_sweep", "gamma": 1.4,
+                      "cfl": 0.5, "steps": args.steps, "warmup": args.warmup, "rows": rows}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -442,7 +492,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="q2_1024_four_quadrant",
-                    choices=sorted(WORKLOADS) + ["batched_q1_riemann", "served_stream"])
+                    choices=sorted(WORKLOADS) + ["batched_q1_riemann", "served_stream", "q1_vortex_periodic_sweep"])
     ap.add_argument("--requests", type=int, default=32, help="served workload: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="served workload: arrivals per second")
     ap.add_argument("--n-max", type=int, default=48, help="served workload: largest N")
@@ -479,6 +529,8 @@ def main():
         return run_batched(args)
     if args.workload == "served_stream":
         return run_served(args)
+    if args.workload == "q1_vortex_periodic_sweep":
+        return run_vortex_sweep(args)
 
     import numpy as np
     import torch

@@ -278,15 +278,16 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
   }
 }
 
-// The element sweep as two kernels, because they want different register budgets: the FP64 path, bound by
-// the FP64 pipe and memory latency, runs fastest at 72 registers (three 288-thread blocks per SM, a few
-// spills); the mixed path, whose FP32 work needs more live values, at 96.
+// The element sweep of each path as its own kernel with its own register budget.  Both run fastest at 72
+// registers (three 288-thread blocks per SM, a few spills): with the per-entry streams contiguous, the
+// resident warps matter more than the spills (the mixed path took 3.97 ms per launch at 96 registers,
+// 3.37 ms at 72, at 1024^2 Q2).
 template <int DIM, class Src>
 __global__ void __maxnreg__(72) k_high(Src src, int eb) {
   high_sweep<DIM, false, Src>(src, eb);
 }
 template <int DIM, class Src>
-__global__ void __maxnreg__(96) k_high_mixed(Src src, int eb) {
+__global__ void __maxnreg__(72) k_high_mixed(Src src, int eb) {
   high_sweep<DIM, true, Src>(src, eb);
 }
 
