@@ -275,9 +275,10 @@ def test_sod_exact_solution(oracle_mod):
 
 
 def _vortex_error(oracle_mod, ne, k, order):
+    """L1 error of the vortex at t = 2 (the oracle's multi-core build, bit-identical to the pinned one)."""
     P, U, bdata = dirichlet_vortex_problem(ne, k)
     g = 5.0 / 3.0
-    O = oracle_mod.Oracle(P, gamma=g, params=dict(order=order))
+    O = oracle_mod.Oracle(P, gamma=g, params=dict(order=order), openmp=True)
     t, tF = 0.0, 2.0
     while t < tF - 1e-12:
         tau = min(O.max_dt(U, 0.5, bdata=bdata(t)), tF - t)
