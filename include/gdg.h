@@ -78,7 +78,13 @@ typedef struct {
   double ls_tol;
   int32_t ls_maxit;
   int32_t precision;      /* GDG_PRECISION_FP64 (default) or GDG_PRECISION_MIXED */
+  int32_t relax_measure;  /* the mesh size h_i of the relaxation r_h^+- = 1 +- c_r h_i^{p_r} (Sec. 5.4):
+                             GDG_RELAX_NODE (default): h_i = (m_i / |Omega|)^{1/d} as eq. (ViscMinConst2)'s
+                             passage prints it; GDG_RELAX_ELEMENT: h_i = (|K_i| / |Omega|)^{1/d} with |K_i|
+                             the measure (the sum of the lumped masses) of i's element, with which the
+                             limited scheme reproduces the paper's Q2 and Q3 vortex table */
 } gdg_params;
+enum { GDG_RELAX_NODE = 0, GDG_RELAX_ELEMENT = 1 };
 
 /* One mesh instance (all host pointers, copied by gdg_setup).
  * Requirements (gdg_setup returns GDG_ESETUP when one fails):

@@ -593,7 +593,15 @@ int orc_stage(const orc_problem* P, const double* Uin, const double* Ubase, doub
           sl = fmin(sl, fmin(s_tilde(Uk, d, g), s_tilde(Ubk, d, g)));
         }
       }
-      double hh = pow(pow(P->mi[i] / P->omega, 1.0 / d), P->p_r);
+      /* r_h^{+-} = 1 +- c_r h_i^{p_r}, h_i = (m_i / |Omega|)^{1/d} (eq. (ViscMinConst2)'s passage); with
+       * relax_measure = 1 the measure of i's element, the sum of its nodes' lumped masses, replaces m_i
+       * (the reading under which the limited scheme reproduces the paper's Q2 and Q3 vortex errors) */
+      double meas = P->mi[i];
+      if (P->relax_measure == 1) {
+        meas = 0.0;
+        for (long a = (i / nl) * nl; a < (i / nl + 1) * nl; ++a) meas += P->mi[a];
+      }
+      double hh = pow(pow(meas / P->omega, 1.0 / d), P->p_r);
       double rm = 1.0 - P->c_r * hh, rp = 1.0 + P->c_r * hh;
       if (P->bounds_mode == 1) {
         rmin[i] = 0.0; rmax[i] = INFINITY; smin[i] = 0.0;

@@ -42,6 +42,7 @@ typedef struct {
   double c_k, p_k, c_ev, c_r, p_r;
   double ls_tol;
   int ls_maxit;
+  int relax_measure;  /* 0: h_i = (m_i / |Omega|)^{1/d} in r_h (Sec. 5.4 as printed); 1: h_i of i's element */
 } orc_problem;
 
 /* Optional outputs of a stage; every pointer may be NULL. */

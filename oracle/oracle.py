@@ -48,7 +48,7 @@ class _Problem(C.Structure):
                 ("order", C.c_int), ("limiter_passes", C.c_int), ("bounds_mode", C.c_int),
                 ("c_k", C.c_double), ("p_k", C.c_double), ("c_ev", C.c_double),
                 ("c_r", C.c_double), ("p_r", C.c_double),
-                ("ls_tol", C.c_double), ("ls_maxit", C.c_int)]
+                ("ls_tol", C.c_double), ("ls_maxit", C.c_int), ("relax_measure", C.c_int)]
 
 
 _TRACE_FIELDS = ["dL", "dB", "dii", "UB", "ubar", "ubarB", "UL", "N", "dH", "dBH", "UH", "A", "AB",
@@ -94,7 +94,8 @@ def default_params(degree: int) -> dict:
     (Sec. 6.1)."""
     return dict(order=LIMITED, limiter_passes=2, bounds_mode=0, c_k=1.0,
                 p_k=0.5 if degree % 2 == 0 else 0.0,
-                c_ev={1: 1.0, 2: 0.5}.get(degree, 0.25), c_r=4.0, p_r=1.5, ls_tol=1e-14, ls_maxit=50)
+                c_ev={1: 1.0, 2: 0.5}.get(degree, 0.25), c_r=4.0, p_r=1.5, ls_tol=1e-14, ls_maxit=50,
+                relax_measure=0)
 
 
 def _p(a):
@@ -133,7 +134,7 @@ class Oracle:
                            _p(k["MK"]), _p(k["b_node"]), _p(k["b_c"]), _p(k["b_type"]),
                            self.gamma, P.omega_measure, pr["order"], pr["limiter_passes"],
                            pr["bounds_mode"], pr["c_k"], pr["p_k"], pr["c_ev"], pr["c_r"], pr["p_r"],
-                           pr["ls_tol"], pr["ls_maxit"])
+                           pr["ls_tol"], pr["ls_maxit"], pr["relax_measure"])
 
     def set(self, **kw):
         for key, val in kw.items():

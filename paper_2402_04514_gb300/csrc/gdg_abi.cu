@@ -44,6 +44,7 @@ bool check_params(const gdg_params& p) {
     return false;
   if (!(p.ls_tol > 0) || p.ls_maxit < 0) return false;
   if (p.precision != GDG_PRECISION_FP64 && p.precision != GDG_PRECISION_MIXED) return false;
+  if (p.relax_measure != GDG_RELAX_NODE && p.relax_measure != GDG_RELAX_ELEMENT) return false;
   return true;
 }
 
@@ -172,7 +173,13 @@ int param_arrays(const gdg_handle* h, const gdg_params& p, ParamArrays& A) {
   A.muB.resize(n);
   for (int64_t i = 0; i < n; ++i) {
     double hi = std::pow(h->mi[i] / h->omega, dinv);
-    double rel = p.c_r * std::pow(hi, p.p_r);
+    double hr = hi;  // the relaxation's mesh size: the node's (as printed) or its element's
+    if (p.relax_measure == GDG_RELAX_ELEMENT) {
+      double mel = 0.0;
+      for (int64_t q = i / h->n_loc * h->n_loc; q < (i / h->n_loc + 1) * h->n_loc; ++q) mel += h->mi[q];
+      hr = std::pow(mel / h->omega, dinv);
+    }
+    double rel = p.c_r * std::pow(hr, p.p_r);
     A.rm[i] = 1.0 - rel;
     A.rp[i] = 1.0 + rel;
     A.muB[i] = p.c_k * std::pow(hi, p.p_k);
@@ -225,6 +232,7 @@ void gdg_default_params(int32_t degree, gdg_params* out) {
   out->ls_tol = 1e-14;
   out->ls_maxit = 50;
   out->precision = GDG_PRECISION_FP64;
+  out->relax_measure = GDG_RELAX_NODE;
 }
 
 const char* gdg_error_string(int code) {

@@ -17,6 +17,7 @@ KERNELS = ("prim", "maxdt", "low", "high", "limit2", "final", "edge", "lsfix", "
 BC_SLIP, BC_DIRICHLET, BC_INOUTFLOW = 0, 1, 2
 FLAG_INADMISSIBLE, FLAG_CFL = 1, 2
 PRECISION_FP64, PRECISION_MIXED = 0, 1
+RELAX_NODE, RELAX_ELEMENT = 0, 1
 
 _CODES = {0: "GDG_OK", 1: "GDG_EINVAL", 2: "GDG_ENOMEM", 3: "GDG_ECUDA", 4: "GDG_ESETUP", 5: "GDG_EADMISSIBLE",
           6: "GDG_ECFL", 7: "GDG_ETIMEOUT", 8: "GDG_ENOTSUP"}
@@ -31,7 +32,8 @@ class GdgError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("order", C.c_int32), ("limiter_passes", C.c_int32), ("bounds_mode", C.c_int32),
                 ("c_k", C.c_double), ("p_k", C.c_double), ("c_ev", C.c_double), ("c_r", C.c_double),
-                ("p_r", C.c_double), ("ls_tol", C.c_double), ("ls_maxit", C.c_int32), ("precision", C.c_int32)]
+                ("p_r", C.c_double), ("ls_tol", C.c_double), ("ls_maxit", C.c_int32), ("precision", C.c_int32),
+                ("relax_measure", C.c_int32)]
 
 
 class _Problem(C.Structure):

@@ -114,6 +114,22 @@ def test_intermediates_parity(torch_cuda, name):
     assert rel_err(S.export("U1"), tr["U1"]) <= STAGE_TOL
 
 
+@pytest.mark.parametrize("name", ["fq_q2_slip", "fq_q3_slip", "oct_q2_3d"])
+def test_stage_parity_element_measure(torch_cuda, name):
+    """A limited stage with the relaxation's mesh size from the element (relax_measure = 1): the bounds
+    equal the oracle's within 1e-13 and the stage within 1e-12."""
+    torch = torch_cuda
+    P, U = _problem(name)
+    S, O = _pair(P, params=dict(relax_measure=1))
+    tau = O.max_dt(U, 0.5)
+    out = S.stage(_dev(torch, U), tau)
+    ref, flags, tr = O.stage(U, tau, trace=True)
+    for k in ("rho_min", "rho_max", "s_min"):
+        assert rel_err(S.export(k), tr[k]) <= 1e-13
+    assert rel_err(out.cpu().numpy(), ref) <= STAGE_TOL
+    assert S.status() == flags == 0
+
+
 def test_dirichlet_q3_and_bounds_off(torch_cuda):
     torch = torch_cuda
     P, U, bdata = dirichlet_vortex_problem(6, 3)

@@ -87,11 +87,12 @@ def _adjacency(P):
     return A, pos
 
 
-def _hand_bounds(P, U, tr, hops=2):
+def _hand_bounds(P, U, tr, hops=2, element=False):
     """rho_min, rho_max, s_min of eq. (eq:local_bounds) by brute force: states over the two-hop set
     (I(i) and i, then I(j) and j), bar states U_jk over j in I(i) and i, k in I(j), the boundary bar states
     of node i itself, relaxed by r_h^+- = 1 +- c_r h_i^{p_r}, h_i = (m_i / |Omega|)^{1/d}.  hops=1 gives
-    the one-hop variant, used only to show that a case tells the two apart."""
+    the one-hop variant, used only to show that a case tells the two apart.  element=True takes h_i from the
+    measure of i's element (the sum of its nodes' lumped masses) instead of m_i."""
     n, d = P.n, P.dim
     A, pos = _adjacency(P)
     A1 = A | np.eye(n, dtype=bool)
@@ -124,7 +125,11 @@ def _hand_bounds(P, U, tr, hops=2):
             Ug[1:1 + d] = Ui[1:1 + d] - 2 * (Ui[1:1 + d] * nrm).sum() * nrm
             Ub = _bar(Ui, Ug, cb, tr["dB"][b])
             lo, hi, sl = min(lo, Ub[0]), max(hi, Ub[0]), min(sl, _s_tilde(Ub))
-        h = (LD(P.mi[i]) / LD(P.omega_measure)) ** (LD(1) / d)
+        meas = LD(P.mi[i])
+        if element:
+            K = i // P.n_loc
+            meas = np.asarray(P.mi[K * P.n_loc:(K + 1) * P.n_loc], LD).sum()
+        h = (meas / LD(P.omega_measure)) ** (LD(1) / d)
         r = LD(C_R) * h ** LD(P_R)
         out["rho_min"][i] = (1 - r) * lo
         out["rho_max"][i] = (1 + r) * hi
@@ -196,8 +201,8 @@ def _cases():
 CASES = _cases()
 
 
-def _limited_stage(oracle_mod, P, U, k):
-    O = oracle_mod.Oracle(P, gamma=G)
+def _limited_stage(oracle_mod, P, U, k, **extra):
+    O = oracle_mod.Oracle(P, gamma=G, params=extra)
     assert (O.params["c_r"], O.params["p_r"], O.params["c_k"], O.params["p_k"], O.params["c_ev"]) == (
         C_R, P_R, C_K, p_k(k), c_ev(k))
     _, flags, tr = O.stage(U, O.max_dt(U, 0.5), trace=True)
@@ -237,3 +242,27 @@ def test_high_order_viscosity_by_hand(oracle_mod, case):
         assert (np.asarray(tr["dBH"]) != np.asarray(tr["dB"])).any(), name
     if name.endswith("graded"):
         assert unequal > 0, name
+
+
+ELEMENT_CASES = ["2d_q2_4x4", "1d_q2_graded"]
+
+
+def _element_case(name):
+    if name == "2d_q2_4x4":
+        P = assembly.assemble_2d(4, 4, 2)
+        return P, workloads.four_quadrant(P.x[0], P.x[1], gamma=G, seed=3, split=(0.4, 0.6)), 2
+    return next((P, U, k) for n, P, U, k in CASES if n == name)
+
+
+@pytest.mark.parametrize("name", ELEMENT_CASES)
+def test_relaxed_local_bounds_by_hand_element_measure(oracle_mod, name):
+    """The same brute force with the relaxation's mesh size taken from the element (relax_measure = 1):
+    h_i = (|K_i| / |Omega|)^{1/d}, |K_i| the sum of the lumped masses of i's element; within 1e-13, and
+    different from the node-measure bounds (every node of a Q2 element has m_i < |K_i|)."""
+    P, U, k = _element_case(name)
+    tr = _limited_stage(oracle_mod, P, U, k, relax_measure=1)
+    want = _hand_bounds(P, U, tr, element=True)
+    for key in ("rho_min", "rho_max", "s_min"):
+        assert _rel(tr[key], want[key]) <= 1e-13, (name, key, _rel(tr[key], want[key]))
+    node = _hand_bounds(P, U, tr)
+    assert (np.abs(node["rho_max"] - want["rho_max"]) > 1e-6 * np.abs(want["rho_max"])).all()

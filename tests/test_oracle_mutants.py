@@ -59,8 +59,10 @@ MUTANTS = {
                                         "double rm = 1.0 - P->c_r * hh, rp = 1.0 + 2.0 * P->c_r * hh;"),
     "bounds_one_hop_only": ("for (long ek = P->row_ptr[j]; ek < P->row_ptr[j + 1]; ++ek) {",
                             "for (long ek = P->row_ptr[j]; ek < P->row_ptr[j + 1] && j == i; ++ek) {"),
-    "bounds_mesh_size_without_the_dimension_root": ("double hh = pow(pow(P->mi[i] / P->omega, 1.0 / d), P->p_r);",
-                                                    "double hh = pow(P->mi[i] / P->omega, P->p_r);"),
+    "bounds_mesh_size_without_the_dimension_root": ("double hh = pow(pow(meas / P->omega, 1.0 / d), P->p_r);",
+                                                    "double hh = pow(meas / P->omega, P->p_r);"),
+    "relaxation_element_measure_from_one_node": ("for (long a = (i / nl) * nl; a < (i / nl + 1) * nl; ++a) meas += P->mi[a];",
+                                                 "for (long a = (i / nl) * nl; a < (i / nl + 1) * nl; ++a) meas = P->mi[a];"),
     # the minimal and boundary high-order viscosities (Sec. 5.1, eq. (ViscMin); the boundary reading)
     "minimal_viscosity_power_dropped": ("dmin = P->c_k * pow(hij, P->p_k) * dL[e];", "dmin = P->c_k * dL[e];"),
     "minimal_viscosity_mesh_size_of_the_row_node": (
@@ -94,6 +96,7 @@ FAST_PINS = [
     lambda O: pins.test_entropy_indicator_vanishes_in_smooth_flow(O),
     lambda O: [hand.test_relaxed_local_bounds_by_hand(O, c) for c in range(len(hand.CASES))],
     lambda O: [hand.test_high_order_viscosity_by_hand(O, c) for c in range(len(hand.CASES))],
+    lambda O: [hand.test_relaxed_local_bounds_by_hand_element_measure(O, c) for c in hand.ELEMENT_CASES],
 ]
 
 
