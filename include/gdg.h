@@ -172,6 +172,20 @@ int gdg_stage(gdg_handle* h, const double* U_in, const double* U_base, double al
  * Flags as gdg_stage. */
 int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream);
 
+/* gdg_ssprk3_step for a state kept in host memory: reads the step's input from U_host_in (host [m][n]),
+ * runs the step on the device in U, T1, T2 (device [m][n], distinct; all three overwritten, U left holding
+ * the new state) and writes the new state to U_host_out (host [m][n]; may equal U_host_in).
+ * When U_host_in is page-locked memory mapped into the device's address space (cudaHostAlloc,
+ * cudaMallocHost, or cudaHostRegister with mapping), the first stage's primitive sweep reads it over the
+ * host link and stores it in U itself, so that the transfer overlaps that sweep's arithmetic; any other
+ * input is copied to U by cudaMemcpyAsync before the step.  The result goes back by cudaMemcpyAsync.
+ * Asynchronous on stream for page-locked buffers: U_host_out is complete, and U_host_in may change, only
+ * once the stream has been synchronized (pageable buffers make the copies wait for the host as
+ * cudaMemcpyAsync does).  Clock, bdata (device), flags and errors as gdg_ssprk3_step; with a finished clock
+ * the state is copied through unchanged. */
+int gdg_ssprk3_step_host(gdg_handle* h, const double* U_host_in, double* U_host_out, double* U, double* T1,
+                         double* T2, const double* bdata, void* stream);
+
 /* One SSPRK(5,4) step: the five-stage fourth-order SSP Runge-Kutta method the paper's experiments use
  * (Sec. 6.2; the optimal coefficients of Spiteri and Ruuth, SSP coefficient C = 1.508), in Shu-Osher form
  * from limited forward-Euler stages, with dt = min(cfl * C * min_i (-m_i / (2 d_ii(U))), t_end - t) chosen

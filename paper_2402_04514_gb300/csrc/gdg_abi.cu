@@ -693,7 +693,10 @@ int gdg_max_dt(gdg_handle* h, const double* U, const double* bdata, double cfl, 
 // The kernels of one stage (Sec. 6.1): primitives, edge sweep, [the fused step's tau bound], sweep A,
 // then, as the order and the number of limiter passes ask, the element sweep, the deferred line searches
 // of pass 1, sweep C, those of pass 2 and sweep D.
-static int run_stage(gdg_handle* h, const gdg::Ctx& c, bool with_tau, cudaStream_t s) {
+// prim_ctx, when given, is the context of the primitive sweep alone (a stage whose input it reads from
+// host memory and stores where c.U points).
+static int run_stage(gdg_handle* h, const gdg::Ctx& c, bool with_tau, cudaStream_t s,
+                     const gdg::Ctx* prim_ctx = nullptr) {
   const int dim = h->dim;
   const gdg::Dev& D = h->D;
   cudaError_t e;
@@ -701,7 +704,12 @@ static int run_stage(gdg_handle* h, const gdg::Ctx& c, bool with_tau, cudaStream
     return timed(h, id, s, [&] { return gdg::launch_one(kern, dim, c, arg, h->sched, s); });
   };
   const bool low_only = D.order == GDG_ORDER_LOW || (D.order == GDG_ORDER_LIMITED && D.passes == 0);
-  if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) return cuda_fail(e);
+  if (prim_ctx) {
+    e = timed(h, GDG_K_PRIM, s, [&] { return gdg::launch_one(gdg::KN_PRIM, dim, *prim_ctx, 0, h->sched, s); });
+    if (e != cudaSuccess) return cuda_fail(e);
+  } else if ((e = go(GDG_K_PRIM, gdg::KN_PRIM, 0)) != cudaSuccess) {
+    return cuda_fail(e);
+  }
   if ((e = go(GDG_K_EDGE, gdg::KN_EDGE, 0)) != cudaSuccess) return cuda_fail(e);
   if (with_tau && (e = go(GDG_K_TAU, gdg::KN_TAU, 0)) != cudaSuccess) return cuda_fail(e);
   if ((e = go(GDG_K_LOW, gdg::KN_LOW, low_only ? 1 : 0)) != cudaSuccess) return cuda_fail(e);
@@ -755,21 +763,61 @@ int gdg_clock_get(gdg_handle* h, double* t, double* tau, int64_t* steps, void* s
   return GDG_OK;
 }
 
-int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream) {
-  if (!h || ((!U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
-  if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
-  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
+// The three stages of the fused SSP-RK3 step on U (device); with U_mapped, the first stage's primitive
+// sweep reads the step's input from that kernel-addressable host memory and stores it in U first.
+static int ssprk3_stages(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata,
+                         const double* U_mapped, cudaStream_t s) {
   // Shu-Osher form of SSP-RK3 (Sec. 6.2): U1 = FE(U); U2 = 3/4 U + 1/4 FE(U1); U <- 1/3 U + 2/3 FE(U2),
   // the last in place (each node reads its base value before writing it)
   const gdg::Ctx c1 = make_ctx(h, U, nullptr, T1, bdata, 0.0, 0.0, h->clk);
   const gdg::Ctx c2 = make_ctx(h, T1, U, T2, bdata, 0.75, 0.0, h->clk);
   const gdg::Ctx c3 = make_ctx(h, T2, U, U, bdata, 1.0 / 3.0, 0.0, h->clk);
-  if (int rc = run_stage(h, c1, true, s); rc != GDG_OK) return rc;
+  gdg::Ctx p1 = c1;
+  if (U_mapped) {
+    p1.U = U_mapped;
+    p1.Ucopy = U;
+  }
+  if (int rc = run_stage(h, c1, true, s, U_mapped ? &p1 : nullptr); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c2, false, s); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c3, false, s); rc != GDG_OK) return rc;
   cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, 1.0, s); });
   return e == cudaSuccess ? GDG_OK : cuda_fail(e);
+}
+
+int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata, void* stream) {
+  if (!h || ((!U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
+  if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  return ssprk3_stages(h, U, T1, T2, bdata, nullptr, (cudaStream_t)stream);
+}
+
+// The address kernels on the current device use for host memory p, when p lies in page-locked memory
+// mapped into the device's address space (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping);
+// null for any other memory.
+static const double* mapped_host(const double* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // not a pointer the runtime knows: plain host memory
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<const double*>(a.devicePointer) : nullptr;
+}
+
+int gdg_ssprk3_step_host(gdg_handle* h, const double* U_host_in, double* U_host_out, double* U, double* T1,
+                         double* T2, const double* bdata, void* stream) {
+  if (!h || ((!U_host_in || !U_host_out || !U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
+  if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
+  if (h->has_dirichlet && !bdata) return GDG_EINVAL;
+  if (h->n == 0) return ssprk3_stages(h, U, T1, T2, bdata, nullptr, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)(h->dim + 2) * h->n;
+  const double* in_dev = mapped_host(U_host_in);
+  cudaError_t e;
+  if (!in_dev && (e = cudaMemcpyAsync(U, U_host_in, bytes, cudaMemcpyDefault, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if (int rc = ssprk3_stages(h, U, T1, T2, bdata, in_dev, s); rc != GDG_OK) return rc;
+  if ((e = cudaMemcpyAsync(U_host_out, U, bytes, cudaMemcpyDefault, s)) != cudaSuccess) return cuda_fail(e);
+  return GDG_OK;
 }
 
 // SSPRK(5,4): the optimal five-stage fourth-order SSP method (Spiteri-Ruuth coefficients; the method the

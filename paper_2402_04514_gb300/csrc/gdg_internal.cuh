@@ -198,6 +198,7 @@ struct Ctx {
   Dev D;
   Scratch S;
   const double* U;      // stage input U_in [m][n]
+  double* Ucopy;        // where the primitive sweep stores the U_in it read (a stage fed from host memory), or null
   const double* Ubase;  // SSP-RK base (read only where alpha != 0)
   double* Uout;         // stage output; may equal Ubase (each node reads its base before writing itself)
   const double* bdata;  // Dirichlet data [m][nb] or null

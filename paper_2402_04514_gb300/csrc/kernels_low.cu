@@ -15,23 +15,31 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // f(s) = exp(s / (gamma + 1)) of the entropy-viscosity indicator and s~ = rho^{-gamma} eps (Sec. 5.4).
 // Flags a state outside the admissible set of eq. (AddSet).  Being the first kernel of every stage, it
 // also empties the stage's deferred line-search queues.  The mixed path (MX) keeps 1/rho and p in FP64
-// (the fluxes use them) and computes the rest in FP32.
+// (the fluxes use them) and computes the rest in FP32.  With c.Ucopy set (the first stage of a step whose
+// state comes from host memory, read here over the host link) it also stores the state it read there, for
+// the later sweeps of the stage, even when the instance's clock has finished.
 template <int DIM, bool MX, class Src>
 __device__ __forceinline__ void prim_body(const Src& src) {
   __shared__ Ctx sctx;
   int lb;
   const Ctx& c = src.get(&sctx, &lb);
-  if (finished(c)) return;
+  const bool done = finished(c);
+  if (done && !c.Ucopy) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
   const int i = lb * blockDim.x + threadIdx.x;
-  if (i == 0) {
+  if (i == 0 && !done) {
     S.lsq_n[0] = 0u;
     S.lsq_n[1] = 0u;
   }
   if (i >= D.n) return;
   double Ui[DIM + 2];
   load_state<DIM>(c.U, D.n, i, Ui);
+  if (c.Ucopy) {
+#pragma unroll
+    for (int q = 0; q < DIM + 2; ++q) c.Ucopy[(size_t)q * D.n + i] = Ui[q];
+    if (done) return;
+  }
   double irho = rcp64(Ui[0]);
   double m2 = 0.0;
 #pragma unroll

@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
     L.gdg_stage.argtypes = [vp, vp, vp, d, d, vp, vp, vp]
     L.gdg_ssprk3_step.argtypes = [vp, vp, vp, vp, vp, vp]
     L.gdg_ssprk54_step.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.gdg_ssprk3_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.gdg_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(vp)]
     L.gdg_batch_step.argtypes = [vp, vp]
@@ -140,6 +141,7 @@ def load(build_if_missing: bool = False):
     L.gdg_error_string.argtypes = [C.c_int]
     L.gdg_error_string.restype = C.c_char_p
     for f in ("gdg_setup", "gdg_set_params", "gdg_max_dt", "gdg_stage", "gdg_ssprk3_step", "gdg_ssprk54_step",
+              "gdg_ssprk3_step_host",
               "gdg_clock_set",
               "gdg_clock_get", "gdg_batch_create", "gdg_batch_step", "gdg_batch_set_persistent", "gdg_batch_profile", "gdg_batch_profile_read",
               "gdg_footprint", "gdg_server_create", "gdg_server_submit", "gdg_server_wait", "gdg_server_stats",
@@ -374,6 +376,32 @@ class Solver:
         else:
             raise ValueError("work holds two (SSPRK3) or three (SSPRK(5,4)) scratch states")
         return U
+
+    def _host_state(self, X, writable: bool):
+        """Address of a host state [m][n] of float64: a CPU torch tensor (page-locked or not) or a numpy array."""
+        if isinstance(X, np.ndarray):
+            assert X.dtype == np.float64 and X.flags.c_contiguous and X.shape == (self.m, self.n), X.shape
+            assert X.flags.writeable or not writable
+            return C.c_void_p(X.ctypes.data)
+        import torch
+
+        assert isinstance(X, torch.Tensor) and not X.is_cuda and X.dtype == torch.float64
+        assert X.is_contiguous() and tuple(X.shape) == (self.m, self.n), X.shape
+        return C.c_void_p(X.data_ptr())
+
+    def step_host(self, U_host_in, U_host_out, U, work, bdata=None, stream=None):
+        """gdg_ssprk3_step_host: one fused SSP-RK3 step of a state in host memory (U_host_in -> U_host_out,
+        which may be the same buffer), on the device in U and work = (T1, T2).  Asynchronous for
+        page-locked buffers: synchronize the stream before reading U_host_out."""
+        self._check_state(U)
+        for T in work:
+            self._check_state(T)
+        T1, T2 = work
+        bd = self._bdata(bdata)
+        _check(load().gdg_ssprk3_step_host(self._h, self._host_state(U_host_in, False),
+                                           self._host_state(U_host_out, True), _ptr(U), _ptr(T1), _ptr(T2),
+                                           _ptr(bd), _stream(stream)), "gdg_ssprk3_step_host")
+        return U_host_out
 
     def autotune(self, U, work, trials: int = 2, bdata=None, stream=None) -> dict:
         """gdg_autotune: picks the launch schedule by timing fused steps from U (restored afterwards)."""
