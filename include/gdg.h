@@ -177,8 +177,10 @@ int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const doub
  * the new state) and writes the new state to U_host_out (host [m][n]; may equal U_host_in).
  * When U_host_in is page-locked memory mapped into the device's address space (cudaHostAlloc,
  * cudaMallocHost, or cudaHostRegister with mapping), the first stage's primitive sweep reads it over the
- * host link and stores it in U itself, so that the transfer overlaps that sweep's arithmetic; any other
- * input is copied to U by cudaMemcpyAsync before the step.  The result goes back by cudaMemcpyAsync.
+ * host link and stores it in U itself, so that the transfer overlaps that sweep's arithmetic; if
+ * U_host_out is such memory too, the last stage's sweeps write each node's new state there as they write
+ * it to U, overlapping the transfer back with the rest of the stage.  Other buffers are copied by
+ * cudaMemcpyAsync before and after the step.
  * Asynchronous on stream for page-locked buffers: U_host_out is complete, and U_host_in may change, only
  * once the stream has been synchronized (pageable buffers make the copies wait for the host as
  * cudaMemcpyAsync does).  Clock, bdata (device), flags and errors as gdg_ssprk3_step; with a finished clock

@@ -763,21 +763,25 @@ int gdg_clock_get(gdg_handle* h, double* t, double* tau, int64_t* steps, void* s
   return GDG_OK;
 }
 
-// The three stages of the fused SSP-RK3 step on U (device); with U_mapped, the first stage's primitive
-// sweep reads the step's input from that kernel-addressable host memory and stores it in U first.
+// The three stages of the fused SSP-RK3 step on U (device).  With in_mapped, the first stage's primitive
+// sweep reads the step's input from that kernel-addressable host memory and stores it in U first; with
+// out_mapped (only together with in_mapped), the last stage's writers also write the new state there, and
+// so does the primitive sweep when the clock has finished and the step changes nothing.
 static int ssprk3_stages(gdg_handle* h, double* U, double* T1, double* T2, const double* bdata,
-                         const double* U_mapped, cudaStream_t s) {
+                         const double* in_mapped, double* out_mapped, cudaStream_t s) {
   // Shu-Osher form of SSP-RK3 (Sec. 6.2): U1 = FE(U); U2 = 3/4 U + 1/4 FE(U1); U <- 1/3 U + 2/3 FE(U2),
   // the last in place (each node reads its base value before writing it)
   const gdg::Ctx c1 = make_ctx(h, U, nullptr, T1, bdata, 0.0, 0.0, h->clk);
   const gdg::Ctx c2 = make_ctx(h, T1, U, T2, bdata, 0.75, 0.0, h->clk);
-  const gdg::Ctx c3 = make_ctx(h, T2, U, U, bdata, 1.0 / 3.0, 0.0, h->clk);
+  gdg::Ctx c3 = make_ctx(h, T2, U, U, bdata, 1.0 / 3.0, 0.0, h->clk);
   gdg::Ctx p1 = c1;
-  if (U_mapped) {
-    p1.U = U_mapped;
+  if (in_mapped) {
+    p1.U = in_mapped;
     p1.Ucopy = U;
+    p1.Uhost = out_mapped;
+    c3.Uhost = out_mapped;
   }
-  if (int rc = run_stage(h, c1, true, s, U_mapped ? &p1 : nullptr); rc != GDG_OK) return rc;
+  if (int rc = run_stage(h, c1, true, s, in_mapped ? &p1 : nullptr); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c2, false, s); rc != GDG_OK) return rc;
   if (int rc = run_stage(h, c3, false, s); rc != GDG_OK) return rc;
   cudaError_t e = timed(h, GDG_K_CLOCK, s, [&] { return gdg::launch_clock_one(h->clk, 1.0, s); });
@@ -788,19 +792,19 @@ int gdg_ssprk3_step(gdg_handle* h, double* U, double* T1, double* T2, const doub
   if (!h || ((!U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
   if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
-  return ssprk3_stages(h, U, T1, T2, bdata, nullptr, (cudaStream_t)stream);
+  return ssprk3_stages(h, U, T1, T2, bdata, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 // The address kernels on the current device use for host memory p, when p lies in page-locked memory
 // mapped into the device's address space (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping);
 // null for any other memory.
-static const double* mapped_host(const double* p) {
+static double* mapped_host(const double* p) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();  // not a pointer the runtime knows: plain host memory
     return nullptr;
   }
-  return a.type == cudaMemoryTypeHost ? static_cast<const double*>(a.devicePointer) : nullptr;
+  return a.type == cudaMemoryTypeHost ? static_cast<double*>(a.devicePointer) : nullptr;
 }
 
 int gdg_ssprk3_step_host(gdg_handle* h, const double* U_host_in, double* U_host_out, double* U, double* T1,
@@ -808,15 +812,17 @@ int gdg_ssprk3_step_host(gdg_handle* h, const double* U_host_in, double* U_host_
   if (!h || ((!U_host_in || !U_host_out || !U || !T1 || !T2) && h->n > 0)) return GDG_EINVAL;
   if (h->n > 0 && (U == T1 || U == T2 || T1 == T2)) return GDG_EINVAL;
   if (h->has_dirichlet && !bdata) return GDG_EINVAL;
-  if (h->n == 0) return ssprk3_stages(h, U, T1, T2, bdata, nullptr, (cudaStream_t)stream);
+  if (h->n == 0) return ssprk3_stages(h, U, T1, T2, bdata, nullptr, nullptr, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * (size_t)(h->dim + 2) * h->n;
   const double* in_dev = mapped_host(U_host_in);
+  double* out_dev = in_dev ? mapped_host(U_host_out) : nullptr;
   cudaError_t e;
   if (!in_dev && (e = cudaMemcpyAsync(U, U_host_in, bytes, cudaMemcpyDefault, s)) != cudaSuccess)
     return cuda_fail(e);
-  if (int rc = ssprk3_stages(h, U, T1, T2, bdata, in_dev, s); rc != GDG_OK) return rc;
-  if ((e = cudaMemcpyAsync(U_host_out, U, bytes, cudaMemcpyDefault, s)) != cudaSuccess) return cuda_fail(e);
+  if (int rc = ssprk3_stages(h, U, T1, T2, bdata, in_dev, out_dev, s); rc != GDG_OK) return rc;
+  if (!out_dev && (e = cudaMemcpyAsync(U_host_out, U, bytes, cudaMemcpyDefault, s)) != cudaSuccess)
+    return cuda_fail(e);
   return GDG_OK;
 }
 

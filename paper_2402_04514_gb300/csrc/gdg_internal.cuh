@@ -199,6 +199,7 @@ struct Ctx {
   Scratch S;
   const double* U;      // stage input U_in [m][n]
   double* Ucopy;        // where the primitive sweep stores the U_in it read (a stage fed from host memory), or null
+  double* Uhost;        // a second copy of U_out in mapped host memory (the last stage of a host-fed step), or null
   const double* Ubase;  // SSP-RK base (read only where alpha != 0)
   double* Uout;         // stage output; may equal Ubase (each node reads its base before writing itself)
   const double* bdata;  // Dirichlet data [m][nb] or null
@@ -215,6 +216,12 @@ struct Ctx {
 __device__ __forceinline__ double rk_out(const Ctx& c, size_t idx, double fe) {
   if (c.Ubase2) return c.alpha * c.Ubase[idx] + c.alpha2 * c.Ubase2[idx] + c.w_fe * fe;
   return c.alpha != 0.0 ? c.alpha * c.Ubase[idx] + (1.0 - c.alpha) * fe : fe;
+}
+
+// Writes one value of the stage's output, and its host copy where the stage has one.
+__device__ __forceinline__ void store_out(const Ctx& c, size_t idx, double v) {
+  c.Uout[idx] = v;
+  if (c.Uhost) c.Uhost[idx] = v;
 }
 
 // An instance whose clock has reached t_end: every kernel of the fused step returns at once, so the

@@ -77,6 +77,7 @@ inline gdg::Ctx make_ctx(const gdg_handle* h, const double* U, const double* Uba
   c.S = h->S;
   c.U = U;
   c.Ucopy = nullptr;
+  c.Uhost = nullptr;
   c.Ubase = Ubase;
   c.Uout = Uout;
   c.bdata = bdata;

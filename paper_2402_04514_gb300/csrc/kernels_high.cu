@@ -206,7 +206,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
           du = to_f64(dUi[q]);
         else
           du = dUi[q];
-        c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, Ui[q] + du);
+        store_out(c, (size_t)q * n + i, rk_out(c, (size_t)q * n + i, Ui[q] + du));
       }
     }
   }

@@ -23,7 +23,7 @@ __device__ __forceinline__ void limit2_body(const Src& src, int sliced, int last
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
-  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced && !(last && c.Uhost));
   if (i < 0) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   double acc[M];
@@ -49,7 +49,7 @@ __device__ __forceinline__ void limit2_body(const Src& src, int sliced, int last
   for (int q = 0; q < M; ++q) U1[q] = S.UL[q * n + i] + acc[q] * inv_mi;
   if (last) {
 #pragma unroll
-    for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, U1[q]);
+    for (int q = 0; q < M; ++q) store_out(c, q * n + i, rk_out(c, q * n + i, U1[q]));
     return;
   }
 #pragma unroll
@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(kLsfixThreads) k_lsfix(Src src, int pass) {
 }
 
 // Sweep D: U^(2)_i = U^(1)_i + (sum_j l2_ij (1 - l1_ij) A_ij + sum_k l2_i^k (1 - l1_i^k) A_i^k) / m_i,
-// symmetrised as in sweep C, and U_out = alpha U_base + (1 - alpha) U^(2).
+// symmetrised as in sweep C, and U_out = alpha U_base + (1 - alpha) U^(2).  A writer of the step's host
+// output (c.Uhost) takes its rows in node order whatever the schedule says, so that each warp's stores
+// over the host link are contiguous (sweep C with one pass and the low-order sweep likewise).
 template <int DIM, class Src>
 __device__ __forceinline__ void final_body(const Src& src, int sliced) {
   constexpr int M = DIM + 2;
@@ -149,12 +151,12 @@ __device__ __forceinline__ void final_body(const Src& src, int sliced) {
   if (finished(c)) return;
   const Dev& D = c.D;
   const Scratch& S = c.S;
-  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced && !c.Uhost);
   if (i < 0) return;
   const size_t n = D.n, nnz = D.nnz, nb = D.nb;
   if (!S.rem[i]) {  // no remainder in the row: U^(2)_i = U^(1)_i
 #pragma unroll
-    for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, S.U1[q * n + i]);
+    for (int q = 0; q < M; ++q) store_out(c, q * n + i, rk_out(c, q * n + i, S.U1[q * n + i]));
     return;
   }
   double acc[M];
@@ -177,7 +179,7 @@ __device__ __forceinline__ void final_body(const Src& src, int sliced) {
   }
   const double inv_mi = D.inv_mi[i];
 #pragma unroll
-  for (int q = 0; q < M; ++q) c.Uout[q * n + i] = rk_out(c, q * n + i, S.U1[q * n + i] + acc[q] * inv_mi);
+  for (int q = 0; q < M; ++q) store_out(c, q * n + i, rk_out(c, q * n + i, S.U1[q * n + i] + acc[q] * inv_mi));
 }
 
 template <int DIM, class Src>

@@ -17,7 +17,8 @@ constexpr int kThreads = kRowMaxThreads;  // launch bound; the schedule launches
 // also empties the stage's deferred line-search queues.  The mixed path (MX) keeps 1/rho and p in FP64
 // (the fluxes use them) and computes the rest in FP32.  With c.Ucopy set (the first stage of a step whose
 // state comes from host memory, read here over the host link) it also stores the state it read there, for
-// the later sweeps of the stage, even when the instance's clock has finished.
+// the later sweeps of the stage; when the instance's clock has finished, the step is a no-op and it also
+// writes that state to c.Uhost, the step's host output, where the last stage's writers would have.
 template <int DIM, bool MX, class Src>
 __device__ __forceinline__ void prim_body(const Src& src) {
   __shared__ Ctx sctx;
@@ -38,7 +39,12 @@ __device__ __forceinline__ void prim_body(const Src& src) {
   if (c.Ucopy) {
 #pragma unroll
     for (int q = 0; q < DIM + 2; ++q) c.Ucopy[(size_t)q * D.n + i] = Ui[q];
-    if (done) return;
+    if (done) {
+      if (c.Uhost)
+#pragma unroll
+        for (int q = 0; q < DIM + 2; ++q) c.Uhost[(size_t)q * D.n + i] = Ui[q];
+      return;
+    }
   }
   double irho = rcp64(Ui[0]);
   double m2 = 0.0;
@@ -331,7 +337,7 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
   const Dev& D = c.D;
   const Scratch& S = c.S;
   const double* U = c.U;
-  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced);
+  const int i = row_node(D, lb * blockDim.x + threadIdx.x, sliced && !(write_out && c.Uhost));
   if (i < 0) return;
   const double tau = stage_tau(c);
   size_t n = D.n;
@@ -436,7 +442,7 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
   for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
   if (write_out) {
 #pragma unroll
-    for (int q = 0; q < M; ++q) c.Uout[(size_t)q * n + i] = rk_out(c, (size_t)q * n + i, UL[q]);
+    for (int q = 0; q < M; ++q) store_out(c, (size_t)q * n + i, rk_out(c, (size_t)q * n + i, UL[q]));
     return;
   }
 #pragma unroll

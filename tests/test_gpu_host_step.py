@@ -1,7 +1,8 @@
 """gdg_ssprk3_step_host: the fused SSP-RK3 step (Sec. 6.2) of a state kept in host memory.  Page-locked
-input is read by the first stage's primitive sweep over the host link; pageable input and every output go
-through cudaMemcpyAsync.  Either way the result must be bit for bit the device step's (the same kernels on
-the same values), and the device step is compared with the oracle here once more and in test_gpu_step."""
+input is read by the first stage's primitive sweep over the host link, and page-locked output (with
+page-locked input) is written by the last stage's sweeps; other buffers go through cudaMemcpyAsync.  Every
+way the result must be bit for bit the device step's (the same kernels on the same values), and the device
+step is compared with the oracle here once more and in test_gpu_step."""
 import numpy as np
 import pytest
 
@@ -91,22 +92,50 @@ def test_pinned_host_step_equals_device_step(torch_cuda, name):
     assert rel_err(ref[0], first) <= 1e-12
 
 
-def test_pageable_and_aliased_host_buffers(torch_cuda):
-    """numpy (pageable) buffers take the copy path, and one page-locked buffer may be both input and
-    output: both give the device step's bits."""
+def test_pageable_mixed_and_aliased_host_buffers(torch_cuda):
+    """numpy (pageable) buffers take the copy path; page-locked input with pageable output, and pageable
+    input with page-locked output, take it on one side; one page-locked buffer may be both input and
+    output.  Every combination gives the device step's bits."""
     torch = torch_cuda
     P, U0, bd, (Sd, Sh), _ = _pair(torch, "fq_q2_slip")
-    ref, _ = _device_steps(torch, Sd, U0, bd, 2)
+    ref, _ = _device_steps(torch, Sd, U0, bd, 4)
     U = torch.empty(U0.shape, dtype=torch.float64, device="cuda")
     work = (torch.empty_like(U), torch.empty_like(U))
+    sync = torch.cuda.current_stream().synchronize
     a, b = U0.copy(), np.full_like(U0, np.nan)
     Sh.step_host(a, b, U, work)
-    torch.cuda.current_stream().synchronize()
+    sync()
     assert np.array_equal(b, ref[0]) and np.array_equal(a, U0)
-    h = torch.from_numpy(b.copy()).pin_memory()
-    Sh.step_host(h, h, U, work)
-    torch.cuda.current_stream().synchronize()
-    assert np.array_equal(h.numpy(), ref[1])
+    pin_in, page_out = torch.from_numpy(b.copy()).pin_memory(), np.full_like(U0, np.nan)
+    Sh.step_host(pin_in, page_out, U, work)
+    sync()
+    assert np.array_equal(page_out, ref[1])
+    pin_out = torch.full(U0.shape, np.nan, dtype=torch.float64).pin_memory()
+    Sh.step_host(page_out, pin_out, U, work)
+    sync()
+    assert np.array_equal(pin_out.numpy(), ref[2])
+    Sh.step_host(pin_out, pin_out, U, work)
+    sync()
+    assert np.array_equal(pin_out.numpy(), ref[3])
+
+
+@pytest.mark.parametrize("order,passes", [(0, 2), (1, 2), (2, 1), (2, 0)])
+def test_host_output_from_every_final_writer(torch_cuda, order, passes):
+    """The last stage's output, and its host copy, come from the low-order sweep (order LOW, or no limiter
+    pass), the element sweep (order HIGH) or sweep C (one pass): each gives the device step's bits."""
+    torch = torch_cuda
+    P, U0, bd, (Sd, Sh), _ = _pair(torch, "fq_q2_slip", params=dict(order=order, limiter_passes=passes))
+    ref, _ = _device_steps(torch, Sd, U0, bd, 2)
+    hin = torch.from_numpy(U0.copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    U = torch.empty(U0.shape, dtype=torch.float64, device="cuda")
+    work = (torch.empty_like(U), torch.empty_like(U))
+    for k in range(2):
+        hout.fill_(np.nan)
+        Sh.step_host(hin, hout, U, work)
+        torch.cuda.current_stream().synchronize()
+        assert np.array_equal(hout.numpy(), ref[k]), k
+        hin, hout = hout, hin
 
 
 def test_mixed_precision_host_step(torch_cuda):
