@@ -234,8 +234,11 @@ int gdg_profile_read(gdg_handle* h, double* total_ms, int64_t* launches);
  * 3 = CUDA's pow(x, -1.0 / q), 4 = the integer-only FP64 -> FP32 -> FP64 conversion pair of the FP32
  * certificates (truncation to 23 significand bits in the FP32 normal range, zeros kept, NaN otherwise),
  * 5 = square root from the FP32 reciprocal square root, 6 = CUDA's sqrt; x, y: device [n];
- * 1 <= q <= 16.  Asynchronous on stream.  The tests compare 0 with 2, 1 with 3 and 5 with 6 in ulps,
- * and 4 with the truncation done on the host. */
+ * 1 <= q <= 16.  fn 7..10 take pairs: x is [2n] and y[i] is computed from x[2i] and x[2i+1] by 7 = the
+ * integer-pipe binary64 product of the sweep kernels, 8 = CUDA's __dmul_rn, 9 = the integer-pipe sum,
+ * 10 = CUDA's __dadd_rn, 11 = the integer-pipe scaling x[2i] * 2^k with k = x[2i+1], an integer in
+ * [-1022, 1023] (q is not used).  Asynchronous on stream.  The tests compare 0 with 2, 1 with 3
+ * and 5 with 6 in ulps, 4 with the truncation done on the host, 7 with 8 and 9 with 10 bit for bit. */
 int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream);
 
 /* Check of the mixed-precision wave-speed bound (GDG_PRECISION_MIXED) against the FP64 one, for gamma

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "../../include/gdg.h"
+#include "softfp64.cuh"
 
 namespace gdg {
 
@@ -212,10 +213,13 @@ struct Ctx {
   double dt_factor;     // dt = min(cfl * dt_factor * bound, t_end - t): the method's SSP coefficient
 };
 
-// The stage's output at flat index idx from its forward-Euler value fe (Shu-Osher combination).
+// The stage's output at flat index idx from its forward-Euler value fe (Shu-Osher combination).  Sums of
+// products are written as explicit fused operations: left to the compiler, which product it fuses can
+// differ between two instantiations of one kernel, and a batch member must give the bits of its solve
+// alone.
 __device__ __forceinline__ double rk_out(const Ctx& c, size_t idx, double fe) {
-  if (c.Ubase2) return c.alpha * c.Ubase[idx] + c.alpha2 * c.Ubase2[idx] + c.w_fe * fe;
-  return c.alpha != 0.0 ? c.alpha * c.Ubase[idx] + (1.0 - c.alpha) * fe : fe;
+  if (c.Ubase2) return fma(c.w_fe, fe, fma(c.alpha2, c.Ubase2[idx], sf::mul(c.alpha, c.Ubase[idx])));
+  return c.alpha != 0.0 ? fma(1.0 - c.alpha, fe, sf::mul(c.alpha, c.Ubase[idx])) : fe;
 }
 
 // Writes one value of the stage's output, and its host copy where the stage has one.
@@ -412,13 +416,13 @@ inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sc
 __device__ __forceinline__ double ipow(double x, int k) {
   if (k <= 0) return 1.0;
   while (!(k & 1)) {
-    x *= x;
+    x = sf::mul(x, x);
     k >>= 1;
   }
   double r = x;
   while (k >>= 1) {
-    x *= x;
-    if (k & 1) r *= x;
+    x = sf::mul(x, x);
+    if (k & 1) r = sf::mul(r, x);
   }
   return r;
 }
@@ -498,7 +502,7 @@ __device__ __forceinline__ double sqrt64(double x) {
   if (!(xf > 1e-37f && xf < 1e37f)) return sqrt(x);
   const float yf = rsqrtf(xf);
   const double h = f2d_fast(0.5f * yf);
-  double s = x * f2d_fast(yf);
+  double s = sf::mul(x, f2d_fast(yf));
   s = fma(fma(-s, s, x), h, s);
   return fma(fma(-s, s, x), h, s);
 }
@@ -515,7 +519,7 @@ __device__ __forceinline__ double rootinv(double x, const RootQ& r) {
   if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -r.iq);
   double y = f2d_fast(exp2f(-log2f(xf) / (float)r.q));
   const double t = fma(-x, ipow(y, r.q), 1.0);
-  y = fma(y * t, fma(r.c2, t, r.iq), y);
+  y = fma(sf::mul(y, t), fma(r.c2, t, r.iq), y);
   // |t| > 2^-19, compared on the bit patterns (integer pipe)
   if ((__double_as_longlong(t) & 0x7fffffffffffffffLL) > 0x3ec0000000000000LL) {
     const double t2 = fma(-x, ipow(y, r.q), 1.0);
@@ -533,7 +537,7 @@ __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double
     const double y = rootinv(rho, D.root_gq);
     const double yq = ipow(y, D.gq);
     *inv_rho = yq;
-    return Share ? yq * ipow(y, D.gp - D.gq) : ipow(y, D.gp);
+    return Share ? sf::mul(yq, ipow(y, D.gp - D.gq)) : ipow(y, D.gp);
   }
   *inv_rho = rcp64(rho);
   return pow(rho, -D.gamma);
@@ -545,8 +549,8 @@ __device__ __forceinline__ double rho_pow_gamma(const Dev& D, double rho, double
   if (D.gq > 0) {
     const double y = rootinv(rho, D.root_gq);
     const double yc = ipow(y, D.gc);
-    *inv_rho = yc * ipow(y, D.gq - D.gc);
-    return ipow(rho, D.gk) * yc;
+    *inv_rho = sf::mul(yc, ipow(y, D.gq - D.gc));
+    return sf::mul(ipow(rho, D.gk), yc);
   }
   *inv_rho = rcp64(rho);
   return pow(rho, D.gamma);
@@ -573,14 +577,14 @@ __device__ __forceinline__ double lambda_max(const Dev& D, double uL, double pL,
   // max(x, 0), the tests x > 0 and the final maximum of two non-negative values on the integer pipe
   // (a positive double is a positive int64)
   auto pos = [](double x) { return __double_as_longlong(x) > 0 ? x : 0.0; };
-  double num = pos(aL + aR - D.gm1h * (uR - uL));
-  double r = num * rcp64(aL * pmeL + aR * pmeR);
+  double num = pos(fma(-D.gm1h, uR - uL, aL + aR));
+  double r = sf::mul(num, rcp64(fma(aL, pmeL, sf::mul(aR, pmeR))));
   double pt = D.ie > 0 ? ipow(r, D.ie) : pow(r, D.inv_e);
   double xL = pt - pL, xR = pt - pR;
-  double sL = __double_as_longlong(xL) > 0 ? sqrt64(1.0 + D.k13 * xL * ipL) : 1.0;
-  double sR = __double_as_longlong(xR) > 0 ? sqrt64(1.0 + D.k13 * xR * ipR) : 1.0;
-  double l1 = uL - aL * sL;
-  double l3 = uR + aR * sR;
+  double sL = __double_as_longlong(xL) > 0 ? sqrt64(fma(sf::mul(D.k13, xL), ipL, 1.0)) : 1.0;
+  double sR = __double_as_longlong(xR) > 0 ? sqrt64(fma(sf::mul(D.k13, xR), ipR, 1.0)) : 1.0;
+  double l1 = fma(-aL, sL, uL);
+  double l3 = fma(aR, sR, uR);
   return pmax(pos(-l1), pos(l3));
 }
 
@@ -679,7 +683,7 @@ __device__ __forceinline__ float lambda_max_mx(const Dev& D, float uL, float pL,
 // The FP64 primitives of k_prim's FP64 path from rho (as 1/rho) and p.
 __device__ __forceinline__ void prim_fp64(const Dev& D, double irho, double p, double* ip, double* a, double* pme) {
   *ip = 1.0 / p;
-  *a = sqrt64(D.gamma * p * irho);
+  *a = sqrt64(sf::mul(sf::mul(D.gamma, p), irho));
   *pme = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
 }
 
@@ -694,7 +698,7 @@ __device__ __forceinline__ void prim_of(const Dev& D, double rho, double irho, d
     *pme = to_f64(f.pme);
   } else {
     *ip = 1.0 / p;
-    *a = sqrt64(D.gamma * p * irho);
+    *a = sqrt64(sf::mul(sf::mul(D.gamma, p), irho));
     *pme = pow(p, -D.e_exp);
   }
 }
@@ -722,16 +726,25 @@ __device__ __forceinline__ void flux_n(const double* U, const double* n, double 
                                        double* out) {
   out[0] = mn;
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) out[1 + k] = U[1 + k] * un + p * n[k];
-  out[DIM + 1] = (U[DIM + 1] + p) * un;
+  for (int k = 0; k < DIM; ++k) out[1 + k] = fma(U[1 + k], un, sf::mul(p, n[k]));
+  out[DIM + 1] = sf::mul(U[DIM + 1] + p, un);
+}
+
+// a . b for DIM-vectors, as an explicit chain: the first product rounded on its own (integer pipe), each
+// later one fused into the sum.  Written out so that the compiler has no choice of which products to fuse:
+// where it has one, two instantiations of a kernel can round differently.
+template <int DIM>
+__device__ __forceinline__ double dot(const double* a, const double* b) {
+  double s = sf::mul(a[0], b[0]);
+#pragma unroll
+  for (int k = 1; k < DIM; ++k) s = fma(a[k], b[k], s);
+  return s;
 }
 
 template <int DIM>
 __device__ __forceinline__ double internal_energy(const double* U) {
-  double m2 = 0.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) m2 += U[1 + k] * U[1 + k];
-  return U[DIM + 1] - 0.5 * m2 / U[0];
+  const double m2 = dot<DIM>(U + 1, U + 1);
+  return U[DIM + 1] - sf::mul_pow2(m2, -1) / U[0];
 }
 
 // In- and outflow boundary state (Sec. 4.1) from the interior state Ui, the data Ud and the outward unit
@@ -810,12 +823,10 @@ __device__ __forceinline__ void boundary_state(const Dev& D, int b, const double
     for (int q = 0; q < M; ++q) Ud[q] = bdata[(size_t)q * D.nb + o];
     inoutflow_state<DIM>(D.gamma, Ui, Ud, n, UB);
   } else {
-    double mn = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) mn += Ui[1 + k] * n[k];
+    const double mn2 = sf::mul_pow2(dot<DIM>(Ui + 1, n), 1);  // 2 m.n
     UB[0] = Ui[0];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) UB[1 + k] = Ui[1 + k] - 2.0 * mn * n[k];
+    for (int k = 0; k < DIM; ++k) UB[1 + k] = fma(-mn2, n[k], Ui[1 + k]);
     UB[DIM + 1] = Ui[DIM + 1];
   }
 }
@@ -845,7 +856,7 @@ __device__ __forceinline__ void ls_row(const Dev& D, LsRow<DIM>& c, const double
   c.smin = smin;
   double ir;
   double rg = (U0[0] > 0.0) ? rho_pow_gamma(D, U0[0], &ir) : 0.0;
-  c.psi0 = (U0[0] > 0.0) ? U0[DIM + 1] - 0.5 * m2 * ir - smin * rg : -1.0;
+  c.psi0 = (U0[0] > 0.0) ? fma(-smin, rg, fma(-sf::mul_pow2(m2, -1), ir, U0[DIM + 1])) : -1.0;
   c.r0 = d2f_fast(U0[0]);
   c.ir0 = __frcp_rn(c.r0);
 #pragma unroll
@@ -880,7 +891,7 @@ __device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const d
   for (int k = 0; k < DIM; ++k) m2 += V[1 + k] * V[1 + k];
   double irho;
   double rg = rho_pow_gamma(D, V[0], &irho);
-  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
+  return fma(-smin, rg, fma(-sf::mul_pow2(m2, -1), irho, V[DIM + 1]));
 }
 
 // d psi / d s
@@ -920,7 +931,7 @@ __device__ __forceinline__ double ls_psi_dpsi(const Dev& D, const double* U0, co
   double deps = A[DIM + 1] - mA * irho + 0.5 * m2 * A[0] * irho * irho;
   *dpsi = deps - smin * D.gamma * rg * irho * A[0];
   if (!(V[0] > 0.0)) return -1.0;
-  return V[DIM + 1] - 0.5 * m2 * irho - smin * rg;
+  return fma(-smin, rg, fma(-sf::mul_pow2(m2, -1), irho, V[DIM + 1]));
 }
 
 // Certifies psi(s) >= 0 from psi(0) and the increment dpsi = psi(s) - psi(0) evaluated in FP32 in

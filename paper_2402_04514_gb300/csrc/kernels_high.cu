@@ -127,15 +127,16 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
           S.A[(size_t)q * D.nnz + e] = to_f64(td * du);  // viscous part of A_ij, completed below
         }
       } else {
+        // products on the integer pipe (sf::mul, the same bits as the FP64 instruction)
         const double dl = dl64;
-        const double dev = dl * pmin(D.c_ev * pmax(Ni, Nj), 1.0);
-        const double dd = pmax(mu * dl, dev) - dl;
-        const double td = tau * dd;
+        const double dev = sf::mul(dl, pmin(sf::mul(D.c_ev, pmax(Ni, Nj)), 1.0));
+        const double dd = pmax(sf::mul(mu, dl), dev) - dl;
+        const double td = sf::mul(tau, dd);
 #pragma unroll
         for (int q = 0; q < M; ++q) {
           const double du = Uj[q] - Ui[q];
           rhs[q] = fma(-dd, du, rhs[q]);
-          S.A[(size_t)q * D.nnz + e] = td * du;  // viscous part of A_ij, completed below
+          S.A[(size_t)q * D.nnz + e] = sf::mul(td, du);  // viscous part of A_ij, completed below
         }
       }
     }
@@ -165,9 +166,9 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
     if (lim) {  // relaxed local bounds, read back after the solve
       double rmin = 0.0, rmax = INFINITY, smin = 0.0;
       if (D.bounds_mode == 0) {
-        rmin = D.rminus[i] * lo;
-        rmax = D.rplus[i] * hi;
-        smin = D.rminus[i] * sl;
+        rmin = sf::mul(D.rminus[i], lo);
+        rmax = sf::mul(D.rplus[i], hi);
+        smin = sf::mul(D.rminus[i], sl);
       }
       S.bounds[i] = rmin;
       S.bounds[n + i] = rmax;
@@ -195,7 +196,10 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
     }
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      dUi[q] = -tau_r * acc[q];
+      if constexpr (MX)
+        dUi[q] = -tau_r * acc[q];
+      else
+        dUi[q] = sf::mul(-tau, acc[q]);
       sdU[q][sh] = dUi[q];
     }
     if (D.order == GDG_ORDER_HIGH) {

@@ -230,7 +230,7 @@ __device__ __forceinline__ void axpy_body(const Src& src) {
 #pragma unroll
   for (int q = 0; q < M; ++q) {
     const size_t idx = (size_t)q * n + i;
-    c.Uout[idx] = alpha != 0.0 ? alpha * c.Ubase[idx] + (1.0 - alpha) * c.U[idx] : c.U[idx];
+    c.Uout[idx] = alpha != 0.0 ? fma(1.0 - alpha, c.U[idx], sf::mul(alpha, c.Ubase[idx])) : c.U[idx];
   }
 }
 

@@ -47,12 +47,13 @@ __device__ __forceinline__ void prim_body(const Src& src) {
     }
   }
   double irho = rcp64(Ui[0]);
-  double m2 = 0.0;
+  // products on the integer pipe (sf::mul, the same bits as the FP64 instruction) where no sum follows
+  double m2 = sf::mul(Ui[1], Ui[1]);
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) m2 += Ui[1 + k] * Ui[1 + k];
-  double eps = Ui[DIM + 1] - 0.5 * m2 * irho;
+  for (int k = 1; k < DIM; ++k) m2 = fma(Ui[1 + k], Ui[1 + k], m2);
+  double eps = fma(-sf::mul_pow2(m2, -1), irho, Ui[DIM + 1]);
   if (!(Ui[0] > 0.0) || !(eps > 0.0)) atomicOr(S.flags, (unsigned)GDG_FLAG_INADMISSIBLE);
-  double p = D.gm1 * eps;
+  double p = sf::mul(D.gm1, eps);
   double* P = S.prim;
   size_t n = D.n;
   if constexpr (MX) {
@@ -74,16 +75,16 @@ __device__ __forceinline__ void prim_body(const Src& src) {
     return;
   }
   double ir;
-  double st = rho_neg_gamma<false>(D, Ui[0], &ir) * eps;
+  double st = sf::mul(rho_neg_gamma<false>(D, Ui[0], &ir), eps);
   P[PR_IRHO * n + i] = irho;
   P[PR_P * n + i] = p;
   P[PR_IP * n + i] = rcp64(p);
-  P[PR_A * n + i] = sqrt64(D.gamma * p * irho);
+  P[PR_A * n + i] = sqrt64(sf::mul(sf::mul(D.gamma, p), irho));
   P[PR_PME * n + i] = D.ie_root > 0 ? rootinv(p, D.root_ie) : pow(p, -D.e_exp);
   // f = (gm1 s~)^{1/(gamma+1)} = x^{q/(p+q)} = x (x^{-1/(p+q)})^p for gamma = p/q
-  double x = D.gm1 * st;
+  double x = sf::mul(D.gm1, st);
   P[PR_F * n + i] =
-      (D.gq > 0 && D.gp + D.gq <= 16) ? x * ipow(rootinv(x, D.root_gpq), D.gp) : pow(x, D.inv_gp1);
+      (D.gq > 0 && D.gp + D.gq <= 16) ? sf::mul(x, ipow(rootinv(x, D.root_gpq), D.gp)) : pow(x, D.inv_gp1);
   P[PR_ST * n + i] = st;
 }
 
@@ -104,17 +105,12 @@ __device__ __forceinline__ double boundary_viscosity(const Dev& D, int b, const 
   for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
   boundary_state<DIM>(D, b, Ui, bdata, nv, UB);
   double irB = 1.0 / UB[0];
-  double pB = D.gm1 * internal_energy<DIM>(UB);
-  double uL = 0.0, uR = 0.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    uL += Ui[1 + k] * nv[k];
-    uR += UB[1 + k] * nv[k];
-  }
+  double pB = sf::mul(D.gm1, internal_energy<DIM>(UB));
+  const double uL = dot<DIM>(Ui + 1, nv), uR = dot<DIM>(UB + 1, nv);
   double ipB, aB, pmeB;
   prim_of<MX>(D, UB[0], irB, pB, &ipB, &aB, &pmeB);
-  return D.bnorm[b] *
-         lambda_pair<MX>(D, uL * irho_i, p_i, irho_i, ip_i, a_i, pme_i, uR * irB, pB, irB, ipB, aB, pmeB);
+  return sf::mul(D.bnorm[b], lambda_pair<MX>(D, sf::mul(uL, irho_i), p_i, irho_i, ip_i, a_i, pme_i, sf::mul(uR, irB),
+                                             pB, irB, ipB, aB, pmeB));
 }
 
 // Block minimum of val, then one 64-bit atomicMin per block on the bit pattern (positive doubles order
@@ -158,22 +154,20 @@ __device__ __forceinline__ void maxdt_body(const Src& src, int sliced) {
     for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
       double cnm = D.cnorm[e];
       int j = D.col[e];
-      double nv[DIM], uL = 0.0, uR = 0.0;
+      double nv[DIM], mj[DIM];
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         nv[k] = D.cn[(size_t)k * D.nnz + e];
-        uL += Ui[1 + k] * nv[k];
-        uR += U[(size_t)(1 + k) * n + j] * nv[k];
+        mj[k] = U[(size_t)(1 + k) * n + j];
       }
       const double irho_j = P[PR_IRHO * n + j];
-      uL *= irho_i;
-      uR *= irho_j;
-      dsum += cnm * lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], irho_j,
-                                    P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
+      const double uL = sf::mul(dot<DIM>(Ui + 1, nv), irho_i), uR = sf::mul(dot<DIM>(mj, nv), irho_j);
+      dsum = fma(cnm, lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, P[PR_P * n + j], irho_j,
+                                      P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]), dsum);
     }
     for (int b = D.b_ptr[i]; b < D.b_ptr[i + 1]; ++b)
       dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, irho_i, p_i, ip_i, a_i, pme_i);
-    if (dsum > 0.0) val = 0.5 * D.mi[i] * rcp64(dsum);
+    if (dsum > 0.0) val = sf::mul(sf::mul_pow2(D.mi[i], -1), rcp64(dsum));
   }
   block_min_to(val, S.tau_bits);
 }
@@ -213,7 +207,7 @@ __device__ __forceinline__ void tau_body(const Src& src, int sliced) {
         dsum += boundary_viscosity<DIM, MX>(D, b, Ui, c.bdata, P[PR_IRHO * n + i], P[PR_P * n + i], P[PR_IP * n + i],
                                         P[PR_A * n + i], P[PR_PME * n + i]);
     }
-    if (dsum > 0.0) val = 0.5 * D.mi[i] * rcp64(dsum);
+    if (dsum > 0.0) val = sf::mul(sf::mul_pow2(D.mi[i], -1), rcp64(dsum));
   }
   block_min_to(val, &c.clk->tau_bits);
 }
@@ -251,27 +245,29 @@ __device__ __forceinline__ void edge_body(const Src& src) {
   load_state<DIM>(c.U, D.n, i, Ui);
   load_state<DIM>(c.U, D.n, j, Uj);
   const double cnm = D.cnorm[e];
-  double mnL = 0.0, mnR = 0.0;
+  // products on the integer pipe (sf::mul, the same bits as the FP64 instruction) where no sum follows
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) {
-    nv[q] = D.cn[(size_t)q * nnz + e];
-    mnL += Ui[1 + q] * nv[q];
-    mnR += Uj[1 + q] * nv[q];
+  for (int q = 0; q < DIM; ++q) nv[q] = D.cn[(size_t)q * nnz + e];
+  double mnL = sf::mul(Ui[1], nv[0]), mnR = sf::mul(Uj[1], nv[0]);
+#pragma unroll
+  for (int q = 1; q < DIM; ++q) {
+    mnL = fma(Ui[1 + q], nv[q], mnL);
+    mnR = fma(Uj[1 + q], nv[q], mnR);
   }
   const double p_i = P[PR_P * n + i], p_j = P[PR_P * n + j];
   const double ir_i = P[PR_IRHO * n + i], ir_j = P[PR_IRHO * n + j];
-  const double uL = mnL * ir_i, uR = mnR * ir_j;
+  const double uL = sf::mul(mnL, ir_i), uR = sf::mul(mnR, ir_j);
   const double lam = lambda_pair<MX>(D, uL, p_i, ir_i, P[PR_IP * n + i], P[PR_A * n + i], P[PR_PME * n + i], uR, p_j,
                                      ir_j, P[PR_IP * n + j], P[PR_A * n + j], P[PR_PME * n + j]);
-  const double d = cnm * lam;
+  const double d = sf::mul(cnm, lam);
   S.dL[e] = d;
   S.dL[t] = d;
   // f(U) c_ij with c_ij = |c_ij| n_ij, from m.c = |c| m.n and v.c = |c| v.n
   double cv[DIM], gi[M], gj[M];
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) cv[q] = cnm * nv[q];
-  flux_n<DIM>(Ui, cv, cnm * mnL, cnm * uL, p_i, gi);
-  flux_n<DIM>(Uj, cv, cnm * mnR, cnm * uR, p_j, gj);
+  for (int q = 0; q < DIM; ++q) cv[q] = sf::mul(cnm, nv[q]);
+  flux_n<DIM>(Ui, cv, sf::mul(cnm, mnL), sf::mul(cnm, uL), p_i, gi);
+  flux_n<DIM>(Uj, cv, sf::mul(cnm, mnR), sf::mul(cnm, uR), p_j, gj);
   // W = 2 Ubar = U_i + U_j - (f(U_j) - f(U_i)) c_ij / d_ij, halved where it is used
   const double r = MX ? to_f64(1.f / to_f32(d)) : rcp64(d);
   double W[M];
@@ -282,12 +278,12 @@ __device__ __forceinline__ void edge_body(const Src& src) {
     W[q] = fma(-r, gj[q] - gi[q], Ui[q] + Uj[q]);
   }
   double Ub[M];
-  Ub[0] = 0.5 * W[0];
-  Ub[DIM + 1] = 0.5 * W[DIM + 1];
-  double mw2 = 0.0, irb;  // |2 m(Ubar)|^2; 0.125 mw2 = |m(Ubar)|^2 / 2
+  Ub[0] = sf::mul_pow2(W[0], -1);
+  Ub[DIM + 1] = sf::mul_pow2(W[DIM + 1], -1);
+  double mw2 = sf::mul(W[1], W[1]), irb;  // |2 m(Ubar)|^2; 0.125 mw2 = |m(Ubar)|^2 / 2
 #pragma unroll
-  for (int q = 0; q < DIM; ++q) mw2 += W[1 + q] * W[1 + q];
-  const double hm2 = 0.125 * mw2;
+  for (int q = 1; q < DIM; ++q) mw2 = fma(W[1 + q], W[1 + q], mw2);
+  const double hm2 = sf::mul_pow2(mw2, -3);
   double stb;
   if constexpr (MX) {
     // eps(Ubar) in FP64 (E - |m|^2 / (2 rho) cancels at high Mach numbers) with 1/rho(Ubar) from one
@@ -303,7 +299,7 @@ __device__ __forceinline__ void edge_body(const Src& src) {
     }
   } else {
     const double rgb = rho_neg_gamma(D, Ub[0], &irb);  // sets irb = 1 / rho(Ubar) before its use below
-    stb = rgb * fma(-hm2, irb, Ub[DIM + 1]);
+    stb = sf::mul(rgb, fma(-hm2, irb, Ub[DIM + 1]));
   }
   S.barR[e] = Ub[0];
   S.barR[t] = Ub[0];
@@ -383,7 +379,7 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
     if constexpr (MX)
       psum += to_f32(S.G[e]) * (to_f32(P[PR_F * n + j]) - to_f32(f_i));
     else
-      psum += S.G[e] * (P[PR_F * n + j] - f_i);  // (m_j . c_ij) (f_j - f_i)
+      psum = fma(S.G[e], P[PR_F * n + j] - f_i, psum);  // (m_j . c_ij) (f_j - f_i)
     lo = pmin(lo, pmin(Uj[0], S.barR[e]));
     hi = pmax(hi, pmax(Uj[0], S.barR[e]));
     sl = pmin(sl, pmin(P[PR_ST * n + j], S.barS[e]));
@@ -398,26 +394,19 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
     for (int k = 0; k < DIM; ++k) nv[k] = D.bn[(size_t)k * D.nb + b];
     boundary_state<DIM>(D, b, Ui, c.bdata, nv, UB);
     double irB = 1.0 / UB[0];
-    double pB = D.gm1 * internal_energy<DIM>(UB);
-    double uL = 0.0, uR = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      uL += Ui[1 + k] * nv[k];
-      uR += UB[1 + k] * nv[k];
-    }
-    const double mnL = uL, mnR = uR;
-    uL *= irho_i;
-    uR *= irB;
+    double pB = sf::mul(D.gm1, internal_energy<DIM>(UB));
+    const double mnL = dot<DIM>(Ui + 1, nv), mnR = dot<DIM>(UB + 1, nv);
+    const double uL = sf::mul(mnL, irho_i), uR = sf::mul(mnR, irB);
     double cnm = D.bnorm[b];
     double ipB, aB, pmeB;
     prim_of<MX>(D, UB[0], irB, pB, &ipB, &aB, &pmeB);
-    double d = cnm * lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, pB, irB, ipB, aB, pmeB);
+    double d = sf::mul(cnm, lambda_pair<MX>(D, uL, p_i, irho_i, ip_i, a_i, pme_i, uR, pB, irB, ipB, aB, pmeB));
     S.dB[b] = d;
     dsum += d;
     double fi[M], fB[M];
     flux_n<DIM>(Ui, nv, mnL, uL, p_i, fi);
     flux_n<DIM>(UB, nv, mnR, uR, pB, fB);
-    double t = cnm / (2.0 * d);
+    double t = cnm / sf::mul_pow2(d, 1);
     double Ub[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) {
@@ -426,20 +415,20 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
       if constexpr (MX)
         Fsum[q] -= to_f32(cnm * fi[q]);
       else
-        Fsum[q] -= cnm * fi[q];
-      Ub[q] = 0.5 * (Ui[q] + UB[q]) - t * (fB[q] - fi[q]);
+        Fsum[q] = fma(-cnm, fi[q], Fsum[q]);
+      Ub[q] = fma(-t, fB[q] - fi[q], 0.5 * (Ui[q] + UB[q]));
     }
     S.bbar[b] = Ub[0];
-    S.bbar[(size_t)D.nb + b] = pow(Ub[0], -D.gamma) * internal_energy<DIM>(Ub);
+    S.bbar[(size_t)D.nb + b] = sf::mul(pow(Ub[0], -D.gamma), internal_energy<DIM>(Ub));
   }
   const double inv_mi = D.inv_mi[i];
-  if (2.0 * tau * dsum * inv_mi > 1.0 + 1e-12) atomicOr(S.flags, (unsigned)GDG_FLAG_CFL);
+  if (sf::mul(sf::mul(sf::mul_pow2(tau, 1), dsum), inv_mi) > 1.0 + 1e-12) atomicOr(S.flags, (unsigned)GDG_FLAG_CFL);
   double rhs[M];
 #pragma unroll
   for (int q = 0; q < M; ++q) rhs[q] = sg[q] - sdu[q];
   double UL[M];
 #pragma unroll
-  for (int q = 0; q < M; ++q) UL[q] = Ui[q] - tau * inv_mi * rhs[q];
+  for (int q = 0; q < M; ++q) UL[q] = fma(-sf::mul(tau, inv_mi), rhs[q], Ui[q]);
   if (write_out) {
 #pragma unroll
     for (int q = 0; q < M; ++q) store_out(c, (size_t)q * n + i, rk_out(c, (size_t)q * n + i, UL[q]));
@@ -467,7 +456,7 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
       v2 += v[k] * v[k];
     }
     float grad[M];
-    grad[0] = pref * (D.gm1h_f * v2 * ipf - D.gamma_f * irf);
+    grad[0] = pref * fmaf(D.gm1h_f * v2, ipf, -(D.gamma_f * irf));
 #pragma unroll
     for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-gm1 * v[k] * ipf);
     grad[DIM + 1] = pref * (gm1 * ipf);
@@ -480,23 +469,26 @@ __device__ __forceinline__ void low_body(const Src& src, int sliced, int write_o
     S.N[i] = Dn > 0.f ? to_f64(R / Dn) : 0.0;
   } else {
     // rho f / (gamma + 1) from rho itself and 1/p from k_prim, so that no division is needed here
-    const double pref = f_i * D.inv_gp1 * Ui[0];
+    const double pref = sf::mul(sf::mul(f_i, D.inv_gp1), Ui[0]);
     const double ip = ip_i;
-    double v2 = 0.0;
+    double vk[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) v2 += (Ui[1 + k] * irho_i) * (Ui[1 + k] * irho_i);
+    for (int k = 0; k < DIM; ++k) vk[k] = sf::mul(Ui[1 + k], irho_i);
+    double v2 = sf::mul(vk[0], vk[0]);
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) v2 = fma(vk[k], vk[k], v2);
     double grad[M];
-    grad[0] = pref * (D.gm1 * 0.5 * v2 * ip - D.gamma * irho_i);
+    grad[0] = sf::mul(pref, fma(sf::mul(sf::mul(D.gm1, 0.5), v2), ip, -sf::mul(D.gamma, irho_i)));
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) grad[1 + k] = pref * (-D.gm1 * (Ui[1 + k] * irho_i) * ip);
-    grad[DIM + 1] = pref * (D.gm1 * ip);
+    for (int k = 0; k < DIM; ++k) grad[1 + k] = sf::mul(pref, sf::mul(sf::mul(-D.gm1, vk[k]), ip));
+    grad[DIM + 1] = sf::mul(pref, sf::mul(D.gm1, ip));
     double R = psum, Dn = fabs(psum);
 #pragma unroll
     for (int q = 0; q < M; ++q) {
-      R -= grad[q] * Fsum[q];
-      Dn += fabs(grad[q]) * fabs(Fsum[q]);
+      R = fma(-grad[q], Fsum[q], R);
+      Dn = fma(fabs(grad[q]), fabs(Fsum[q]), Dn);
     }
-    S.N[i] = Dn > 0.0 ? R * rcp64(Dn) : 0.0;
+    S.N[i] = Dn > 0.0 ? sf::mul(R, rcp64(Dn)) : 0.0;
   }
 }
 

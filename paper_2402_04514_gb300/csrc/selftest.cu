@@ -21,15 +21,33 @@ __global__ void k_math(int fn, int q, const double* __restrict__ x, double* __re
   }
 }
 
+// The integer-pipe binary64 product and sum against the FP64 instructions: pairs (x[2i], x[2i+1]).
+__global__ void k_math2(int fn, const double* __restrict__ x, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = x[2 * i], b = x[2 * i + 1];
+  switch (fn) {
+    case 7: y[i] = sf::mul(a, b); break;
+    case 8: y[i] = __dmul_rn(a, b); break;
+    case 9: y[i] = sf::add(a, b); break;
+    case 10: y[i] = __dadd_rn(a, b); break;
+    case 11: y[i] = sf::mul_pow2(a, (int)b); break;
+    default: y[i] = 0.0;
+  }
+}
+
 }  // namespace
 }  // namespace gdg
 
 extern "C" int gdg_math_selftest(int32_t fn, int32_t q, const double* x, double* y, int64_t n, void* stream) {
-  if (fn < 0 || fn > 6 || q < 1 || q > 16 || n < 0 || (n > 0 && (!x || !y))) return GDG_EINVAL;
+  if (fn < 0 || fn > 11 || q < 1 || q > 16 || n < 0 || (n > 0 && (!x || !y))) return GDG_EINVAL;
   if (n == 0) return GDG_OK;
   int threads = 256;
   long long blocks = (n + threads - 1) / threads;
-  gdg::k_math<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(fn, q, x, y, n);
+  if (fn >= 7)
+    gdg::k_math2<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(fn, x, y, n);
+  else
+    gdg::k_math<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(fn, q, x, y, n);
   return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
 }
 

@@ -178,11 +178,13 @@ def _stream(stream):
 
 
 def math_selftest(fn: int, q: int, x, stream=None):
-    """Runs gdg_math_selftest on the device tensor x (float64) and returns the result tensor."""
+    """Runs gdg_math_selftest on the device tensor x (float64) and returns the result tensor (for the
+    binary functions 7..10, x holds pairs and the result has half its length)."""
     import torch
 
-    y = torch.empty_like(x)
-    _check(load().gdg_math_selftest(fn, q, _ptr(x), _ptr(y), x.numel(), _stream(stream)), "gdg_math_selftest")
+    n = x.numel() // 2 if fn >= 7 else x.numel()
+    y = torch.empty(n, dtype=x.dtype, device=x.device)
+    _check(load().gdg_math_selftest(fn, q, _ptr(x), _ptr(y), n, _stream(stream)), "gdg_math_selftest")
     return y
 
 

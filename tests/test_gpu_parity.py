@@ -357,6 +357,68 @@ def test_square_root_against_cuda(torch_cuda):
     assert mine[-3:].tolist() == ref[-3:].tolist()
 
 
+def _binary64_pairs(rng, n):
+    """Operand pairs for the integer-pipe product and sum: any bit patterns, magnitudes near 1, opposite
+    signs with close exponents (cancellation), significands with trailing zeros (exact results and ties),
+    exponents near both ends of the range, and zeros, infinities, NaN and subnormals."""
+    bits = rng.integers(0, 2**63, (8, n), dtype=np.int64).astype(np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, (8, n)).astype(np.uint64)
+    frac, sign = bits & np.uint64(0xFFFFFFFFFFFFF), bits >> np.uint64(63)
+
+    def make(s, field, f):
+        return ((s << np.uint64(63)) | (field.astype(np.uint64) << np.uint64(52)) | f).view(np.float64)
+
+    fields = [rng.integers(1000, 1047, n), rng.integers(1, 2047, n), rng.integers(1, 40, n),
+              rng.integers(2007, 2047, n)]
+    a = [bits[0].view(np.float64), make(sign[1], fields[0], frac[1]), make(sign[2], fields[1], frac[2])]
+    b = [bits[1].view(np.float64), make(sign[3], fields[0], frac[3]), -a[2] * (1 + np.ldexp(1.0, -rng.integers(1, 60, n)))]
+    shift = rng.integers(0, 32, n).astype(np.uint64)
+    a.append(make(sign[4], fields[1], (frac[4] >> shift) << shift))
+    b.append(make(sign[5], fields[1], (frac[5] >> shift) << shift))
+    a.append(make(sign[6], np.where(fields[2] % 2 == 0, fields[2], fields[3]), frac[6]))
+    b.append(make(sign[7], np.where(fields[2] % 3 == 0, fields[2], fields[3]), frac[7]))
+    special = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 5e-324, -2.5e-320, 2.2250738585072014e-308,
+                        1.7976931348623157e308, 0.5])
+    a.append(np.where(rng.random(n) < 0.5, special[rng.integers(0, 12, n)], a[1]))
+    b.append(special[rng.integers(0, 12, n)])
+    ia, ib = rng.integers(1, 2**27, n) | 1, rng.integers(1, 2**28, n) | 1
+    a.append(np.ldexp(ia.astype(np.float64), rng.integers(-100, 100, n)))
+    b.append(np.ldexp(ib.astype(np.float64), rng.integers(-100, 100, n)) * rng.choice([-1.0, 1.0], n))
+    A, B = np.concatenate(a), np.concatenate(b)
+    return np.stack([A, B], axis=1).reshape(-1)
+
+
+def test_integer_binary64_against_cuda(torch_cuda):
+    """The integer-pipe product and sum of the sweep kernels give the FP64 instructions' results bit for bit
+    (any NaN for any NaN) over 1.4 million operand pairs, and agree with numpy's binary64 arithmetic; the
+    scaling by 2^k agrees with the product by 2^k."""
+    torch = torch_cuda
+    from paper_2402_04514_gb300.gdg import math_selftest
+
+    x = _binary64_pairs(np.random.default_rng(11), 200000)
+    xd = torch.from_numpy(x).cuda()
+    a, b = x[0::2], x[1::2]
+    with np.errstate(all="ignore"):
+        host = {7: a * b, 9: a + b}
+    for soft, hw in ((7, 8), (9, 10)):
+        mine, ref = math_selftest(soft, 1, xd).cpu().numpy(), math_selftest(hw, 1, xd).cpu().numpy()
+        nan = np.isnan(ref)
+        assert (np.isnan(mine) == nan).all()
+        assert (mine[~nan].view(np.uint64) == ref[~nan].view(np.uint64)).all()
+        assert (ref[~nan].view(np.uint64) == host[soft][~nan].view(np.uint64)).all()
+    # x 2^k by the exponent field against numpy's ldexp (the same rounding as the product by 2^k)
+    rng = np.random.default_rng(12)
+    k = np.clip(rng.integers(-60, 61, a.size) + np.where(rng.random(a.size) < 0.1, rng.integers(-1022, 1023, a.size), 0),
+                -1022, 1023)
+    xk = np.stack([a, k.astype(np.float64)], axis=1).reshape(-1)
+    mine = math_selftest(11, 1, torch.from_numpy(xk).cuda()).cpu().numpy()
+    with np.errstate(all="ignore"):
+        ref = a * np.ldexp(1.0, k)
+    nan = np.isnan(ref)
+    assert (np.isnan(mine) == nan).all()
+    assert (mine[~nan].view(np.uint64) == ref[~nan].view(np.uint64)).all()
+
+
 def test_integer_float_conversions(torch_cuda):
     """The FP64 -> FP32 -> FP64 conversions of the FP32 certificates, done with integer operations only:
     truncation to 23 significand bits in the FP32 normal range, signed zeros kept, NaN for everything
