@@ -616,10 +616,12 @@ def main():
             os.path.join(ROOT, "profiles", "dram_traffic_q2_512_four_quadrant.txt"), top, n,
             "mixed" if mixed else "fp64")
         alu = {"bound": "alu", "kernel": f"k_{top}", "achieved": fl / avg_s / 1e12,
-               "peak": costmodel.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": fl / avg_s / 1e12 / costmodel.FP64_PEAK_TFLOPS, "traffic": traffic,
-               "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-               "alg_flops_per_launch": fl}
+               "peak": costmodel.ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": fl / avg_s / 1e12 / costmodel.ALU_PEAK_TFLOPS, "traffic": traffic,
+               "peak_source": "unit counts and clock (2.07 GHz, 152 SMs): FP64 pipe 2 DFMA/clk/SM x 2 flop "
+                              f"({costmodel.FP64_PEAK_TFLOPS:.3f}) + integer-pipe binary64 products, 64 ALU lanes/clk/SM / "
+                              f"{costmodel.INT_MUL_ALU_INST} ALU instructions per product ({costmodel.INT_MUL_PEAK_TFLOPS:.3f})",
+               "fp64_pipe_peak": costmodel.FP64_PEAK_TFLOPS, "alg_flops_per_launch": fl}
         hbm = {"bound": "hbm", "kernel": f"k_{top}", "achieved": by / avg_s / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": by / avg_s / 1e9 / hbm_peak, "alg_bytes_per_launch": by,
                "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}

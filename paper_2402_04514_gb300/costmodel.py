@@ -84,8 +84,16 @@ def flops_per_launch(c: Counts) -> dict:
     )
 
 
-# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz.
+# FP64 pipe peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# The sweep kernels also run binary64 products on the integer pipe (csrc/softfp64.cuh).  One such product
+# issues INT_MUL_ALU_INST instructions on the ALU pipe (ncu instruction counts of a kernel doing nothing
+# else; the rest go to the FMA-heavy pipe, which is not the tighter one), and the ALU pipe retires 64
+# thread-instructions per clock per SM, so the integer pipes add 64 / INT_MUL_ALU_INST products (1 flop each)
+# per clock per SM.  The arithmetic roof of a kernel that keeps both pipes busy is the sum of the two.
+INT_MUL_ALU_INST = 33
+INT_MUL_PEAK_TFLOPS = 152 * 64 / INT_MUL_ALU_INST * 2.07e9 / 1e12
+ALU_PEAK_TFLOPS = FP64_PEAK_TFLOPS + INT_MUL_PEAK_TFLOPS
 
 
 def library_source_digest() -> str:

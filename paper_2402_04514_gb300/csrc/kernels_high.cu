@@ -101,7 +101,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
       hi = S.agg[n + i];
       sl = S.agg[2 * n + i];
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
       const int j = __ldg(D.col + e);
       const double dl64 = __ldg(S.dL + e), mu = __ldg(D.mu + e), Nj = abs_bits(__ldg(S.N + j));
@@ -166,9 +166,9 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
     if (lim) {  // relaxed local bounds, read back after the solve
       double rmin = 0.0, rmax = INFINITY, smin = 0.0;
       if (D.bounds_mode == 0) {
-        rmin = sf::mul(D.rminus[i], lo);
-        rmax = sf::mul(D.rplus[i], hi);
-        smin = sf::mul(D.rminus[i], sl);
+        rmin = D.rminus[i] * lo;
+        rmax = D.rplus[i] * hi;
+        smin = D.rminus[i] * sl;
       }
       S.bounds[i] = rmin;
       S.bounds[n + i] = rmax;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
       if constexpr (MX)
         dUi[q] = -tau_r * acc[q];
       else
-        dUi[q] = sf::mul(-tau, acc[q]);
+        dUi[q] = -tau * acc[q];
       sdU[q][sh] = dUi[q];
     }
     if (D.order == GDG_ORDER_HIGH) {

@@ -308,7 +308,7 @@ __device__ __forceinline__ void edge_body(const Src& src) {
 }
 
 template <int DIM, bool MX, class Src>
-__global__ void __launch_bounds__(kThreads, 1) k_edge(Src src) {
+__global__ void __launch_bounds__(kThreads, 2) k_edge(Src src) {
   edge_body<DIM, MX, Src>(src);
 }
 
