@@ -5,7 +5,8 @@ arrays of nnz entries, per-node arrays of n nodes); neighbour states are counted
 entry (an ideal cache).  FP64 operations: the arithmetic of the method as the kernels state it, counted
 per stencil entry (c_ij != 0), per CSR entry and per node, with add/sub/mul = 1, fused multiply-add = 2,
 and division, square root and power = 1 each (the usual floating-point operation count; their cost in
-hardware is several to ~100 FMA issue slots, which is why the sweep is bound by the FP64 pipe).
+hardware is several to ~100 FMA issue slots, which is why the sweep is bound by arithmetic: the FP64 pipe
+and, for the products the kernels move there, the integer pipe).
 The line-search counts assume no bracketing iteration (the common case); iterations add work that is
 not counted, so the FP64 fraction reported is a lower bound.
 """
