@@ -259,7 +259,9 @@ int gdg_certificate_check(int32_t dim, double gamma, const double* in, double* o
 /* Measured throughput (operations per second over the GPU, timed with CUDA events) of the arithmetic
  * the sweep is made of: op 0 = FP64 FMA, 1 = FP64 division, 2 = FP64 sqrt, 3 = FP64 pow, 4 = FP32 FMA,
  * 5 = this library's FP64 reciprocal, 6 = this library's x^{-1/5}, 7 = an FP64 -> FP32 -> FP64
- * conversion pair.  Allocates and frees a scratch
+ * conversion pair, 8 = FP64 multiplication, 9 = the integer-pipe binary64 product of the sweep kernels,
+ * 10 = half of the chains on each of the two, 11 = FP64 addition, 12 = the integer-pipe sum, 13 = a
+ * quarter of the chains on the integer pipe.  Allocates and frees a scratch
  * buffer; synchronises the stream.  Used for the FP64 roofline of the measurement script. */
 int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream);
 

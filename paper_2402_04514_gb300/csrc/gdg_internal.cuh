@@ -411,18 +411,31 @@ inline cudaError_t launch_one(int kern, int dim, const Ctx& c, int arg, const Sc
 // ------------------------------------------------------------------------------------------------
 // Device helpers (Euler equations of Sec. 2.2 and the pieces of Sec. 3-5 used by several kernels).
 
+// a * b on the integer pipe (Soft, csrc/softfp64.cuh) or on the FP64 pipe: the same bits either way.  The
+// deferred line searches take the FP64 pipe: their few active lanes per warp hide less of the integer
+// routine's latency than they gain from the freed FP64 slots (k_lsfix 0.37 -> 0.41 ms per launch at Q2
+// 1024^2 with the integer products).
+template <bool Soft>
+__device__ __forceinline__ double mulp(double a, double b) {
+  if constexpr (Soft)
+    return sf::mul(a, b);
+  else
+    return a * b;
+}
+
 // x^k for an integer k >= 0 by binary powering without a trailing square (k = 5, 7, 12 take 3, 4, 4
 // multiplications).
+template <bool Soft = true>
 __device__ __forceinline__ double ipow(double x, int k) {
   if (k <= 0) return 1.0;
   while (!(k & 1)) {
-    x = sf::mul(x, x);
+    x = mulp<Soft>(x, x);
     k >>= 1;
   }
   double r = x;
   while (k >>= 1) {
-    x = sf::mul(x, x);
-    if (k & 1) r = sf::mul(r, x);
+    x = mulp<Soft>(x, x);
+    if (k & 1) r = mulp<Soft>(r, x);
   }
   return r;
 }
@@ -514,15 +527,16 @@ __device__ __forceinline__ double sqrt64(double x) {
 // gives for arguments near 1.  Far
 // from 1 log2f's absolute error grows with |log2 x| and the seed can be worse; then one Newton step
 // y <- y + y (1 - x y^q) / q squares the remaining error.  Arguments outside the FP32 normal range use pow.
+template <bool Soft = true>
 __device__ __forceinline__ double rootinv(double x, const RootQ& r) {
   float xf = d2f_fast(x);
   if (!(xf > 1e-37f && xf < 1e37f)) return pow(x, -r.iq);
   double y = f2d_fast(exp2f(-log2f(xf) / (float)r.q));
-  const double t = fma(-x, ipow(y, r.q), 1.0);
-  y = fma(sf::mul(y, t), fma(r.c2, t, r.iq), y);
+  const double t = fma(-x, ipow<Soft>(y, r.q), 1.0);
+  y = fma(mulp<Soft>(y, t), fma(r.c2, t, r.iq), y);
   // |t| > 2^-19, compared on the bit patterns (integer pipe)
   if ((__double_as_longlong(t) & 0x7fffffffffffffffLL) > 0x3ec0000000000000LL) {
-    const double t2 = fma(-x, ipow(y, r.q), 1.0);
+    const double t2 = fma(-x, ipow<Soft>(y, r.q), 1.0);
     y = fma(y * t2, r.iq, y);
   }
   return y;
@@ -545,12 +559,13 @@ __device__ __forceinline__ double rho_neg_gamma(const Dev& D, double rho, double
 
 // rho^gamma and 1/rho together.  With gamma = p/q, k = ceil(p/q) and c = kq - p (0 <= c < q):
 // rho^gamma = rho^k y^c and 1/rho = y^q = y^c y^{q-c}.
+template <bool Soft = true>
 __device__ __forceinline__ double rho_pow_gamma(const Dev& D, double rho, double* inv_rho) {
   if (D.gq > 0) {
-    const double y = rootinv(rho, D.root_gq);
-    const double yc = ipow(y, D.gc);
-    *inv_rho = sf::mul(yc, ipow(y, D.gq - D.gc));
-    return sf::mul(ipow(rho, D.gk), yc);
+    const double y = rootinv<Soft>(rho, D.root_gq);
+    const double yc = ipow<Soft>(y, D.gc);
+    *inv_rho = mulp<Soft>(yc, ipow<Soft>(y, D.gq - D.gc));
+    return mulp<Soft>(ipow<Soft>(rho, D.gk), yc);
   }
   *inv_rho = rcp64(rho);
   return pow(rho, D.gamma);
@@ -890,7 +905,7 @@ __device__ __forceinline__ double ls_psi(const Dev& D, const double* U0, const d
 #pragma unroll
   for (int k = 0; k < DIM; ++k) m2 += V[1 + k] * V[1 + k];
   double irho;
-  double rg = rho_pow_gamma(D, V[0], &irho);
+  double rg = rho_pow_gamma<false>(D, V[0], &irho);
   return fma(-smin, rg, fma(-sf::mul_pow2(m2, -1), irho, V[DIM + 1]));
 }
 
@@ -907,7 +922,7 @@ __device__ __forceinline__ double ls_dpsi(const Dev& D, const double* U0, const 
     m2 += V[1 + k] * V[1 + k];
   }
   double irho;
-  double rg = rho_pow_gamma(D, V[0], &irho);
+  double rg = rho_pow_gamma<false>(D, V[0], &irho);
   double deps = A[DIM + 1] - mA * irho + 0.5 * m2 * A[0] * irho * irho;
   return deps - smin * D.gamma * rg * irho * A[0];
 }
@@ -927,7 +942,7 @@ __device__ __forceinline__ double ls_psi_dpsi(const Dev& D, const double* U0, co
     m2 += V[1 + k] * V[1 + k];
   }
   double irho;
-  double rg = rho_pow_gamma(D, V[0], &irho);
+  double rg = rho_pow_gamma<false>(D, V[0], &irho);
   double deps = A[DIM + 1] - mA * irho + 0.5 * m2 * A[0] * irho * irho;
   *dpsi = deps - smin * D.gamma * rg * irho * A[0];
   if (!(V[0] > 0.0)) return -1.0;

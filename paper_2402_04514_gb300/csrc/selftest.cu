@@ -164,6 +164,12 @@ __global__ void k_rate(double* out, int iters, double a, double b) {
       if (OP == 5) x[k] = rcp64(x[k]) + b;                 // reciprocal of this library
       if (OP == 6) x[k] = rootinv(x[k], root_q(5)) + b;            // x^{-1/5} of this library
       if (OP == 7) x[k] = (double)((float)x[k] * 0.5f) + b;  // FP64 -> FP32 -> FP64 conversion pair
+      if (OP == 8) x[k] = x[k] * a;                                  // DMUL
+      if (OP == 9) x[k] = sf::mul(x[k], a);                          // product on the integer pipe
+      if (OP == 10) x[k] = k < kIlp / 2 ? sf::mul(x[k], a) : x[k] * a;  // half the chains on each pipe
+      if (OP == 11) x[k] = x[k] + (k & 1 ? b : -b);                  // DADD
+      if (OP == 12) x[k] = sf::add(x[k], k & 1 ? b : -b);            // sum on the integer pipe
+      if (OP == 13) x[k] = k < kIlp / 4 ? sf::add(x[k], k & 1 ? b : -b) : x[k] + (k & 1 ? b : -b);  // a quarter
     }
   }
   double s = 0.0;
@@ -177,7 +183,8 @@ cudaError_t run_rate(int blocks, int threads, int iters, double* buf, cudaStream
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double a = (OP == 3) ? 0.3 : 0.999, b = (OP == 0 || OP == 4) ? 1e-3 : 0.5;
+  double a = (OP == 3) ? 0.3 : (OP >= 8 && OP <= 10) ? 0.9999 : 0.999;
+  double b = (OP == 0 || OP == 4 || OP >= 11) ? 1e-3 : 0.5;
   k_rate<OP><<<blocks, threads, 0, s>>>(buf, iters, a, b);  // warm-up
   cudaEventRecord(e0, s);
   k_rate<OP><<<blocks, threads, 0, s>>>(buf, iters, a, b);
@@ -193,12 +200,12 @@ cudaError_t run_rate(int blocks, int threads, int iters, double* buf, cudaStream
 }  // namespace gdg
 
 extern "C" int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream) {
-  if (op < 0 || op > 7 || !ops_per_s) return GDG_EINVAL;
+  if (op < 0 || op > 13 || !ops_per_s) return GDG_EINVAL;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int threads = 256, blocks = sms * 8;
-  const int iters[8] = {4096, 256, 256, 32, 16384, 512, 128, 1024};
+  const int iters[14] = {4096, 256, 256, 32, 16384, 512, 128, 1024, 4096, 2048, 4096, 4096, 2048, 4096};
   double* buf = nullptr;
   if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess) return GDG_ENOMEM;
   float ms = 0.f;
@@ -212,7 +219,13 @@ extern "C" int gdg_fp64_throughput(int32_t op, double* ops_per_s, void* stream) 
     case 4: e = gdg::run_rate<4>(blocks, threads, iters[4], buf, s, &ms); break;
     case 5: e = gdg::run_rate<5>(blocks, threads, iters[5], buf, s, &ms); break;
     case 6: e = gdg::run_rate<6>(blocks, threads, iters[6], buf, s, &ms); break;
-    default: e = gdg::run_rate<7>(blocks, threads, iters[7], buf, s, &ms); break;
+    case 7: e = gdg::run_rate<7>(blocks, threads, iters[7], buf, s, &ms); break;
+    case 8: e = gdg::run_rate<8>(blocks, threads, iters[8], buf, s, &ms); break;
+    case 9: e = gdg::run_rate<9>(blocks, threads, iters[9], buf, s, &ms); break;
+    case 10: e = gdg::run_rate<10>(blocks, threads, iters[10], buf, s, &ms); break;
+    case 11: e = gdg::run_rate<11>(blocks, threads, iters[11], buf, s, &ms); break;
+    case 12: e = gdg::run_rate<12>(blocks, threads, iters[12], buf, s, &ms); break;
+    default: e = gdg::run_rate<13>(blocks, threads, iters[13], buf, s, &ms); break;
   }
   cudaFree(buf);
   if (e != cudaSuccess) return GDG_ECUDA;

@@ -216,7 +216,8 @@ def max_dt_noalloc(mesh: DevMesh, U, cfl: float, tau_out, bdata=None, stream=Non
     return load().gdg_max_dt_noalloc(C.byref(mesh), _ptr(U), _ptr(bdata), cfl, _ptr(tau_out), _stream(stream))
 
 
-RATE_OPS = ("dfma", "ddiv", "dsqrt", "dpow", "ffma", "rcp64", "rootinv5", "f2f_pair")
+RATE_OPS = ("dfma", "ddiv", "dsqrt", "dpow", "ffma", "rcp64", "rootinv5", "f2f_pair", "dmul", "int_mul",
+            "dmul_half_int", "dadd", "int_add", "dadd_quarter_int")
 
 
 def fp64_throughput(stream=None) -> dict:
