@@ -101,6 +101,8 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
       hi = S.agg[n + i];
       sl = S.agg[2 * n + i];
     }
+    // not unrolled: with its products on the integer pipe the loop body is large, and unrolled by 2 the
+    // kernel stalled on instruction fetch (4.24 against 4.14 ms per launch at Q2 1024^2)
 #pragma unroll 1
     for (int e = D.rbeg[i]; e < e1; e += kEll) {  // I(i)
       const int j = __ldg(D.col + e);
@@ -285,7 +287,7 @@ __device__ __forceinline__ void high_sweep(const Src& src, int eb) {
 // The element sweep of each path as its own kernel with its own register budget.  Both run fastest at 72
 // registers (three 288-thread blocks per SM, a few spills): with the per-entry streams contiguous, the
 // resident warps matter more than the spills (the mixed path took 3.97 ms per launch at 96 registers,
-// 3.37 ms at 72, at 1024^2 Q2).
+// 3.37 ms at 72, at 1024^2 Q2; with the integer-pipe products the FP64 path 4.36 ms at 64, 4.15 at 72).
 template <int DIM, class Src>
 __global__ void __maxnreg__(72) k_high(Src src, int eb) {
   high_sweep<DIM, false, Src>(src, eb);

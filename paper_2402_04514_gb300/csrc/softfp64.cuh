@@ -3,9 +3,12 @@
 //
 // The GB300's FP64 pipe retires 2 thread-operations per clock per SM, 1/64 of the FP32 rate, while its
 // integer pipes retire 64.  The sweep kernels are bound by the FP64 pipe with most of their issue slots
-// free, so moving part of their FP64 products and sums to these integer routines runs both pipes at once.
+// free, so moving part of their FP64 products to these integer routines runs both pipes at once (the sum
+// is here too; it costs about twice a product and the kernels keep their sums on the FP64 pipe).
 // Every result is the correctly rounded IEEE result (the same bits as the hardware instruction), so a
-// kernel gives the same results whichever of its operations take this path.
+// kernel gives the same results whichever of its operations take this path.  The routines follow the
+// definition of the operations in IEEE 754 (form the exact result, then round it to nearest, ties to
+// even) on the significands as integers.
 //
 // The integer path covers normal operands whose result is normal, and zeros.  Everything else (subnormal,
 // infinite or NaN operands, a result at the ends of the exponent range) takes the hardware instruction, so
